@@ -1,0 +1,311 @@
+"""CPU oracle of the CNN-SNS particle-location path.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg may import this package; the product path never does.
+
+The particle-location part is plain C (oracle.c, single-threaded, FP64, user
+element ids, no reordering) reached through ctypes; the learned start
+predictor is plain numpy in FP64 (cnn.py). Nothing here shares code with the
+CUDA library.
+
+Result definition (Sec. 2.2 containment test with tolerance eps): the host of
+x_p is the lowest user id l with every lambda_i^l(x_p) >= -eps, or -1.
+Algorithm 1 gives the path length I_t from a start element.
+"""
+
+import ctypes
+import functools
+
+import numpy as np
+
+from . import build as _build
+
+EPS = 1e-12
+
+# walk exits
+CONTAINED, BOUNDARY, CAP, INVALID = 0, 1, 2, 3
+# track status (same codes as the library)
+ST_FOUND, ST_OUTSIDE, ST_FALLBACK, ST_INVALID = 0, 1, 2, 3
+
+_f64 = ctypes.POINTER(ctypes.c_double)
+_i32 = ctypes.POINTER(ctypes.c_int32)
+_u8 = ctypes.POINTER(ctypes.c_uint8)
+_i64t = ctypes.c_int64
+
+
+@functools.lru_cache(maxsize=1)
+def lib():
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    sig = {
+        "or_neighbors": (ctypes.c_int, [ctypes.c_int, _i64t, _i32, _i32]),
+        "or_neighbors_bruteforce": (ctypes.c_int, [ctypes.c_int, _i64t, _i32, _i32]),
+        "or_inverse_affine": (_i64t, [ctypes.c_int, _f64, _i64t, _i32, _f64, _f64]),
+        "or_bary": (None, [ctypes.c_int, _f64, _f64, _f64, _f64]),
+        "or_bary_det": (None, [ctypes.c_int, _f64, _f64, _f64]),
+        "or_departure": (None, [ctypes.c_int, _i64t, _f64, _f64, ctypes.c_double, _f64]),
+        "or_locate_bruteforce": (None, [ctypes.c_int, _i64t, _f64, _f64, _i64t, _f64,
+                                        ctypes.c_double, _i32]),
+        "or_locate_bucketed": (ctypes.c_int, [ctypes.c_int, _i64t, _f64, _i64t, _i32, _f64,
+                                              _f64, _i64t, _f64, ctypes.c_double,
+                                              ctypes.c_int, _i32]),
+        "or_walk": (None, [ctypes.c_int, _f64, _f64, _i32, _i64t, _f64, _i32,
+                           ctypes.c_double, ctypes.c_int32, _i32, _i32, _u8]),
+        "or_node_elements": (None, [ctypes.c_int, _i64t, _i64t, _i32, _i32]),
+        "or_grid_centres": (None, [ctypes.c_int, _f64, _f64, _i32, _f64]),
+        "or_grid_cell": (_i64t, [ctypes.c_int, _f64, _f64, _i32, _f64]),
+        "or_grid_cells": (None, [ctypes.c_int, _f64, _f64, _i32, _i64t, _f64,
+                                 ctypes.POINTER(ctypes.c_int64)]),
+        "or_p1_interpolate": (None, [ctypes.c_int, _i32, _f64, _f64, _f64, _i64t, _f64,
+                                     _i32, _f64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ct)
+
+
+def _f(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+# primitives
+# ---------------------------------------------------------------------------
+
+def neighbors(dim, conn, brute=False):
+    conn = _i(conn)
+    nbr = np.empty_like(conn)
+    fn = lib().or_neighbors_bruteforce if brute else lib().or_neighbors
+    rc = fn(dim, conn.shape[0], _p(conn, _i32), _p(nbr, _i32))
+    if rc != 0:
+        raise ValueError("non-manifold mesh (a face shared by more than two elements)")
+    return nbr
+
+
+def inverse_affine(xyz, conn):
+    xyz, conn = _f(xyz), _i(conn)
+    dim = xyz.shape[1]
+    n_e = conn.shape[0]
+    v0 = np.empty((n_e, dim))
+    M = np.empty((n_e, dim, dim))
+    bad = lib().or_inverse_affine(dim, _p(xyz, _f64), n_e, _p(conn, _i32),
+                                  _p(v0, _f64), _p(M, _f64))
+    if bad:
+        raise ValueError("degenerate element %d" % (bad - 1))
+    return v0, M
+
+
+def bary(v0, M, p):
+    v0, M, p = _f(v0), _f(M), _f(p)
+    dim = v0.shape[-1]
+    lam = np.empty(dim + 1)
+    lib().or_bary(dim, _p(v0, _f64), _p(M, _f64), _p(p, _f64), _p(lam, _f64))
+    return lam
+
+
+def bary_det(verts, p):
+    verts, p = _f(verts), _f(p)
+    dim = verts.shape[1]
+    lam = np.empty(dim + 1)
+    lib().or_bary_det(dim, _p(verts, _f64), _p(p, _f64), _p(lam, _f64))
+    return lam
+
+
+def departure(x, u, dt):
+    x, u = _f(x), _f(u)
+    xp = np.empty_like(x)
+    lib().or_departure(x.shape[1], x.shape[0], _p(x, _f64), _p(u, _f64), float(dt),
+                       _p(xp, _f64))
+    return xp
+
+
+def locate_bruteforce(v0, M, pts, eps=EPS):
+    v0, M, pts = _f(v0), _f(M), _f(pts)
+    host = np.empty(pts.shape[0], dtype=np.int32)
+    lib().or_locate_bruteforce(v0.shape[1], v0.shape[0], _p(v0, _f64), _p(M, _f64),
+                               pts.shape[0], _p(pts, _f64), eps, _p(host, _i32))
+    return host
+
+
+def locate_bucketed(xyz, conn, v0, M, pts, eps=EPS, g=None):
+    xyz, conn, v0, M, pts = _f(xyz), _i(conn), _f(v0), _f(M), _f(pts)
+    dim = xyz.shape[1]
+    if g is None:
+        g = max(1, int(round((conn.shape[0] / 4.0) ** (1.0 / dim))))
+    host = np.empty(pts.shape[0], dtype=np.int32)
+    rc = lib().or_locate_bucketed(dim, xyz.shape[0], _p(xyz, _f64), conn.shape[0],
+                                  _p(conn, _i32), _p(v0, _f64), _p(M, _f64), pts.shape[0],
+                                  _p(pts, _f64), eps, int(g), _p(host, _i32))
+    if rc:
+        raise MemoryError("oracle bucket grid")
+    return host
+
+
+def walk(v0, M, nbr, pts, start, eps=EPS, cap=None):
+    v0, M, nbr, pts, start = _f(v0), _f(M), _i(nbr), _f(pts), _i(start)
+    dim = v0.shape[1]
+    n = pts.shape[0]
+    if cap is None:
+        cap = step_cap(dim, v0.shape[0])
+    end = np.empty(n, dtype=np.int32)
+    it = np.empty(n, dtype=np.int32)
+    reason = np.empty(n, dtype=np.uint8)
+    lib().or_walk(dim, _p(v0, _f64), _p(M, _f64), _p(nbr, _i32), n, _p(pts, _f64),
+                  _p(start, _i32), eps, int(cap), _p(end, _i32), _p(it, _i32),
+                  _p(reason, _u8))
+    return end, it, reason
+
+
+def node_elements(n_v, conn):
+    conn = _i(conn)
+    dim = conn.shape[1] - 1
+    out = np.empty(n_v, dtype=np.int32)
+    lib().or_node_elements(dim, n_v, conn.shape[0], _p(conn, _i32), _p(out, _i32))
+    return out
+
+
+def step_cap(dim, n_e):
+    """Step cap 8 * n_e^(1/d) + 64 (the paper sets none; Algorithm 1 may cycle
+    on non-Delaunay meshes)."""
+    return int(8 * round(n_e ** (1.0 / dim)) + 64)
+
+
+# ---------------------------------------------------------------------------
+# ASG grid (Sec. 1, 2.3)
+# ---------------------------------------------------------------------------
+
+def bbox(xyz):
+    xyz = _f(xyz)
+    return xyz.min(axis=0).copy(), xyz.max(axis=0).copy()
+
+
+def grid_centres(lo, hi, g):
+    lo, hi, g = _f(lo), _f(hi), _i(g)
+    dim = lo.shape[0]
+    n = int(np.prod(g.astype(np.int64)))
+    out = np.empty((n, dim))
+    lib().or_grid_centres(dim, _p(lo, _f64), _p(hi, _f64), _p(g, _i32), _p(out, _f64))
+    return out
+
+
+def grid_cells(lo, hi, g, pts):
+    lo, hi, g, pts = _f(lo), _f(hi), _i(g), _f(pts)
+    dim = lo.shape[0]
+    out = np.empty(pts.shape[0], dtype=np.int64)
+    lib().or_grid_cells(dim, _p(lo, _f64), _p(hi, _f64), _p(g, _i32), pts.shape[0],
+                        _p(pts, _f64), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return out
+
+
+def p1_interpolate(conn, v0, M, u_nodal, pts, host):
+    conn, v0, M, u_nodal, pts, host = _i(conn), _f(v0), _f(M), _f(u_nodal), _f(pts), _i(host)
+    dim = v0.shape[1]
+    out = np.empty((pts.shape[0], dim))
+    lib().or_p1_interpolate(dim, _p(conn, _i32), _p(v0, _f64), _p(M, _f64),
+                            _p(u_nodal, _f64), pts.shape[0], _p(pts, _f64),
+                            _p(host, _i32), _p(out, _f64))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# whole mesh + track
+# ---------------------------------------------------------------------------
+
+class Mesh:
+    """The oracle's own view of a mesh: neighbours, inverse-affine form,
+    plain-SNS starts and the ASG seed grid (host of every cell centre)."""
+
+    def __init__(self, xyz, conn, grid=None, brute_limit=20000):
+        self.xyz = _f(xyz)
+        self.conn = _i(conn)
+        self.dim = self.xyz.shape[1]
+        self.n_v = self.xyz.shape[0]
+        self.n_e = self.conn.shape[0]
+        self.nbr = neighbors(self.dim, self.conn)
+        self.v0, self.M = inverse_affine(self.xyz, self.conn)
+        self.node_elem = node_elements(self.n_v, self.conn)
+        self.cap = step_cap(self.dim, self.n_e)
+        self.brute = self.n_e <= brute_limit
+        self.lo, self.hi = bbox(self.xyz)
+        if grid is None:
+            grid = default_grid(self.n_v, self.dim)
+        self.grid = _i(np.broadcast_to(np.asarray(grid), (self.dim,)))
+        self._seed = None
+
+    def locate(self, pts, eps=EPS):
+        if self.brute:
+            return locate_bruteforce(self.v0, self.M, pts, eps)
+        return locate_bucketed(self.xyz, self.conn, self.v0, self.M, pts, eps)
+
+    @property
+    def seed(self):
+        """seed[c] = host of the centre of ASG cell c (or -1)."""
+        if self._seed is None:
+            self._seed = self.locate(grid_centres(self.lo, self.hi, self.grid))
+        return self._seed
+
+    def cells(self, pts):
+        return grid_cells(self.lo, self.hi, self.grid, pts)
+
+    def centroids(self):
+        return self.xyz[self.conn].mean(axis=1)
+
+    def track(self, x, u, dt, start=None, mode="sns", dhat=None):
+        """Full path for every particle: departure point, start element,
+        Algorithm 1 walk, exact host and status.
+
+        mode 'sns': start = the given start (user ids) or the node's element;
+        'asg': start = seed grid cell of x_p itself; 'cnn': start = seed grid
+        cell of x + dhat * s (dhat in cell units). A seed of -1 falls back to
+        the plain start. Returns dict of host, path_len, status, start, xp."""
+        x, u = _f(x), _f(u)
+        n = x.shape[0]
+        xp = departure(x, u, dt)
+        if start is None:
+            if n != self.n_v:
+                raise ValueError("start needed unless the particles are the mesh nodes")
+            plain = self.node_elem.copy()
+        else:
+            plain = _i(start).copy()
+        if mode == "sns":
+            st = plain
+        elif mode == "asg":
+            c = self.cells(xp)
+            s = self.seed[c]
+            st = np.where(s >= 0, s, plain).astype(np.int32)
+        elif mode == "cnn":
+            s_cell = (self.hi - self.lo) / self.grid
+            y = x + (np.asarray(dhat, dtype=np.float32).astype(np.float64) * s_cell)
+            c = self.cells(y)
+            s = self.seed[c]
+            st = np.where(s >= 0, s, plain).astype(np.int32)
+        else:
+            raise ValueError(mode)
+        end, it, reason = walk(self.v0, self.M, self.nbr, xp, st, cap=self.cap)
+        host = self.locate(xp)
+        status = np.where(reason == CONTAINED, ST_FOUND,
+                          np.where(host < 0, ST_OUTSIDE, ST_FALLBACK)).astype(np.uint8)
+        finite = np.isfinite(xp).all(axis=1)
+        nostart = finite & (st < 0)
+        it = np.where(nostart, 0, it).astype(np.int32)
+        status[~finite] = ST_INVALID
+        host = np.where(finite, host, -1).astype(np.int32)
+        it[~finite] = 0
+        return dict(host=host, path_len=it, status=status, start=st, xp=xp,
+                    end=end, reason=reason)
+
+
+def default_grid(n_v, dim):
+    """Default ASG resolution per axis: round(n_v^(1/d)) - 1, at least 1."""
+    return max(1, int(round(n_v ** (1.0 / dim))) - 1)

@@ -1,0 +1,139 @@
+"""Seeded mesh generators (inputs only).
+
+2-D: an n x n lattice on the unit square, interior points jittered uniformly
+by +-j*h per coordinate (boundary points fixed), Delaunay-triangulated with
+scipy's Qhull. 3-D: an n^3 lattice on the unit cube, interior points jittered
+by +-j*h, each lattice cell split into six Kuhn tetrahedra along its main
+diagonal; a vertex whose jitter inverts one of its tetrahedra is redrawn.
+
+Connectivity rows keep the vertex order the generator produces; the method
+never reorders the vertices of an element, so local index i always names the
+same vertex on both sides.
+"""
+
+import functools
+
+import numpy as np
+
+
+def lattice_2d(n_side, jitter, seed):
+    """Jittered n_side x n_side lattice on [0,1]^2; returns (xyz[n_v,2], h)."""
+    h = 1.0 / (n_side - 1)
+    g = np.linspace(0.0, 1.0, n_side)
+    X, Y = np.meshgrid(g, g, indexing="xy")          # node id = iy*n + ix
+    p = np.stack([X.ravel(), Y.ravel()], axis=1)
+    rng = np.random.default_rng(seed)
+    dj = rng.uniform(-jitter * h, jitter * h, size=p.shape)
+    i = np.arange(n_side)
+    ix = np.tile(i, n_side)
+    iy = np.repeat(i, n_side)
+    edge = (ix == 0) | (ix == n_side - 1) | (iy == 0) | (iy == n_side - 1)
+    dj[edge] = 0.0
+    return np.ascontiguousarray(p + dj), h
+
+
+def delaunay_2d(xyz):
+    """Delaunay triangulation of a 2-D point set; conn[n_e,3] int32."""
+    from scipy.spatial import Delaunay
+    tri = Delaunay(xyz)
+    if len(tri.coplanar):
+        raise RuntimeError("Qhull dropped %d coplanar points" % len(tri.coplanar))
+    return np.ascontiguousarray(tri.simplices.astype(np.int32))
+
+
+@functools.lru_cache(maxsize=8)
+def _mesh_2d_cached(n_side, jitter, seed):
+    xyz, h = lattice_2d(n_side, jitter, seed)
+    conn = delaunay_2d(xyz)
+    xyz.setflags(write=False)
+    conn.setflags(write=False)
+    return xyz, conn, h
+
+
+def mesh_2d(n_side, jitter=0.3, seed=1):
+    """(xyz, conn, h) of the jittered Delaunay square (read-only, cached)."""
+    return _mesh_2d_cached(int(n_side), float(jitter), int(seed))
+
+
+# Six Kuhn tetrahedra of the cell [0,1]^3: each is the path
+# 000 -> e_a -> e_a+e_b -> 111 for one permutation (a, b, c) of the axes.
+# Corner bit k of a corner index is its offset along axis k.
+def _kuhn_corners():
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        c0 = 0
+        c1 = c0 | (1 << perm[0])
+        c2 = c1 | (1 << perm[1])
+        c3 = 7
+        tets.append((c0, c1, c2, c3))
+    return np.array(tets, dtype=np.int64)
+
+
+def _signed_volumes(xyz, conn):
+    a = xyz[conn[:, 1]] - xyz[conn[:, 0]]
+    b = xyz[conn[:, 2]] - xyz[conn[:, 0]]
+    c = xyz[conn[:, 3]] - xyz[conn[:, 0]]
+    return np.einsum("ij,ij->i", a, np.cross(b, c))
+
+
+def kuhn_3d(n_side, jitter, seed, max_redraw=64):
+    """Jittered unit cube split into 6 Kuhn tets per cell.
+
+    Returns (xyz[n_v,3], conn[n_e,4] int32, h); node id = (iz*n + iy)*n + ix.
+    Every tetrahedron keeps the orientation it has on the unjittered lattice;
+    vertices of a tetrahedron whose orientation flips (or collapses) are
+    redrawn from the same generator.
+    """
+    n = n_side
+    h = 1.0 / (n - 1)
+    g = np.linspace(0.0, 1.0, n)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    base = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    i = np.arange(n)
+    ix = np.tile(i, n * n)
+    iy = np.tile(np.repeat(i, n), n)
+    iz = np.repeat(i, n * n)
+    interior = (ix > 0) & (ix < n - 1) & (iy > 0) & (iy < n - 1) & (iz > 0) & (iz < n - 1)
+
+    # connectivity
+    c = np.arange(n - 1)
+    cx = np.tile(c, (n - 1) ** 2)
+    cy = np.tile(np.repeat(c, n - 1), n - 1)
+    cz = np.repeat(c, (n - 1) ** 2)
+    corner = np.empty((cx.size, 8), dtype=np.int64)
+    for k in range(8):
+        dx, dy, dz = k & 1, (k >> 1) & 1, (k >> 2) & 1
+        corner[:, k] = ((cz + dz) * n + (cy + dy)) * n + (cx + dx)
+    kc = _kuhn_corners()
+    conn = corner[:, kc].reshape(-1, 4)
+    ref_sign = np.sign(_signed_volumes(base, conn))
+
+    rng = np.random.default_rng(seed)
+    dj = rng.uniform(-jitter * h, jitter * h, size=base.shape)
+    dj[~interior] = 0.0
+    xyz = base + dj
+    for _ in range(max_redraw):
+        vol = _signed_volumes(xyz, conn)
+        bad = np.sign(vol) != ref_sign
+        if not bad.any():
+            break
+        verts = np.unique(conn[bad].ravel())
+        verts = verts[interior[verts]]
+        dj = rng.uniform(-jitter * h, jitter * h, size=(verts.size, 3))
+        xyz[verts] = base[verts] + dj
+    else:
+        raise RuntimeError("could not draw a valid jittered Kuhn mesh")
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(conn.astype(np.int32)), h
+
+
+@functools.lru_cache(maxsize=4)
+def _mesh_3d_cached(n_side, jitter, seed):
+    xyz, conn, h = kuhn_3d(n_side, jitter, seed)
+    xyz.setflags(write=False)
+    conn.setflags(write=False)
+    return xyz, conn, h
+
+
+def mesh_3d(n_side, jitter=0.1, seed=3):
+    """(xyz, conn, h) of the jittered Kuhn cube (read-only, cached)."""
+    return _mesh_3d_cached(int(n_side), float(jitter), int(seed))
