@@ -1,0 +1,188 @@
+/*
+ * cnnsns.h -- C ABI of the GB300 particle-location library for the CNN-SNS
+ * method (Luo et al., "A CNN-based particle tracking method for large-scale
+ * fluid simulations with Lagrangian-Eulerian approaches").
+ *
+ * The library finds, for every Lagrangian particle, the host element of its
+ * departure point x_p = x - (u * dt) (Sec. 2.1, Eq. 3-4) in an unstructured
+ * triangle (dim 2) or tetrahedron (dim 3) mesh by the successive neighbour
+ * search of Algorithm 1 (Sec. 2.2), started from the particle's own element
+ * (plain SNS), from the ASG cell of x_p, or from a CNN-predicted location
+ * (CNN-SNS, Algorithm 2, Sec. 2.3).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: CS_OK (0) or a negative cs_status; cs_last_error() then
+ *    holds a message. On error nothing has been written to any output.
+ *  - Per-particle outcomes go to status_out, never to the return value.
+ *  - Element ids across the ABI are the caller's ("user") ids: the row index
+ *    of the element in the connectivity passed to cs_mesh_upload.
+ *  - Local index i names vertex i of an element; face i lies opposite it.
+ *  - Arrays are row-major and densely packed: xyz[n_v][dim], conn[n_e][dim+1],
+ *    x[n][dim], u[n][dim].
+ *  - The caller owns every array it passes; the library owns its device
+ *    copies of meshes (until cs_mesh_release / cs_destroy).
+ *  - One context serves one thread at a time; calls on a context must not
+ *    overlap (it owns one scratch arena).
+ *
+ * Result definition (Sec. 2.2 containment test, with tolerance CS_EPS): the
+ * host of x_p is the LOWEST user id l with lambda_i^l(x_p) >= -CS_EPS for all
+ * i, or -1 when no element contains x_p. Barycentric coordinates are FP64,
+ * computed from a per-element inverse-affine matrix with a fixed rounding
+ * order, so results are reproducible bit for bit.
+ */
+#ifndef CNNSNS_H
+#define CNNSNS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_ctx cs_ctx;
+typedef int32_t cs_status;
+
+/* return codes */
+#define CS_OK        0
+#define CS_EINVAL   (-1)   /* bad argument (null pointer, size, id, mode)    */
+#define CS_ENOMEM   (-2)   /* host or device allocation failed               */
+#define CS_ENOMESH  (-3)   /* mesh id not uploaded or already released       */
+#define CS_EBUSY    (-4)   /* resource in use                                */
+#define CS_ECUDA    (-5)   /* CUDA runtime error (message has the CUDA text) */
+#define CS_EMESH    (-6)   /* malformed mesh: index out of range, degenerate
+                              element (det == 0), face shared by > 2 elements */
+#define CS_ENOPRED  (-7)   /* CNN-SNS requested without a loaded predictor   */
+#define CS_EDEVICE  (-8)   /* device-side wait gave up (bounded spin)        */
+
+/* start rules of cs_track */
+#define CS_SNS        0    /* start = given start, else the node's element   */
+#define CS_CNN_SNS    1    /* start = seed of the ASG cell at x + CNN(d)     */
+#define CS_ASG_DIRECT 2    /* start = seed of the ASG cell of x_p (control)  */
+
+/* per-particle status */
+#define CS_FOUND              0  /* the walk ended inside the host           */
+#define CS_OUTSIDE            1  /* no element contains x_p; host = -1       */
+#define CS_FOUND_VIA_FALLBACK 2  /* walk left the mesh or hit the step cap;
+                                    the exact search found the host          */
+#define CS_INVALID            3  /* x_p not finite; host = -1, path_len = 0  */
+
+#define CS_EPS 1e-12
+
+typedef struct cs_mesh_info {
+    int32_t dim;
+    int64_t n_vertices;
+    int64_t n_elements;
+    int32_t asg_grid[3];        /* ASG cells per axis (seed grid, CNN grid)  */
+    int32_t bucket_grid[3];     /* cells per axis of the exact-search index  */
+    int64_t bucket_items;       /* total entries of the exact-search index   */
+    double  lo[3], hi[3];       /* bounding box of the vertices              */
+    double  tau;                /* canonicalisation threshold (see cs_track) */
+    int32_t step_cap;           /* walk stops after this many evaluations    */
+    int32_t record_bytes;       /* bytes of one element record (64 or 128)   */
+    size_t  device_bytes;       /* device memory held by this mesh           */
+} cs_mesh_info;
+
+/* Create a context on CUDA device `cuda_device`. */
+cs_status cs_create(cs_ctx **out, int cuda_device);
+
+/* Release every mesh, predictor and scratch buffer of the context. */
+void cs_destroy(cs_ctx *ctx);
+
+/* Message of the last failed call on this context (owned by the context). */
+const char *cs_last_error(const cs_ctx *ctx);
+
+/*
+ * Upload a mesh {K_l} (Sec. 2.2). Host pointers. Builds on the host: the
+ * neighbour table m_i^l, the inverse-affine matrix of every element, a
+ * Hilbert order of the element centroids, the exact-search bucket index and
+ * the plain-SNS start of every vertex; then on the device the ASG seed grid
+ * (the host of every ASG cell centre).
+ *   asg_grid: cells per axis of the ASG grid over the vertex bounding box, or
+ *             NULL for round(n_v^(1/dim)) - 1 per axis.
+ * Errors: CS_EINVAL (dim not 2/3, sizes < 1, null pointer), CS_EMESH
+ * (vertex index out of range, degenerate element, non-manifold face),
+ * CS_ENOMEM, CS_ECUDA.
+ */
+cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_vertices, const double *xyz,
+                         int64_t n_elements, const int32_t *conn,
+                         const int32_t *asg_grid, int32_t *mesh_id_out);
+
+cs_status cs_mesh_release(cs_ctx *ctx, int32_t mesh_id);
+cs_status cs_mesh_query(cs_ctx *ctx, int32_t mesh_id, cs_mesh_info *info_out);
+
+/* Plain-SNS start K_m of every vertex (Sec. 2.1, Eq. 4: an element owning the
+ * node; the lowest user id among them). Host output [n_vertices]. */
+cs_status cs_node_start_elements(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
+
+/* ASG seed grid: user id of the host of every cell centre, or -1 (host
+ * output, [prod asg_grid], x fastest). */
+cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
+
+/*
+ * Locate n particles (Algorithm 1 / Algorithm 2). DEVICE pointers; the work
+ * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * the call returns without synchronising.
+ *   x[n][dim], u[n][dim]: particle position and velocity; x_p = x - (u*dt).
+ *   start[n]: user ids of the plain-SNS start, or NULL when the particles are
+ *             the mesh vertices in order (n == n_vertices): then start =
+ *             cs_node_start_elements(). A start of -1 skips the walk.
+ *   mode: CS_SNS, CS_ASG_DIRECT or CS_CNN_SNS (needs cs_predictor_* first).
+ *   host_out[n]  user id of the host of x_p, or -1.
+ *   path_len_out[n]  I_t of Algorithm 1 (elements evaluated, start included).
+ *   status_out[n]    CS_FOUND / CS_OUTSIDE / CS_FOUND_VIA_FALLBACK / CS_INVALID.
+ *   start_out[n]     (may be NULL) user id of the element the walk started in.
+ * The walk stops when every lambda >= -CS_EPS, steps across the face of the
+ * smallest lambda (equal minima: lowest local index), stops at a -1
+ * neighbour, and stops after step_cap evaluations. Particles whose walk
+ * left the mesh or hit the cap, and those whose final element has some
+ * lambda < tau (near a face, where a lower id may also contain x_p), go
+ * through an exact search of the bucket index; the result is the host
+ * defined at the top of this file.
+ * Errors: CS_EINVAL (n < 0, null pointer, start == NULL with n != n_v,
+ * bad mode), CS_ENOMESH, CS_ENOPRED, CS_ENOMEM, CS_ECUDA.
+ */
+cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                   const double *u, double dt, const int32_t *start, int mode,
+                   int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                   int32_t *start_out, void *stream);
+
+/* cs_track with HOST pointers: copies inputs to the device, runs, copies the
+ * results back and synchronises. Same arguments and errors. */
+cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                        const double *u, double dt, const int32_t *start, int mode,
+                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                        int32_t *start_out);
+
+/* Walk statistics of a finished cs_track (DEVICE pointers, synchronous):
+ * out[0] = sum of path_len, out[1] = max path_len, out[2..5] = particles with
+ * status 0..3. */
+cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len,
+                         const uint8_t *status, int64_t out[6], void *stream);
+
+/* Launch counter: kernels this context has launched since creation. */
+int64_t cs_kernel_launches(const cs_ctx *ctx);
+
+/* Per-stage device time, measured with CUDA events recorded on the stream
+ * each kernel is launched on (enabled by cs_profile_enable; off by default). */
+typedef struct cs_profile {
+    int64_t launches[8];   /* per stage: calls measured                      */
+    double  ms[8];         /* per stage: summed event time, milliseconds     */
+} cs_profile;
+#define CS_STAGE_WALK      0   /* departure + start + Algorithm 1 walk       */
+#define CS_STAGE_FALLBACK  1   /* exact search / canonicalisation            */
+#define CS_STAGE_RESAMPLE  2   /* nodal velocity -> ASG grid                 */
+#define CS_STAGE_CNN       3   /* CNN forward over the ASG grid              */
+#define CS_STAGE_TRAIN     4   /* one training step (forward+backward+Adam)  */
+
+/* Turn event timing on (1) or off (0). */
+cs_status cs_profile_enable(cs_ctx *ctx, int on);
+
+/* Synchronise the recorded events and add their times into *out (zeroed
+ * first); reset != 0 clears the record afterwards. */
+cs_status cs_profile_read(cs_ctx *ctx, cs_profile *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

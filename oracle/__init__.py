@@ -142,7 +142,8 @@ def locate_bucketed(xyz, conn, v0, M, pts, eps=EPS, g=None):
     xyz, conn, v0, M, pts = _f(xyz), _i(conn), _f(v0), _f(M), _f(pts)
     dim = xyz.shape[1]
     if g is None:
-        g = max(1, int(round((conn.shape[0] / 4.0) ** (1.0 / dim))))
+        per_cell = 4.0 if dim == 2 else 24.0
+        g = max(1, int(round((conn.shape[0] / per_cell) ** (1.0 / dim))))
     host = np.empty(pts.shape[0], dtype=np.int32)
     rc = lib().or_locate_bucketed(dim, xyz.shape[0], _p(xyz, _f64), conn.shape[0],
                                   _p(conn, _i32), _p(v0, _f64), _p(M, _f64), pts.shape[0],

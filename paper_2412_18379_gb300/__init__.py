@@ -1,0 +1,182 @@
+"""GB300 particle location for the CNN-SNS method (thin Python binding).
+
+Every step of the path runs in libcnnsns.so (CUDA kernels for sm_103a + host
+C++); this module only marshals arguments: numpy arrays for host inputs,
+torch CUDA tensors for device memory and streams.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (CS_SNS, CS_CNN_SNS, CS_ASG_DIRECT, CS_FOUND, CS_OUTSIDE,
+                    CS_FOUND_VIA_FALLBACK, CS_INVALID, CS_EPS, CsError)
+
+MODES = {"sns": CS_SNS, "cnn": CS_CNN_SNS, "cnn_sns": CS_CNN_SNS, "asg": CS_ASG_DIRECT,
+         "asg_direct": CS_ASG_DIRECT}
+
+__all__ = ["Context", "Mesh", "CsError", "CS_SNS", "CS_CNN_SNS", "CS_ASG_DIRECT",
+           "CS_FOUND", "CS_OUTSIDE", "CS_FOUND_VIA_FALLBACK", "CS_INVALID", "CS_EPS"]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    def __init__(self, ctx, mesh_id, dim, n_v, n_e):
+        self.ctx = ctx
+        self.id = mesh_id
+        self.dim = dim
+        self.n_vertices = n_v
+        self.n_elements = n_e
+
+    def info(self):
+        inf = _capi.MeshInfo()
+        self.ctx._check(self.ctx.lib.cs_mesh_query(self.ctx.h, self.id, ctypes.byref(inf)))
+        d = inf.dim
+        return dict(dim=d, n_vertices=inf.n_vertices, n_elements=inf.n_elements,
+                    asg_grid=list(inf.asg_grid[:d]), bucket_grid=list(inf.bucket_grid[:d]),
+                    bucket_items=inf.bucket_items, lo=list(inf.lo[:d]), hi=list(inf.hi[:d]),
+                    tau=inf.tau, step_cap=inf.step_cap, record_bytes=inf.record_bytes,
+                    device_bytes=inf.device_bytes)
+
+    def node_start_elements(self):
+        out = np.empty(self.n_vertices, dtype=np.int32)
+        self.ctx._check(self.ctx.lib.cs_node_start_elements(self.ctx.h, self.id, _ptr(out)))
+        return out
+
+    def seed_grid(self):
+        g = self.info()["asg_grid"]
+        out = np.empty(int(np.prod(g)), dtype=np.int32)
+        self.ctx._check(self.ctx.lib.cs_seed_grid(self.ctx.h, self.id, _ptr(out)))
+        return out
+
+    def release(self):
+        if self.id is not None:
+            self.ctx._check(self.ctx.lib.cs_mesh_release(self.ctx.h, self.id))
+            self.id = None
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device=0, lib_path=None):
+        self.lib = _capi.load(lib_path)
+        h = ctypes.c_void_p()
+        rc = self.lib.cs_create(ctypes.byref(h), int(device))
+        if rc != 0:
+            raise CsError(rc, "cs_create(device=%d) failed" % device)
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.cs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            msg = self.lib.cs_last_error(self.h)
+            raise CsError(rc, msg.decode() if msg else "")
+
+    @property
+    def launches(self):
+        return int(self.lib.cs_kernel_launches(self.h))
+
+    def profile(self, on=True):
+        self._check(self.lib.cs_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{stage: (launches, total ms)} from CUDA events on the launch stream."""
+        p = _capi.Profile()
+        self._check(self.lib.cs_profile_read(self.h, ctypes.byref(p), 1 if reset else 0))
+        return {name: (int(p.launches[i]), float(p.ms[i]))
+                for i, name in enumerate(_capi.STAGES)}
+
+    def upload_mesh(self, xyz, conn, asg_grid=None):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+        dim = xyz.shape[1]
+        if conn.shape[1] != dim + 1:
+            raise ValueError("conn must have dim+1 columns")
+        g = None
+        if asg_grid is not None:
+            g = np.ascontiguousarray(np.broadcast_to(np.asarray(asg_grid), (dim,)),
+                                     dtype=np.int32)
+        mid = ctypes.c_int32()
+        self._check(self.lib.cs_mesh_upload(self.h, dim, xyz.shape[0], _ptr(xyz),
+                                            conn.shape[0], _ptr(conn), _ptr(g),
+                                            ctypes.byref(mid)))
+        return Mesh(self, mid.value, dim, xyz.shape[0], conn.shape[0])
+
+    def track(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
+              stream=None):
+        """Device path: x, u are float64 CUDA tensors [n, dim]; returns (or
+        fills `out` with) device tensors host, path_len, status[, start]."""
+        import torch
+        n = x.shape[0]
+        dev = x.device
+        for t in (x, u):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("x and u must be contiguous float64 CUDA tensors")
+        if out is None:
+            out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
+                       path_len=torch.empty(n, dtype=torch.int32, device=dev),
+                       status=torch.empty(n, dtype=torch.uint8, device=dev))
+            if start_out:
+                out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(self.lib.cs_track(
+            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
+            _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start")),
+            _stream_ptr(st)))
+        return out
+
+    def track_host(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False):
+        """Host path: numpy (or pinned torch CPU) inputs; copies in, runs,
+        copies out and synchronises inside the library."""
+        n = x.shape[0]
+        if out is None:
+            out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
+                       status=np.empty(n, dtype=np.uint8))
+            if start_out:
+                out["start"] = np.empty(n, dtype=np.int32)
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            if start is not None:
+                start = np.ascontiguousarray(start, dtype=np.int32)
+        self._check(self.lib.cs_track_host(
+            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
+            _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start"))))
+        return out
+
+    def stats(self, path_len, status, stream=None):
+        """(sum, max, count FOUND, OUTSIDE, FALLBACK, INVALID) of device outputs."""
+        import torch
+        res = (ctypes.c_int64 * 6)()
+        st = stream if stream is not None else torch.cuda.current_stream(path_len.device)
+        self._check(self.lib.cs_track_stats(self.h, path_len.shape[0], _ptr(path_len),
+                                            _ptr(status), res, _stream_ptr(st)))
+        return dict(sum=res[0], max=res[1], found=res[2], outside=res[3], fallback=res[4],
+                    invalid=res[5])

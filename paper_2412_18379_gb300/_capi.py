@@ -1,0 +1,99 @@
+"""ctypes declarations of the C ABI in include/cnnsns.h (argument marshalling only).
+
+The shared library is built in-tree by paper_2412_18379_gb300.build. If it is
+missing the import fails loudly: there is no CPU fallback for any entry point.
+"""
+
+import ctypes
+import os
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+CS_OK = 0
+CS_SNS, CS_CNN_SNS, CS_ASG_DIRECT = 0, 1, 2
+CS_FOUND, CS_OUTSIDE, CS_FOUND_VIA_FALLBACK, CS_INVALID = 0, 1, 2, 3
+CS_EPS = 1e-12
+
+ERRORS = {
+    -1: "CS_EINVAL", -2: "CS_ENOMEM", -3: "CS_ENOMESH", -4: "CS_EBUSY",
+    -5: "CS_ECUDA", -6: "CS_EMESH", -7: "CS_ENOPRED", -8: "CS_EDEVICE",
+}
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [
+        ("dim", _i32),
+        ("n_vertices", _i64),
+        ("n_elements", _i64),
+        ("asg_grid", _i32 * 3),
+        ("bucket_grid", _i32 * 3),
+        ("bucket_items", _i64),
+        ("lo", _dbl * 3),
+        ("hi", _dbl * 3),
+        ("tau", _dbl),
+        ("step_cap", _i32),
+        ("record_bytes", _i32),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+# name -> (restype, argtypes); every symbol include/cnnsns.h declares
+SIGNATURES = {
+    "cs_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_int]),
+    "cs_destroy": (None, [_vp]),
+    "cs_last_error": (ctypes.c_char_p, [_vp]),
+    "cs_mesh_upload": (_i32, [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _vp,
+                              ctypes.POINTER(_i32)]),
+    "cs_mesh_release": (_i32, [_vp, _i32]),
+    "cs_mesh_query": (_i32, [_vp, _i32, ctypes.POINTER(MeshInfo)]),
+    "cs_node_start_elements": (_i32, [_vp, _i32, _vp]),
+    "cs_seed_grid": (_i32, [_vp, _i32, _vp]),
+    "cs_track": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp, _vp,
+                        _vp, _vp]),
+    "cs_track_host": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp,
+                             _vp, _vp]),
+    "cs_track_stats": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp]),
+    "cs_kernel_launches": (_i64, [_vp]),
+    "cs_profile_enable": (_i32, [_vp, ctypes.c_int]),
+    "cs_profile_read": (_i32, [_vp, _vp, ctypes.c_int]),
+}
+
+STAGES = ["walk", "fallback", "resample", "cnn", "train"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", _i64 * 8), ("ms", _dbl * 8)]
+
+_LIB = None
+
+
+def load(path=None):
+    """Load libcnnsns.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError("libcnnsns.so not built: run paper_2412_18379_gb300.build.build() "
+                          "(expected at %s)" % p)
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+class CsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code

@@ -1,0 +1,395 @@
+// C ABI of the particle-location library (declared in include/cnnsns.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace {
+
+cs_status fail(cs_ctx *ctx, cs_status code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+cs_status cuda_fail(cs_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, CS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CS_CUDA(ctx, call)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <class T>
+cs_status dev_copy(cs_ctx *ctx, cs::Mesh *m, const T *src, size_t count, T **dst) {
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(ctx, CS_ENOMEM, "cudaMalloc of mesh data failed");
+    m->allocs.push_back(p);
+    m->info.device_bytes += bytes;
+    if (count && src) {
+        e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy of mesh data");
+    } else if (count) {
+        e = cudaMemset(p, 0xff, count * sizeof(T));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemset of mesh data");
+    }
+    *dst = static_cast<T *>(p);
+    return CS_OK;
+}
+
+void free_mesh(cs::Mesh *m) {
+    for (void *p : m->allocs) cudaFree(p);
+    delete m;
+}
+
+cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
+    auto it = ctx->meshes.find(id);
+    return it == ctx->meshes.end() ? nullptr : it->second;
+}
+
+cs_status ensure_scratch(cs_ctx *ctx, int64_t n) {
+    cs::Scratch &s = ctx->scratch;
+    if (!s.counters) {
+        if (cudaMalloc(&s.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
+            cudaMalloc(&s.stats, 8 * sizeof(int64_t)) != cudaSuccess)
+            return fail(ctx, CS_ENOMEM, "cudaMalloc of scratch counters failed");
+    }
+    if (s.list_cap < n) {
+        if (s.list) cudaFree(s.list);
+        s.list = nullptr;
+        s.list_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, 1024);
+        if (cudaMalloc(&s.list, size_t(cap) * sizeof(int32_t)) != cudaSuccess)
+            return fail(ctx, CS_ENOMEM, "cudaMalloc of the exact-search list failed");
+        s.list_cap = cap;
+    }
+    return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_create(cs_ctx **out, int cuda_device) {
+    if (!out) return CS_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || cuda_device < 0 || cuda_device >= count)
+        return CS_EINVAL;
+    cs_ctx *ctx = new (std::nothrow) cs_ctx();
+    if (!ctx) return CS_ENOMEM;
+    ctx->device = cuda_device;
+    if (cudaSetDevice(cuda_device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) !=
+            cudaSuccess) {
+        delete ctx;
+        return CS_ECUDA;
+    }
+    *out = ctx;
+    return CS_OK;
+}
+
+void cs_destroy(cs_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (auto &kv : ctx->meshes) free_mesh(kv.second);
+    if (ctx->scratch.counters) cudaFree(ctx->scratch.counters);
+    if (ctx->scratch.stats) cudaFree(ctx->scratch.stats);
+    if (ctx->scratch.list) cudaFree(ctx->scratch.list);
+    if (ctx->scratch.stage) cudaFree(ctx->scratch.stage);
+    for (const auto &r : ctx->prof.pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char *cs_last_error(const cs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t cs_kernel_launches(const cs_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+cs_status cs_profile_enable(cs_ctx *ctx, int on) {
+    if (!ctx) return CS_EINVAL;
+    ctx->prof.on = on != 0;
+    return CS_OK;
+}
+
+cs_status cs_profile_read(cs_ctx *ctx, cs_profile *out, int reset) {
+    if (!ctx || !out) return CS_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    for (const auto &r : ctx->prof.pending) {
+        CS_CUDA(ctx, cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        CS_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+        if (r.stage >= 0 && r.stage < 8) {
+            out->launches[r.stage] += 1;
+            out->ms[r.stage] += ms;
+        }
+    }
+    if (reset) {
+        for (const auto &r : ctx->prof.pending) {
+            ctx->prof.pool.push_back(r.a);
+            ctx->prof.pool.push_back(r.b);
+        }
+        ctx->prof.pending.clear();
+    }
+    return CS_OK;
+}
+
+cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, int64_t n_e,
+                         const int32_t *conn, const int32_t *asg_grid, int32_t *mesh_id_out) {
+    if (!ctx) return CS_EINVAL;
+    if ((dim != 2 && dim != 3) || n_v < dim + 1 || n_e < 1 || !xyz || !conn || !mesh_id_out)
+        return fail(ctx, CS_EINVAL, "cs_mesh_upload: bad dim, size or null pointer");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs::HostMesh H;
+    std::string msg;
+    cs_status rc;
+    try {
+        rc = cs::build_host_mesh(dim, n_v, xyz, n_e, conn, asg_grid, H, msg);
+    } catch (const std::bad_alloc &) {
+        return fail(ctx, CS_ENOMEM, "host allocation failed while building the mesh");
+    }
+    if (rc != CS_OK) return fail(ctx, rc, "cs_mesh_upload: " + msg);
+
+    cs::Mesh *m = new (std::nothrow) cs::Mesh();
+    if (!m) return fail(ctx, CS_ENOMEM, "host allocation failed");
+    cs::DevMesh &d = m->d;
+    d.dim = dim;
+    d.n_v = n_v;
+    d.n_e = n_e;
+    const int nv = dim + 1;
+    void *rec = nullptr;
+    int32_t *iperm = nullptr, *node = nullptr, *seed = nullptr, *bstart = nullptr,
+            *bitems = nullptr, *cn = nullptr;
+    double *cent = nullptr;
+    std::vector<int32_t> node_int(static_cast<size_t>(n_v));
+    for (int64_t v = 0; v < n_v; ++v)
+        node_int[v] = H.node_elem[v] < 0 ? -1 : H.iperm[H.node_elem[v]];
+    if ((rc = dev_copy(ctx, m, H.rec.data(), H.rec.size(), reinterpret_cast<unsigned char **>(&rec))) ||
+        (rc = dev_copy(ctx, m, H.iperm.data(), H.iperm.size(), &iperm)) ||
+        (rc = dev_copy(ctx, m, node_int.data(), node_int.size(), &node)) ||
+        (rc = dev_copy(ctx, m, H.bstart.data(), H.bstart.size(), &bstart)) ||
+        (rc = dev_copy(ctx, m, H.bitems.data(), H.bitems.size(), &bitems)) ||
+        (rc = dev_copy(ctx, m, H.conn.data(), H.conn.size(), &cn)) ||
+        (rc = dev_copy(ctx, m, H.centroid.data(), H.centroid.size(), &cent))) {
+        free_mesh(m);
+        return rc;
+    }
+    int64_t n_asg = 1, n_b = 1;
+    for (int k = 0; k < dim; ++k) {
+        n_asg *= H.ga[k];
+        n_b *= H.gb[k];
+    }
+    if ((rc = dev_copy<int32_t>(ctx, m, nullptr, size_t(n_asg), &seed))) {
+        free_mesh(m);
+        return rc;
+    }
+    d.rec = rec;
+    d.conn = cn;
+    d.centroid = cent;
+    d.iperm = iperm;
+    d.node_elem = node;
+    d.seed = seed;
+    d.bstart = bstart;
+    d.bitems = bitems;
+    for (int k = 0; k < 3; ++k) {
+        d.lo[k] = k < dim ? H.lo[k] : 0;
+        d.hi[k] = k < dim ? H.hi[k] : 0;
+        d.ga[k] = k < dim ? H.ga[k] : 1;
+        d.sa[k] = k < dim ? H.sa[k] : 1;
+        d.gb[k] = k < dim ? H.gb[k] : 1;
+        d.sb[k] = k < dim ? H.sb[k] : 1;
+    }
+    d.margin = H.margin;
+    d.tau = H.tau;
+    d.cap = H.cap;
+    d.n_asg = n_asg;
+    d.n_bucket = n_b;
+
+    ctx->launches += cs::launch_seed_grid(d, seed, ctx->sm_count, nullptr);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        free_mesh(m);
+        return cuda_fail(ctx, e, "seed grid kernel");
+    }
+
+    cs_mesh_info &I = m->info;
+    I.dim = dim;
+    I.n_vertices = n_v;
+    I.n_elements = n_e;
+    for (int k = 0; k < 3; ++k) {
+        I.asg_grid[k] = d.ga[k];
+        I.bucket_grid[k] = d.gb[k];
+        I.lo[k] = d.lo[k];
+        I.hi[k] = d.hi[k];
+    }
+    I.bucket_items = int64_t(H.bitems.size());
+    I.tau = d.tau;
+    I.step_cap = d.cap;
+    I.record_bytes = dim == 2 ? int32_t(sizeof(cs::Rec2)) : int32_t(sizeof(cs::Rec3));
+    m->node_elem_user = std::move(H.node_elem);
+    (void)nv;
+    const int32_t id = ctx->next_mesh++;
+    ctx->meshes[id] = m;
+    *mesh_id_out = id;
+    return CS_OK;
+}
+
+cs_status cs_mesh_release(cs_ctx *ctx, int32_t mesh_id) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_mesh_release: unknown mesh id");
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    ctx->meshes.erase(mesh_id);
+    free_mesh(m);
+    return CS_OK;
+}
+
+cs_status cs_mesh_query(cs_ctx *ctx, int32_t mesh_id, cs_mesh_info *info) {
+    if (!ctx || !info) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_mesh_query: unknown mesh id");
+    *info = m->info;
+    return CS_OK;
+}
+
+cs_status cs_node_start_elements(cs_ctx *ctx, int32_t mesh_id, int32_t *out) {
+    if (!ctx || !out) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_node_start_elements: unknown mesh id");
+    std::memcpy(out, m->node_elem_user.data(), m->node_elem_user.size() * sizeof(int32_t));
+    return CS_OK;
+}
+
+cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out) {
+    if (!ctx || !out) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_seed_grid: unknown mesh id");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    std::vector<int32_t> seed(static_cast<size_t>(m->d.n_asg)), iperm(static_cast<size_t>(m->d.n_e)),
+        order(static_cast<size_t>(m->d.n_e));
+    CS_CUDA(ctx, cudaMemcpy(seed.data(), m->d.seed, seed.size() * 4, cudaMemcpyDeviceToHost));
+    CS_CUDA(ctx, cudaMemcpy(iperm.data(), m->d.iperm, iperm.size() * 4, cudaMemcpyDeviceToHost));
+    for (size_t u = 0; u < iperm.size(); ++u) order[iperm[u]] = int32_t(u);
+    for (size_t c = 0; c < seed.size(); ++c) out[c] = seed[c] < 0 ? -1 : order[seed[c]];
+    return CS_OK;
+}
+
+cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, const double *u,
+                   double dt, const int32_t *start, int mode, int32_t *host_out,
+                   int32_t *path_len_out, uint8_t *status_out, int32_t *start_out,
+                   void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track: unknown mesh id");
+    if (n < 0 || n >= (int64_t(1) << 31) - 1)
+        return fail(ctx, CS_EINVAL, "cs_track: n out of range");
+    if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS)
+        return fail(ctx, CS_EINVAL, "cs_track: unknown mode");
+    if (mode == CS_CNN_SNS)
+        return fail(ctx, CS_ENOPRED, "cs_track: no predictor loaded");
+    if (n == 0) return CS_OK;
+    if (!x || !u || !host_out || !path_len_out || !status_out)
+        return fail(ctx, CS_EINVAL, "cs_track: null pointer");
+    if (!start && n != m->d.n_v)
+        return fail(ctx, CS_EINVAL, "cs_track: start == NULL needs n == n_vertices");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs_status rc = ensure_scratch(ctx, n);
+    if (rc) return rc;
+    cs::TrackArgs a{};
+    a.n = n;
+    a.x = x;
+    a.u = u;
+    a.dt = dt;
+    a.start_user = start;
+    a.mode = mode;
+    a.dhat = nullptr;
+    a.host = host_out;
+    a.path = path_len_out;
+    a.status = status_out;
+    a.start_out = start_out;
+    ctx->launches += cs::launch_track(m->d, a, ctx->scratch, ctx->sm_count,
+                                      static_cast<cudaStream_t>(stream), &ctx->prof);
+    CS_CUDA(ctx, cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                        const double *u, double dt, const int32_t *start, int mode,
+                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                        int32_t *start_out) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_host: unknown mesh id");
+    if (n < 0) return fail(ctx, CS_EINVAL, "cs_track_host: n < 0");
+    if (n == 0) return CS_OK;
+    if (!x || !u || !host_out || !path_len_out || !status_out)
+        return fail(ctx, CS_EINVAL, "cs_track_host: null pointer");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    const int dim = m->d.dim;
+    const size_t in_b = size_t(n) * dim * sizeof(double);
+    const size_t total = 2 * in_b + size_t(n) * (4 + 4 + 4 + 4 + 1) + 256;
+    cs::Scratch &S = ctx->scratch;
+    if (S.stage_cap < total) {
+        if (S.stage) cudaFree(S.stage);
+        S.stage = nullptr;
+        S.stage_cap = 0;
+        if (cudaMalloc(&S.stage, total) != cudaSuccess)
+            return fail(ctx, CS_ENOMEM, "cs_track_host: device staging allocation failed");
+        S.stage_cap = total;
+    }
+    char *buf = S.stage;
+    double *dx = reinterpret_cast<double *>(buf);
+    double *du = reinterpret_cast<double *>(buf + in_b);
+    int32_t *ds = reinterpret_cast<int32_t *>(buf + 2 * in_b);
+    int32_t *dh = ds + n, *dp = dh + n, *dso = dp + n;
+    uint8_t *dst = reinterpret_cast<uint8_t *>(dso + n);
+    cudaStream_t st = nullptr;
+    cs_status rc = CS_OK;
+    cudaError_t e = cudaMemcpyAsync(dx, x, in_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, in_b, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && start)
+        e = cudaMemcpyAsync(ds, start, size_t(n) * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host: copy in");
+    rc = cs_track(ctx, mesh_id, n, dx, du, dt, start ? ds : nullptr, mode, dh, dp, dst,
+                  start_out ? dso : nullptr, st);
+    if (rc == CS_OK) {
+        e = cudaMemcpyAsync(host_out, dh, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(path_len_out, dp, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(status_out, dst, size_t(n), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && start_out)
+            e = cudaMemcpyAsync(start_out, dso, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cs_track_host: copy out");
+    }
+    return rc;
+}
+
+cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len, const uint8_t *status,
+                         int64_t out[6], void *stream) {
+    if (!ctx || !out || n < 0 || (n > 0 && (!path_len || !status))) return CS_EINVAL;
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs_status rc = ensure_scratch(ctx, 0);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches += cs::launch_stats(n, path_len, status, ctx->scratch.stats, ctx->sm_count, st);
+    CS_CUDA(ctx, cudaMemcpyAsync(out, ctx->scratch.stats, 6 * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    CS_CUDA(ctx, cudaStreamSynchronize(st));
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// Internal types of the particle-location library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "cnnsns.h"
+
+namespace cs {
+
+// One element, packed so that a walk step touches exactly one 64-byte (2-D)
+// or one 128-byte (3-D) aligned line: origin vertex v0, inverse-affine matrix
+// M (row k gives lambda_{k+1} = M[k] . (x_p - v0)), neighbour across face i
+// (internal id, -1 on the boundary), and the caller's id of the element.
+struct alignas(64) Rec2 {
+    double v0[2];
+    double m[4];
+    int32_t nbr[3];
+    int32_t uid;
+};
+struct alignas(128) Rec3 {
+    double v0[3];
+    double m[9];
+    int32_t nbr[4];
+    int32_t uid;
+    int32_t pad[3];
+};
+static_assert(sizeof(Rec2) == 64, "Rec2 must be one 64-byte line");
+static_assert(sizeof(Rec3) == 128, "Rec3 must be one 128-byte line");
+
+// Everything a kernel needs to know about a resident mesh (passed by value).
+struct DevMesh {
+    int32_t dim;
+    int64_t n_v, n_e;
+    const void *rec;          // Rec2 / Rec3 [n_e], Hilbert (internal) order
+    const int32_t *conn;      // [n_e][dim+1] vertex ids, internal order
+    const double *centroid;   // [n_e][dim], internal order
+    const int32_t *iperm;     // user id -> internal id
+    const int32_t *node_elem; // [n_v] internal id of the plain-SNS start
+    const int32_t *seed;      // [n_asg] internal id of the host of each cell centre, or -1
+    const int32_t *bstart;    // [n_bucket + 1] offsets into bitems
+    const int32_t *bitems;    // internal ids listed per bucket cell
+    double lo[3], hi[3];
+    int32_t ga[3];            // ASG cells per axis
+    double sa[3];             // ASG cell size (hi - lo) / ga
+    int32_t gb[3];            // bucket cells per axis
+    double sb[3];
+    double margin;            // bucket boxes are grown by this much
+    double tau;               // canonicalisation threshold
+    int32_t cap;              // step cap
+    int64_t n_asg, n_bucket;
+};
+
+struct Mesh {
+    DevMesh d{};
+    cs_mesh_info info{};
+    std::vector<void *> allocs;
+    std::vector<int32_t> node_elem_user;  // host copy, user ids
+};
+
+// Device scratch owned by a context: counters and the exact-search list.
+struct Scratch {
+    int32_t *counters = nullptr;   // [0] work cursor, [1] fallback count
+    int64_t *stats = nullptr;      // [8]
+    int32_t *list = nullptr;       // [cap] particle indices for exact search
+    int64_t list_cap = 0;
+    char *stage = nullptr;         // device staging of cs_track_host
+    size_t stage_cap = 0;
+};
+
+// Per-call arguments of the track kernels.
+struct TrackArgs {
+    int64_t n;
+    const double *x;
+    const double *u;
+    double dt;
+    const int32_t *start_user;   // may be null: node_elem[p]
+    int32_t mode;
+    const float *dhat;           // CNN-SNS: [n_asg][dim] displacement in ASG cell units
+    int32_t *host;
+    int32_t *path;
+    uint8_t *status;
+    int32_t *start_out;          // may be null
+};
+
+// host-side preprocessing (mesh_build.cpp); returns CS_OK or an error code and
+// fills `msg`.
+struct HostMesh {
+    int dim = 0;
+    int64_t n_v = 0, n_e = 0;
+    std::vector<int32_t> order;      // internal -> user
+    std::vector<int32_t> iperm;      // user -> internal
+    std::vector<unsigned char> rec;  // records, internal order
+    std::vector<int32_t> conn;       // internal order
+    std::vector<double> centroid;    // internal order
+    std::vector<int32_t> node_elem;  // user ids
+    std::vector<int32_t> bstart, bitems;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int32_t ga[3] = {1, 1, 1}, gb[3] = {1, 1, 1};
+    double sa[3] = {1, 1, 1}, sb[3] = {1, 1, 1};
+    double margin = 0, tau = 0;
+    int32_t cap = 0;
+};
+cs_status build_host_mesh(int dim, int64_t n_v, const double *xyz, int64_t n_e,
+                          const int32_t *conn, const int32_t *asg_grid, HostMesh &out,
+                          std::string &msg);
+
+// Event pairs recorded around kernels when profiling is on.
+struct Profiler {
+    bool on = false;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // record a start event for `stage` (returns index) and later its end
+    int begin(int stage, cudaStream_t st) {
+        if (!on) return -1;
+        Rec r{stage, get(), get()};
+        cudaEventRecord(r.a, st);
+        pending.push_back(r);
+        return int(pending.size()) - 1;
+    }
+    void end(int idx, cudaStream_t st) {
+        if (idx >= 0) cudaEventRecord(pending[idx].b, st);
+    }
+};
+
+// kernel launchers (walk.cu); each returns the number of kernels launched
+int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
+                 cudaStream_t st, Profiler *prof = nullptr);
+int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st);
+int launch_stats(int64_t n, const int32_t *path, const uint8_t *status, int64_t *out,
+                 int sm_count, cudaStream_t st);
+
+}  // namespace cs
+
+struct cs_ctx {
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    std::map<int32_t, cs::Mesh *> meshes;
+    int32_t next_mesh = 1;
+    cs::Scratch scratch;
+    cs::Profiler prof;
+    int64_t launches = 0;
+};

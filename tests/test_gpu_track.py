@@ -1,0 +1,207 @@
+"""Parity of the CUDA particle-location path against the CPU oracle.
+
+Every GPU call goes through the C ABI (libcnnsns.so via the ctypes binding).
+Bar: bit-exact host ids, path lengths, statuses and start elements.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2412_18379_gb300 as cs
+    from paper_2412_18379_gb300 import build
+    build.build()
+    c = cs.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(ctx, mesh, case, mode="sns", start=None, dt=None, u=None):
+    import torch
+    x = _dev(case.x)
+    uu = _dev(case.u if u is None else u)
+    st = None if start is None else _dev(start.astype(np.int32))
+    out = ctx.track(mesh, x, uu, case.dt if dt is None else dt, start=st, mode=mode,
+                    start_out=True)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _compare(got, want, name=""):
+    for k in ("host", "path_len", "status", "start"):
+        a, b = got[k], want[k]
+        bad = np.nonzero(a != b)[0]
+        assert bad.size == 0, "%s %s differs at %d particles, first %s: gpu %s oracle %s" % (
+            name, k, bad.size, bad[:5], a[bad[:5]], b[bad[:5]])
+
+
+def _oracle_out(om, r):
+    # the oracle reports starts in user ids; -1 where no walk ran
+    start = np.where(r["path_len"] > 0, r["start"], -1)
+    return dict(host=r["host"], path_len=r["path_len"], status=r["status"], start=start)
+
+
+CASES = [
+    ("rotation2d", {}),
+    ("tg2d", {"n_side": 201, "cfl": 1}),
+    ("tg2d", {"n_side": 201, "cfl": 16}),
+    ("abc3d", {"n_side": 21, "cfl": 4}),
+    ("abc3d", {"n_side": 21, "cfl": 20}),
+]
+
+
+@pytest.mark.parametrize("name,kw", CASES)
+@pytest.mark.parametrize("mode", ["sns", "asg"])
+def test_track_parity(ctx, name, kw, mode):
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    got = _run(ctx, mesh, c, mode=mode)
+    want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode=mode))
+    _compare(got, want, "%s %s %s" % (name, kw, mode))
+    mesh.release()
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 101, "cfl": 8}),
+                                     ("abc3d", {"n_side": 13, "cfl": 8})])
+def test_random_starts(ctx, name, kw):
+    """Explicit user-id starts, including -1 (walk skipped)."""
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    rng = np.random.default_rng(21)
+    start = rng.integers(0, c.n_elements, size=c.n_particles).astype(np.int32)
+    start[::97] = -1
+    got = _run(ctx, mesh, c, start=start)
+    want = _oracle_out(om, om.track(c.x, c.u, c.dt, start=start))
+    _compare(got, want)
+
+
+def test_mesh_tables(ctx):
+    c = make_case("tg2d", n_side=51)
+    mesh = ctx.upload_mesh(c.xyz, c.conn, asg_grid=37)
+    om = oracle.Mesh(c.xyz, c.conn, grid=37)
+    assert (mesh.node_start_elements() == om.node_elem).all()
+    assert (mesh.seed_grid() == om.seed).all()
+    inf = mesh.info()
+    assert inf["asg_grid"] == [37, 37] and inf["record_bytes"] == 64
+    assert inf["step_cap"] == om.cap
+
+
+def test_edge_cases(ctx):
+    import torch
+    c = make_case("rotation2d")
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    # dt = 0: every particle is inside its start element
+    got = _run(ctx, mesh, c, dt=0.0)
+    assert (got["path_len"] == 1).all() and (got["status"] == 0).all()
+    assert (got["host"] == om.node_elem).all()
+    # non-finite velocities -> INVALID, the rest unaffected
+    u = c.u.copy()
+    u[::13, 0] = np.nan
+    u[5, 1] = np.inf
+    got = _run(ctx, mesh, c, u=u)
+    want = _oracle_out(om, om.track(c.x, u, c.dt))
+    _compare(got, want)
+    assert (got["status"][::13] == 3).all()
+    # large dt throws many particles out of the square
+    got = _run(ctx, mesh, c, dt=c.dt * 8)
+    want = _oracle_out(om, om.track(c.x, c.u, c.dt * 8))
+    _compare(got, want)
+    assert (got["status"] == 1).sum() > 100
+    # n = 0 is a no-op
+    e = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    s = torch.empty(0, dtype=torch.int32, device="cuda")
+    out = ctx.track(mesh, e, e, 0.1, start=s)
+    assert out["host"].numel() == 0
+
+
+def test_points_on_vertices_and_edges(ctx):
+    """Points exactly at vertices and on edges: the lowest id must win."""
+    c = make_case("tg2d", n_side=41)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    nbr = om.nbr
+    pts = [c.xyz]
+    mids = []
+    for l in range(0, c.n_elements, 2):
+        for f in range(3):
+            a, b = np.delete(c.conn[l], f)
+            mids.append(0.5 * (c.xyz[a] + c.xyz[b]))
+    pts = np.concatenate([c.xyz, np.array(mids)])
+    zeros = np.zeros_like(pts)
+    rng = np.random.default_rng(3)
+    start = rng.integers(0, c.n_elements, size=pts.shape[0]).astype(np.int32)
+    import torch
+    out = ctx.track(mesh, _dev(pts), _dev(zeros), 0.0, start=_dev(start), start_out=True)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    want = _oracle_out(om, om.track(pts, zeros, 0.0, start=start))
+    _compare(got, want)
+    del nbr
+
+
+def test_host_path_matches_device_path(ctx):
+    c = make_case("abc3d", n_side=11, cfl=10)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    dev = _run(ctx, mesh, c, mode="asg")
+    host = ctx.track_host(mesh, c.x, c.u, c.dt, mode="asg", start_out=True)
+    for k in ("host", "path_len", "status", "start"):
+        assert (dev[k] == host[k]).all()
+
+
+def test_stats_and_determinism(ctx):
+    import torch
+    c = make_case("tg2d", n_side=151, cfl=12)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    x, u = _dev(c.x), _dev(c.u)
+    a = ctx.track(mesh, x, u, c.dt)
+    b = ctx.track(mesh, x, u, c.dt)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k])
+    s = ctx.stats(a["path_len"], a["status"])
+    p = a["path_len"].cpu().numpy()
+    st = a["status"].cpu().numpy()
+    assert s["sum"] == p.sum() and s["max"] == p.max()
+    assert [s["found"], s["outside"], s["fallback"], s["invalid"]] == \
+        [int((st == k).sum()) for k in range(4)]
+
+
+def test_bad_meshes_rejected(ctx):
+    import paper_2412_18379_gb300 as cs
+    xyz = np.array([[0, 0], [1, 0], [1, 1], [0, 1.0], [2, 2.0]])
+    with pytest.raises(cs.CsError) as e:
+        ctx.upload_mesh(xyz, np.array([[0, 1, 2], [0, 2, 9]]))
+    assert e.value.code == -6
+    with pytest.raises(cs.CsError) as e:        # degenerate (collinear)
+        ctx.upload_mesh(xyz, np.array([[0, 2, 4], [0, 1, 2]]))
+    assert e.value.code == -6
+    with pytest.raises(cs.CsError) as e:        # an edge shared by three triangles
+        ctx.upload_mesh(xyz, np.array([[0, 2, 1], [0, 2, 3], [0, 2, 4]]))
+    assert e.value.code == -6
+
+
+def test_full_size_tg2d_parity(ctx):
+    """The 1001 x 1001 Taylor-Green workload at CFL 8, every particle."""
+    c = make_case("tg2d", cfl=8)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    for mode in ("sns", "asg"):
+        got = _run(ctx, mesh, c, mode=mode)
+        want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode=mode))
+        _compare(got, want, "full tg2d " + mode)
+    mesh.release()
