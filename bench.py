@@ -183,7 +183,12 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=200000)
     ap.add_argument("--cpu-sample", type=int, default=200000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="time the main mode only (no other modes, e2e or CPU leg); "
+                         "used for profiler captures")
     args = ap.parse_args()
+    if args.quick:
+        args.no_cpu_baseline = True
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -266,7 +271,7 @@ def main():
 
     # the other start rules, for the same workload
     others = {}
-    for mode in ("sns", "asg"):
+    for mode in (("sns", "asg") if not args.quick else (args.mode,)):
         if mode == args.mode:
             others[mode] = dict(particles_per_s=value / world, ms_per_step=ms_per_step,
                                 mean_path_len=mean_it, max_path_len=st["max"])
@@ -295,11 +300,11 @@ def main():
     hout = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
                 path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
                 status=torch.empty(n, dtype=torch.uint8).pin_memory())
-    for _ in range(3):
+    for _ in range(0 if args.quick else 3):
         ctx.track_host(mesh, xh, uh, case.dt, mode=args.mode, out=hout)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, args.steps // 2) if not args.quick else 1
     for _ in range(e2e_steps):
         ctx.track_host(mesh, xh, uh, case.dt, mode=args.mode, out=hout)
     e2e_s = (time.perf_counter() - t0) / e2e_steps

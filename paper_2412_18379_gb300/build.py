@@ -36,13 +36,14 @@ def _cuda_inc():
 # per-file nvcc flags: the walk keeps every FP64 rounding explicit
 CU_FLAGS = {
     "walk.cu": ["--fmad=false"],
+    "search.cu": ["--fmad=false"],
 }
 
 
 def _sources():
     cu = sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
     cpp = sorted(f for f in os.listdir(CSRC) if f.endswith(".cpp"))
-    hdr = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hdr = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hdr += [os.path.join(INC, f) for f in os.listdir(INC) if f.endswith(".h")]
     return cu, cpp, hdr
 

@@ -167,14 +167,15 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     d.n_v = n_v;
     d.n_e = n_e;
     const int nv = dim + 1;
-    void *rec = nullptr;
+    unsigned char *recw = nullptr, *recx = nullptr;
     int32_t *iperm = nullptr, *node = nullptr, *seed = nullptr, *bstart = nullptr,
             *bitems = nullptr, *cn = nullptr;
     double *cent = nullptr;
     std::vector<int32_t> node_int(static_cast<size_t>(n_v));
     for (int64_t v = 0; v < n_v; ++v)
         node_int[v] = H.node_elem[v] < 0 ? -1 : H.iperm[H.node_elem[v]];
-    if ((rc = dev_copy(ctx, m, H.rec.data(), H.rec.size(), reinterpret_cast<unsigned char **>(&rec))) ||
+    if ((rc = dev_copy(ctx, m, H.recw.data(), H.recw.size(), &recw)) ||
+        (rc = dev_copy(ctx, m, H.recx.data(), H.recx.size(), &recx)) ||
         (rc = dev_copy(ctx, m, H.iperm.data(), H.iperm.size(), &iperm)) ||
         (rc = dev_copy(ctx, m, node_int.data(), node_int.size(), &node)) ||
         (rc = dev_copy(ctx, m, H.bstart.data(), H.bstart.size(), &bstart)) ||
@@ -193,7 +194,8 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         free_mesh(m);
         return rc;
     }
-    d.rec = rec;
+    d.recw = recw;
+    d.recx = recx;
     d.conn = cn;
     d.centroid = cent;
     d.iperm = iperm;
@@ -208,6 +210,9 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         d.sa[k] = k < dim ? H.sa[k] : 1;
         d.gb[k] = k < dim ? H.gb[k] : 1;
         d.sb[k] = k < dim ? H.sb[k] : 1;
+        d.lo_h[k] = static_cast<float>(d.lo[k]);
+        d.lo_l[k] = static_cast<float>(d.lo[k] - static_cast<double>(d.lo_h[k]));
+        d.inv_sa[k] = static_cast<float>(1.0 / d.sa[k]);
     }
     d.margin = H.margin;
     d.tau = H.tau;
@@ -236,7 +241,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     I.bucket_items = int64_t(H.bitems.size());
     I.tau = d.tau;
     I.step_cap = d.cap;
-    I.record_bytes = dim == 2 ? int32_t(sizeof(cs::Rec2)) : int32_t(sizeof(cs::Rec3));
+    I.record_bytes = dim == 2 ? int32_t(sizeof(cs::WalkRec2)) : int32_t(sizeof(cs::WalkRec3));
     m->node_elem_user = std::move(H.node_elem);
     (void)nv;
     const int32_t id = ctx->next_mesh++;

@@ -12,31 +12,48 @@
 
 namespace cs {
 
-// One element, packed so that a walk step touches exactly one 64-byte (2-D)
-// or one 128-byte (3-D) aligned line: origin vertex v0, inverse-affine matrix
-// M (row k gives lambda_{k+1} = M[k] . (x_p - v0)), neighbour across face i
-// (internal id, -1 on the boundary), and the caller's id of the element.
-struct alignas(64) Rec2 {
-    double v0[2];
-    double m[4];
+// Every element has two records.
+//
+// The walk record (read at every walk step) carries what the FP32 filter
+// needs: the origin vertex v0 split into float hi + lo parts, the inverse-
+// affine matrix M rounded to float, the neighbour across face i (internal id,
+// -1 on the boundary) and the caller's id of the element. 48 bytes (2-D, two
+// 32-byte sectors) / 80 bytes (3-D, three sectors).
+//
+// The exact record holds v0 and M in FP64 (row k of M gives
+// lambda_{k+1} = M[k] . (x_p - v0)); it is read only when the FP32 filter
+// cannot certify a decision, and by the exact search.
+struct alignas(16) WalkRec2 {
+    float vh[2], vl[2];
+    float m[4];
     int32_t nbr[3];
     int32_t uid;
 };
-struct alignas(128) Rec3 {
+struct alignas(16) WalkRec3 {
+    float vh[3], vl[3];
+    float m[9];
+    int32_t uid;
+    int32_t nbr[4];
+};
+struct alignas(16) ExactRec2 {
+    double v0[2];
+    double m[4];
+};
+struct alignas(16) ExactRec3 {
     double v0[3];
     double m[9];
-    int32_t nbr[4];
-    int32_t uid;
-    int32_t pad[3];
 };
-static_assert(sizeof(Rec2) == 64, "Rec2 must be one 64-byte line");
-static_assert(sizeof(Rec3) == 128, "Rec3 must be one 128-byte line");
+static_assert(sizeof(WalkRec2) == 48, "WalkRec2 is 48 bytes");
+static_assert(sizeof(WalkRec3) == 80, "WalkRec3 is 80 bytes");
+static_assert(sizeof(ExactRec2) == 48, "ExactRec2 is 48 bytes");
+static_assert(sizeof(ExactRec3) == 96, "ExactRec3 is 96 bytes");
 
 // Everything a kernel needs to know about a resident mesh (passed by value).
 struct DevMesh {
     int32_t dim;
     int64_t n_v, n_e;
-    const void *rec;          // Rec2 / Rec3 [n_e], Hilbert (internal) order
+    const void *recw;         // WalkRec2 / WalkRec3 [n_e], Hilbert (internal) order
+    const void *recx;         // ExactRec2 / ExactRec3 [n_e], same order
     const int32_t *conn;      // [n_e][dim+1] vertex ids, internal order
     const double *centroid;   // [n_e][dim], internal order
     const int32_t *iperm;     // user id -> internal id
@@ -49,6 +66,8 @@ struct DevMesh {
     double sa[3];             // ASG cell size (hi - lo) / ga
     int32_t gb[3];            // bucket cells per axis
     double sb[3];
+    float lo_h[3], lo_l[3];   // lo split into float hi + lo (FP32 cell filter)
+    float inv_sa[3];          // 1 / sa rounded to float
     double margin;            // bucket boxes are grown by this much
     double tau;               // canonicalisation threshold
     int32_t cap;              // step cap
@@ -94,7 +113,8 @@ struct HostMesh {
     int64_t n_v = 0, n_e = 0;
     std::vector<int32_t> order;      // internal -> user
     std::vector<int32_t> iperm;      // user -> internal
-    std::vector<unsigned char> rec;  // records, internal order
+    std::vector<unsigned char> recw; // walk records, internal order
+    std::vector<unsigned char> recx; // exact records, internal order
     std::vector<int32_t> conn;       // internal order
     std::vector<double> centroid;    // internal order
     std::vector<int32_t> node_elem;  // user ids
@@ -141,6 +161,8 @@ struct Profiler {
 // kernel launchers (walk.cu); each returns the number of kernels launched
 int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
                  cudaStream_t st, Profiler *prof = nullptr);
+int launch_fallback(const DevMesh &m, const TrackArgs &a, const int32_t *count,
+                    const int32_t *list, int sm_count, cudaStream_t st, Profiler *prof);
 int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st);
 int launch_stats(int64_t n, const int32_t *path, const uint8_t *status, int64_t *out,
                  int sm_count, cudaStream_t st);

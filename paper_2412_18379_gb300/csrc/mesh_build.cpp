@@ -296,32 +296,48 @@ cs_status build_host_mesh(int dim, int64_t n_v, const double *xyz, int64_t n_e,
     keys.shrink_to_fit();
 
     // ---- records, connectivity and centroids in internal order ----
-    const size_t rb = dim == 2 ? sizeof(Rec2) : sizeof(Rec3);
-    H.rec.assign(size_t(n_e) * rb, 0);
+    // walk record: v0 as float hi + lo (hi = v0 rounded to float, lo = the
+    // remainder v0 - hi rounded to float), M rounded to float
+    const size_t wb = dim == 2 ? sizeof(WalkRec2) : sizeof(WalkRec3);
+    const size_t xb = dim == 2 ? sizeof(ExactRec2) : sizeof(ExactRec3);
+    H.recw.assign(size_t(n_e) * wb, 0);
+    H.recx.assign(size_t(n_e) * xb, 0);
     H.conn.resize(size_t(n_e) * nv);
     H.centroid.resize(size_t(n_e) * dim);
+    auto split = [](double v, float &hi, float &lo) {
+        hi = static_cast<float>(v);
+        lo = static_cast<float>(v - static_cast<double>(hi));
+    };
     for (int64_t i = 0; i < n_e; ++i) {
         const int64_t l = H.order[i];
         if (dim == 2) {
-            Rec2 r{};
-            std::memcpy(r.v0, &v0[l * 2], sizeof(r.v0));
-            std::memcpy(r.m, &M[l * 4], sizeof(r.m));
+            WalkRec2 w{};
+            ExactRec2 x{};
+            std::memcpy(x.v0, &v0[l * 2], sizeof(x.v0));
+            std::memcpy(x.m, &M[l * 4], sizeof(x.m));
+            for (int k = 0; k < 2; ++k) split(v0[l * 2 + k], w.vh[k], w.vl[k]);
+            for (int k = 0; k < 4; ++k) w.m[k] = static_cast<float>(M[l * 4 + k]);
             for (int f = 0; f < 3; ++f) {
                 const int32_t n = nbr_user[l * 3 + f];
-                r.nbr[f] = n < 0 ? -1 : H.iperm[n];
+                w.nbr[f] = n < 0 ? -1 : H.iperm[n];
             }
-            r.uid = int32_t(l);
-            std::memcpy(&H.rec[size_t(i) * rb], &r, rb);
+            w.uid = int32_t(l);
+            std::memcpy(&H.recw[size_t(i) * wb], &w, wb);
+            std::memcpy(&H.recx[size_t(i) * xb], &x, xb);
         } else {
-            Rec3 r{};
-            std::memcpy(r.v0, &v0[l * 3], sizeof(r.v0));
-            std::memcpy(r.m, &M[l * 9], sizeof(r.m));
+            WalkRec3 w{};
+            ExactRec3 x{};
+            std::memcpy(x.v0, &v0[l * 3], sizeof(x.v0));
+            std::memcpy(x.m, &M[l * 9], sizeof(x.m));
+            for (int k = 0; k < 3; ++k) split(v0[l * 3 + k], w.vh[k], w.vl[k]);
+            for (int k = 0; k < 9; ++k) w.m[k] = static_cast<float>(M[l * 9 + k]);
             for (int f = 0; f < 4; ++f) {
                 const int32_t n = nbr_user[l * 4 + f];
-                r.nbr[f] = n < 0 ? -1 : H.iperm[n];
+                w.nbr[f] = n < 0 ? -1 : H.iperm[n];
             }
-            r.uid = int32_t(l);
-            std::memcpy(&H.rec[size_t(i) * rb], &r, rb);
+            w.uid = int32_t(l);
+            std::memcpy(&H.recw[size_t(i) * wb], &w, wb);
+            std::memcpy(&H.recx[size_t(i) * xb], &x, xb);
         }
         for (int k = 0; k < nv; ++k) H.conn[i * nv + k] = conn_user[l * nv + k];
         for (int k = 0; k < dim; ++k) H.centroid[i * dim + k] = cent[l * dim + k];

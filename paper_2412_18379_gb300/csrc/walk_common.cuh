@@ -1,0 +1,226 @@
+// Device helpers shared by the walk and the exact search: record loads, the
+// FP64 barycentric arithmetic (the arbiter), the certified FP32 filter, ASG
+// grid cells and the exact-search list.
+//
+// Exact arithmetic. Every decision of the walk is that of FP64 barycentric
+// coordinates with a pinned rounding order (no fused multiply-add):
+//   x_p       = x - (u * dt)
+//   delta_k   = x_p,k - v0_k
+//   lambda_k  = sum_j M[k-1][j] * delta_j   (k = 1..d, left to right)
+//   lambda_0  = ((1 - lambda_1) - lambda_2) - lambda_3
+//   cell_k    = floor((x_k - lo_k) / s_k), clamped to [0, g_k - 1]
+//
+// FP32 filter. GB300 executes FP64 at 1/64 of the FP32 rate, so each step
+// first evaluates the coordinates in FP32 (x_p and v0 split into float
+// hi + lo parts, M rounded to float) together with a bound T_i on
+// |lambda_i(FP64) - lambda_i(FP32)|, twice the worst-case rounding error of
+// both evaluations. A decision is taken in FP32 only when the bound makes it
+// certain; any other step is recomputed with the FP64 formula above, so every
+// decision equals the FP64 one.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace cs {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint8_t kPending = 0xff;  // status: the exact search decides
+
+// FP32 unit roundoff u = 2^-24 and the filter's constants
+constexpr float kU = 5.9604644775390625e-08f;
+constexpr float k4U = 4.0f * kU;
+constexpr float k8U = 8.0f * kU;
+constexpr float k32UU = 32.0f * kU * kU;
+constexpr float kTiny = 1e-36f;              // covers subnormal rounding
+constexpr float kNegEpsIn = -0.99e-12f;      // certain: lambda >= -eps
+constexpr float kNegEpsOut = -1.01e-12f;     // certain: lambda <  -eps
+
+template <int D> struct Recs;
+template <> struct Recs<2> { using W = WalkRec2; using X = ExactRec2; };
+template <> struct Recs<3> { using W = WalkRec3; using X = ExactRec3; };
+
+// walk record fields in registers
+template <int D> struct WalkE {
+    float vh[D], vl[D], m[D * D];
+    int32_t nbr[D + 1];
+    int32_t uid;
+};
+
+__device__ __forceinline__ void load_walk(const WalkRec2 *__restrict__ r, int32_t e,
+                                          WalkE<2> &o) {
+    const float4 *p = reinterpret_cast<const float4 *>(r + e);
+    const float4 a = __ldg(p + 0), b = __ldg(p + 1);
+    const int4 n = __ldg(reinterpret_cast<const int4 *>(p + 2));
+    o.vh[0] = a.x; o.vh[1] = a.y; o.vl[0] = a.z; o.vl[1] = a.w;
+    o.m[0] = b.x; o.m[1] = b.y; o.m[2] = b.z; o.m[3] = b.w;
+    o.nbr[0] = n.x; o.nbr[1] = n.y; o.nbr[2] = n.z; o.uid = n.w;
+}
+__device__ __forceinline__ void load_walk(const WalkRec3 *__restrict__ r, int32_t e,
+                                          WalkE<3> &o) {
+    const float4 *p = reinterpret_cast<const float4 *>(r + e);
+    const float4 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+    const int4 n = __ldg(reinterpret_cast<const int4 *>(p + 4));
+    o.vh[0] = a.x; o.vh[1] = a.y; o.vh[2] = a.z; o.vl[0] = a.w;
+    o.vl[1] = b.x; o.vl[2] = b.y; o.m[0] = b.z; o.m[1] = b.w;
+    o.m[2] = c.x; o.m[3] = c.y; o.m[4] = c.z; o.m[5] = c.w;
+    o.m[6] = d.x; o.m[7] = d.y; o.m[8] = d.z; o.uid = __float_as_int(d.w);
+    o.nbr[0] = n.x; o.nbr[1] = n.y; o.nbr[2] = n.z; o.nbr[3] = n.w;
+}
+
+// FP64 coordinates from the exact record (the arbiter).
+__device__ __forceinline__ void bary64(const ExactRec2 *__restrict__ r, int32_t e,
+                                       const double *x, double *lam) {
+    const double2 *p = reinterpret_cast<const double2 *>(r + e);
+    const double2 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2);
+    const double dx = __dsub_rn(x[0], a.x), dy = __dsub_rn(x[1], a.y);
+    const double l1 = __dadd_rn(__dmul_rn(b.x, dx), __dmul_rn(b.y, dy));
+    const double l2 = __dadd_rn(__dmul_rn(c.x, dx), __dmul_rn(c.y, dy));
+    lam[0] = __dsub_rn(__dsub_rn(1.0, l1), l2);
+    lam[1] = l1;
+    lam[2] = l2;
+}
+__device__ __forceinline__ void bary64(const ExactRec3 *__restrict__ r, int32_t e,
+                                       const double *x, double *lam) {
+    const double2 *p = reinterpret_cast<const double2 *>(r + e);
+    const double2 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3),
+                  f = __ldg(p + 4), g = __ldg(p + 5);
+    // v0 = (a.x, a.y, b.x); M rows (b.y c.x c.y) (d.x d.y f.x) (f.y g.x g.y)
+    const double dx = __dsub_rn(x[0], a.x), dy = __dsub_rn(x[1], a.y),
+                 dz = __dsub_rn(x[2], b.x);
+    const double l1 = __dadd_rn(__dadd_rn(__dmul_rn(b.y, dx), __dmul_rn(c.x, dy)),
+                                __dmul_rn(c.y, dz));
+    const double l2 = __dadd_rn(__dadd_rn(__dmul_rn(d.x, dx), __dmul_rn(d.y, dy)),
+                                __dmul_rn(f.x, dz));
+    const double l3 = __dadd_rn(__dadd_rn(__dmul_rn(f.y, dx), __dmul_rn(g.x, dy)),
+                                __dmul_rn(g.y, dz));
+    lam[0] = __dsub_rn(__dsub_rn(__dsub_rn(1.0, l1), l2), l3);
+    lam[1] = l1;
+    lam[2] = l2;
+    lam[3] = l3;
+}
+
+// |(xh + xl) - (vh + vl) - df| bound for df = (xh - vh) + (xl - vl) in FP32,
+// given |x - xh - xl| <= 2^-44 |xh| and |v - vh - vl| <= 2^-48 |vh|.
+__device__ __forceinline__ float delta_bound(float df, float xh, float vh) {
+    return fmaf(k4U, fabsf(df), k32UU * (fabsf(xh) + fabsf(vh)));
+}
+
+// FP32 coordinates lf and their bounds T (see the file comment).
+template <int D>
+__device__ __forceinline__ void bary32(const WalkE<D> &e, const float *xh, const float *xl,
+                                       float *lf, float *T) {
+    float df[D], ed[D];
+    #pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const float dh = xh[k] - e.vh[k];
+        const float dl = xl[k] - e.vl[k];
+        df[k] = dh + dl;
+        ed[k] = delta_bound(df[k], xh[k], e.vh[k]);
+    }
+    float sumT = 0.f, suml = 0.f;
+    float l0 = 1.0f;
+    #pragma unroll
+    for (int r = 0; r < D; ++r) {
+        float acc = e.m[r * D] * df[0];
+        float a = fabsf(e.m[r * D]) * fmaf(k4U, fabsf(df[0]), ed[0]);
+        float ms = fabsf(e.m[r * D]);
+        #pragma unroll
+        for (int j = 1; j < D; ++j) {
+            acc = fmaf(e.m[r * D + j], df[j], acc);
+            a = fmaf(fabsf(e.m[r * D + j]), fmaf(k4U, fabsf(df[j]), ed[j]), a);
+            ms += fabsf(e.m[r * D + j]);
+        }
+        lf[r + 1] = acc;
+        T[r + 1] = fmaf(2.0f, a, kTiny * (1.0f + ms));
+        sumT += T[r + 1];
+        suml += fabsf(acc);
+        l0 = l0 - acc;
+    }
+    lf[0] = l0;
+    T[0] = sumT + fmaf(k8U, 1.0f + suml, kTiny);
+}
+
+// x = hi + lo + r with hi = x truncated to 24 significant bits, lo = the
+// remainder truncated to float, |r| <= 2^-44 |hi|, from the bit pattern of x
+// (integer pipe only). Zero gives (0, 0); exponents outside [-74, 127] give
+// hi = NaN, which no filter test certifies (those steps use FP64).
+__device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    if ((b << 1) == 0) {
+        hi = 0.f;
+        lo = 0.f;
+        return;
+    }
+    const int E = int((b >> 52) & 0x7ff) - 1023;
+    if (E < -74 || E > 127) {
+        hi = __int_as_float(0x7fc00000);
+        lo = 0.f;
+        return;
+    }
+    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+    hi = __uint_as_float(sign | (unsigned(E + 127) << 23) | unsigned((b >> 29) & 0x7fffffu));
+    const float low = __uint2float_rz(unsigned(b & 0x1fffffffu));
+    lo = __fmul_rn(sign ? -low : low, __uint_as_float(unsigned(E + 75) << 23));
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7ff0000000000000ull) !=
+           0x7ff0000000000000ull;
+}
+
+// Cell index of one axis, FP64: floor((x - lo) / s) clamped, NaN -> 0.
+__device__ __forceinline__ int64_t cell_axis64(double x, double lo, double s, int32_t g) {
+    const double t = floor(__ddiv_rn(__dsub_rn(x, lo), s));
+    if (!(t >= 0.0)) return 0;
+    if (t > double(g - 1)) return g - 1;
+    return int64_t(t);
+}
+
+template <int D>
+__device__ __forceinline__ int64_t grid_cell(const double *x, const double *lo, const double *s,
+                                             const int32_t *g) {
+    int64_t c = 0;
+    #pragma unroll
+    for (int k = D - 1; k >= 0; --k) c = c * g[k] + cell_axis64(x[k], lo[k], s[k], g[k]);
+    return c;
+}
+
+// Same cell, certified in FP32 per axis when the rounding bound cannot move
+// the quotient across an integer; otherwise the FP64 formula.
+template <int D>
+__device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh, const float *xl,
+                                               const DevMesh &m) {
+    int64_t c = 0;
+    #pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+        const float df = (xh[k] - m.lo_h[k]) + (xl[k] - m.lo_l[k]);
+        const float ed = delta_bound(df, xh[k], m.lo_h[k]);
+        const float q = df * m.inv_sa[k];
+        const float B = fmaf(2.0f * ed, m.inv_sa[k], fmaf(k8U, fabsf(q), kTiny));
+        const float a = floorf(q - B), b = floorf(q + B);
+        int64_t i;
+        if (a == b && fabsf(q) < 4.0e6f) {
+            i = a < 0.f ? 0 : (a > float(m.ga[k] - 1) ? m.ga[k] - 1 : int64_t(a));
+        } else {
+            i = cell_axis64(x[k], m.lo[k], m.sa[k], m.ga[k]);
+        }
+        c = c * m.ga[k] + i;
+    }
+    return c;
+}
+
+// Warp-aggregated append of particle p to the exact-search list.
+__device__ __forceinline__ void push_list(bool want, int64_t p, int32_t *count, int32_t *list,
+                                          int lane) {
+    const unsigned msk = __ballot_sync(kFull, want);
+    if (!msk) return;
+    int base = 0;
+    const int leader = __ffs(msk) - 1;
+    if (lane == leader) base = atomicAdd(count, __popc(msk));
+    base = __shfl_sync(kFull, base, leader);
+    if (want) list[base + __popc(msk & ((1u << lane) - 1u))] = int32_t(p);
+}
+
+}  // namespace cs

@@ -96,7 +96,7 @@ def test_mesh_tables(ctx):
     assert (mesh.node_start_elements() == om.node_elem).all()
     assert (mesh.seed_grid() == om.seed).all()
     inf = mesh.info()
-    assert inf["asg_grid"] == [37, 37] and inf["record_bytes"] == 64
+    assert inf["asg_grid"] == [37, 37] and inf["record_bytes"] == 48
     assert inf["step_cap"] == om.cap
 
 
