@@ -154,6 +154,35 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
                         int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                         int32_t *start_out);
 
+/*
+ * cs_track without any device allocation. (This entry point is a property of
+ * the library, not of the method: the paper has no counterpart.)
+ *
+ * For callers that cannot let the library allocate device memory during a
+ * call -- a solver that owns every byte of device memory through its own pool,
+ * or a time-step loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause. Same arguments, semantics, results and
+ * errors as cs_track (DEVICE pointers, enqueued on `stream`, returns without
+ * synchronising); the caller still provides every input and output array.
+ * The walk's scratch (work cursor, exact-search count and list) lives in one
+ * fixed device array of this library, 8 MiB + 256 B, that every GPU loading
+ * the library holds until the process exits.
+ *   - n must not exceed 2,097,152 (1 << 21); larger n returns CS_EINVAL with a
+ *     message naming the limit. Nothing is allocated, ever: no cudaMalloc,
+ *     cudaFree or allocating library routine is called.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call clears the counters it needs on its stream. Calls whose work
+ *     overlaps on the GPU (other streams, other contexts, other threads on the
+ *     same device) race on the array: serialise them.
+ */
+cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                           const double *u, double dt, const int32_t *start, int mode,
+                           int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                           int32_t *start_out, void *stream);
+
 /* Walk statistics of a finished cs_track (DEVICE pointers, synchronous):
  * out[0] = sum of path_len, out[1] = max path_len, out[2..5] = particles with
  * status 0..3. */

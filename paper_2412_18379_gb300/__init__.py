@@ -151,6 +151,28 @@ class Context:
             _stream_ptr(st)))
         return out
 
+    def track_noalloc(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
+                      stream=None):
+        """cs_track_noalloc: like track(), but the library allocates nothing;
+        pass `out` (preallocated device tensors) to keep the call allocation-
+        free on this side too. n <= 2,097,152."""
+        import torch
+        n = x.shape[0]
+        dev = x.device
+        if out is None:
+            out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
+                       path_len=torch.empty(n, dtype=torch.int32, device=dev),
+                       status=torch.empty(n, dtype=torch.uint8, device=dev))
+            if start_out:
+                out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(self.lib.cs_track_noalloc(
+            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
+            _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start")),
+            _stream_ptr(st)))
+        return out
+
     def track_host(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False):
         """Host path: numpy (or pinned torch CPU) inputs; copies in, runs,
         copies out and synchronises inside the library."""

@@ -11,6 +11,8 @@
 // prepared particles from the queue, so long walks never leave lanes idle
 // while work remains.
 #include <cstdint>
+#include <mutex>
+#include <string>
 
 #include "walk_common.cuh"
 
@@ -272,4 +274,115 @@ int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_
     return 1 + launch_fallback(m, a, s.counters + 1, s.list, sm_count, st, prof);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free tracking (cs_track_noalloc).
+//
+// Some callers cannot let this library allocate device memory during a call:
+// a host solver that owns all device memory through its own pool, or a time-
+// step loop that must not pay the implicit device synchronisation that
+// cudaMalloc / cudaFree can cause. For them the walk's scratch (the work
+// cursor, the exact-search count and the exact-search list) lives in this
+// fixed, file-scope device array instead of the context's scratch buffers.
+// Every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 21;   // 2,097,152 particles
+constexpr int64_t kNoAllocListOffset = 64;                   // list starts 256 B in
+// [0] work cursor, [1] exact-search count, [64 ...] exact-search list
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocListOffset +
+                                                           kNoAllocMaxParticles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int32_t *g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
 }  // namespace cs
+
+extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                                      const double *u, double dt, const int32_t *start,
+                                      int mode, int32_t *host_out, int32_t *path_len_out,
+                                      uint8_t *status_out, int32_t *start_out, void *stream) {
+    using namespace cs;
+    if (!ctx) return CS_EINVAL;
+    auto it = ctx->meshes.find(mesh_id);
+    if (it == ctx->meshes.end()) {
+        ctx->err = "cs_track_noalloc: unknown mesh id";
+        return CS_ENOMESH;
+    }
+    const Mesh *mesh = it->second;
+    if (n < 0 || n > kNoAllocMaxParticles) {
+        ctx->err = "cs_track_noalloc: n = " + std::to_string(n) +
+                   " is outside [0, 2097152], the capacity of its fixed scratch array";
+        return CS_EINVAL;
+    }
+    if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS) {
+        ctx->err = "cs_track_noalloc: unknown mode";
+        return CS_EINVAL;
+    }
+    if (mode == CS_CNN_SNS) {
+        ctx->err = "cs_track_noalloc: no predictor loaded";
+        return CS_ENOPRED;
+    }
+    if (n == 0) return CS_OK;
+    if (!x || !u || !host_out || !path_len_out || !status_out) {
+        ctx->err = "cs_track_noalloc: null pointer";
+        return CS_EINVAL;
+    }
+    if (!start && n != mesh->d.n_v) {
+        ctx->err = "cs_track_noalloc: start == NULL needs n == n_vertices";
+        return CS_EINVAL;
+    }
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) {
+        ctx->err = "cs_track_noalloc: device ordinal out of range";
+        return CS_EINVAL;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cs_track_noalloc: cudaSetDevice: ") + cudaGetErrorString(e);
+        return CS_ECUDA;
+    }
+    // once per device, with that device current: the device address of the
+    // array (its name in host code is only a host-side stand-in)
+    int32_t *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[ctx->device]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                ctx->err = std::string("cs_track_noalloc: cudaGetSymbolAddress: ") +
+                           cudaGetErrorString(e);
+                return CS_ECUDA;
+            }
+            g_noalloc_ptr[ctx->device] = static_cast<int32_t *>(ptr);
+        }
+        base = g_noalloc_ptr[ctx->device];
+    }
+    Scratch s;
+    s.counters = base;                      // zeroed by launch_track on the stream
+    s.list = base + kNoAllocListOffset;
+    s.list_cap = kNoAllocMaxParticles;
+    TrackArgs a{};
+    a.n = n;
+    a.x = x;
+    a.u = u;
+    a.dt = dt;
+    a.start_user = start;
+    a.mode = mode;
+    a.dhat = nullptr;
+    a.host = host_out;
+    a.path = path_len_out;
+    a.status = status_out;
+    a.start_out = start_out;
+    ctx->launches += launch_track(mesh->d, a, s, ctx->sm_count, static_cast<cudaStream_t>(stream),
+                                  nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cs_track_noalloc: launch: ") + cudaGetErrorString(e);
+        return CS_ECUDA;
+    }
+    return CS_OK;
+}

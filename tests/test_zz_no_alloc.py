@@ -1,0 +1,84 @@
+"""cs_track_noalloc: the tracking entry point that allocates no device memory.
+
+It serves callers that cannot let a library allocate during a call (a solver
+that owns all device memory through its own pool, or a time-step loop that
+cannot afford the synchronisation cudaMalloc/cudaFree may bring). Its scratch
+is a fixed device array inside the library, shared by every call. These tests
+call it through the C ABI and compare it with cs_track, which uses the
+context's allocated scratch, on two calls in a row (the second call must not
+see the first call's leftovers). This file is named to be collected last.
+"""
+
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+MAX_N = 1 << 21
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2412_18379_gb300 as cs
+    from paper_2412_18379_gb300 import build
+    build.build()
+    c = cs.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 301, "cfl": 8}),
+                                     ("abc3d", {"n_side": 21, "cfl": 12})])
+def test_noalloc_matches_track_twice(ctx, name, kw):
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    x, u = _dev(c.x), _dev(c.u)
+    n = c.n_particles
+    # two calls in a row with different inputs: the shared scratch keeps the
+    # first call's contents, which must not leak into the second
+    for dt, mode in ((c.dt, "sns"), (c.dt * 3.0, "asg")):
+        want = ctx.track(mesh, x, u, dt, mode=mode, start_out=True)
+        out = dict(host=torch.full((n,), -7, dtype=torch.int32, device="cuda"),
+                   path_len=torch.full((n,), -7, dtype=torch.int32, device="cuda"),
+                   status=torch.full((n,), 9, dtype=torch.uint8, device="cuda"),
+                   start=torch.full((n,), -7, dtype=torch.int32, device="cuda"))
+        got = ctx.track_noalloc(mesh, x, u, dt, mode=mode, out=out)
+        torch.cuda.synchronize()
+        for k in ("host", "path_len", "status", "start"):
+            assert torch.equal(got[k], want[k]), (name, dt, mode, k)
+    mesh.release()
+
+
+def test_noalloc_explicit_starts_and_limit(ctx):
+    import torch
+    import paper_2412_18379_gb300 as cs
+    c = make_case("rotation2d")
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    rng = np.random.default_rng(9)
+    start = _dev(rng.integers(-1, c.n_elements, size=c.n_particles).astype(np.int32))
+    x, u = _dev(c.x), _dev(c.u)
+    for _ in range(2):
+        want = ctx.track(mesh, x, u, c.dt, start=start)
+        got = ctx.track_noalloc(mesh, x, u, c.dt, start=start)
+        torch.cuda.synchronize()
+        for k in want:
+            assert torch.equal(got[k], want[k]), k
+    # beyond the fixed capacity: a clear error, nothing launched or written
+    big = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
+    h = torch.full((4,), -7, dtype=torch.int32, device="cuda")
+    rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, MAX_N + 1, big.data_ptr(), big.data_ptr(),
+                                  0.1, start.data_ptr(), cs.CS_SNS, h.data_ptr(), h.data_ptr(),
+                                  h.data_ptr(), None, None)
+    assert rc == -1                                   # CS_EINVAL
+    assert "2097152" in ctx.lib.cs_last_error(ctx.h).decode()
+    torch.cuda.synchronize()
+    assert (h.cpu().numpy() == -7).all()
+    mesh.release()
