@@ -52,15 +52,24 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_file, dim):
+def source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2412_18379_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+WALK_SOURCES = ("walk.cu", "walk_common.cuh", "internal.h")
+
+
+def ncu_traffic(dim):
     """DRAM bytes per launch of the walk kernel from the committed ncu summary,
     if it was taken on the current source; else None."""
-    src = os.path.join(ROOT, "paper_2412_18379_gb300", "csrc", kernel_file)
     prof = os.path.join(ROOT, "profiles", "walk_kernel_tg2d_ncu.md" if dim == 2
                         else "walk_kernel_abc3d_ncu.md")
-    if not (os.path.exists(src) and os.path.exists(prof)):
+    if not os.path.exists(prof):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    sha = source_sha(WALK_SOURCES)
     vals = {}
     for line in open(prof):
         if ":" in line and line.startswith("- "):
@@ -89,7 +98,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -174,7 +183,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tg2d", choices=sorted(WORKLOADS))
@@ -287,7 +296,7 @@ def main():
     achieved = alg_bytes / (walk_ms / walk_launches * 1e-3) / 1e9 if walk_launches else 0.0
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic("walk.cu", dim),
+                "frac": achieved / peak, "traffic": ncu_traffic(dim),
                 "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "kernel": "walk_kernel<%d>" % dim,

@@ -127,7 +127,11 @@ cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
  *   start[n]: user ids of the plain-SNS start, or NULL when the particles are
  *             the mesh vertices in order (n == n_vertices): then start =
  *             cs_node_start_elements(). A start of -1 skips the walk.
- *   mode: CS_SNS, CS_ASG_DIRECT or CS_CNN_SNS (needs cs_predictor_* first).
+ *   mode: CS_SNS, CS_ASG_DIRECT or CS_CNN_SNS. CS_CNN_SNS needs a loaded
+ *         predictor (cs_predictor_load). When start == NULL and the particles
+ *         are the mesh nodes, u is the nodal field: the call resamples it to
+ *         the ASG grid, runs the predictor and walks (Algorithm 2). Otherwise
+ *         it uses the grid velocity stored by cs_grid_velocity.
  *   host_out[n]  user id of the host of x_p, or -1.
  *   path_len_out[n]  I_t of Algorithm 1 (elements evaluated, start included).
  *   status_out[n]    CS_FOUND / CS_OUTSIDE / CS_FOUND_VIA_FALLBACK / CS_INVALID.
@@ -182,6 +186,101 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double
                            const double *u, double dt, const int32_t *start, int mode,
                            int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                            int32_t *start_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned start predictor (Sec. 2.3 and Algorithm 2).                       */
+/*                                                                          */
+/* Regressor form: a window of the ASG-grid velocity around the cell of the  */
+/* particle (channels u_k * dt / s_k, zero outside the grid; 2-D 9x9, 3-D   */
+/* 7x7x7) goes through valid 3x3 (3x3x3) convolutions of 32 channels with    */
+/* ReLU (2-D: 4 layers, 3-D: 3 layers), then fully connected 32 -> 256      */
+/* (ReLU) -> dim. The output is the displacement in ASG cell units; the walk */
+/* then starts at the seed of the cell of x + displacement * s (Algorithm 2: */
+/* the prediction K_p replaces K_m as the origin of the walk).              */
+/*                                                                          */
+/* Weights: a flat float32 vector; for each conv layer W[32][C_in][taps]     */
+/* then b[32] (tap t = (dz*3 +) dy*3 + dx, offsets 0..2 reading input       */
+/* position (z+dz, y+dy, x+dx) for output (z, y, x)), then fc1 W[256][32],  */
+/* b[256], fc2 W[dim][256], b[dim]. 37,314 floats (2-D), 67,203 (3-D).      */
+/* Arithmetic: BF16 operands, FP32 accumulation, FP32 master weights.       */
+/* ------------------------------------------------------------------------ */
+
+/* Operand precision of the training and window-forward GEMMs: bf16 != 0 (the
+ * default) rounds operands to BF16; 0 keeps FP32 operands, for accuracy
+ * checks. Process-wide (every context). */
+cs_status cs_predictor_precision(cs_ctx *ctx, int bf16);
+
+/* Number of floats of the predictor of dimension dim (0 for other dim). */
+int64_t cs_predictor_size(int dim);
+
+/* Load (replace) the predictor of dimension dim from HOST weights; resets the
+ * optimiser state. Errors: CS_EINVAL (dim, n != cs_predictor_size), CS_ENOMEM. */
+cs_status cs_predictor_load(cs_ctx *ctx, int dim, const float *weights, int64_t n);
+
+/* Copy the current FP32 master weights to HOST memory. CS_ENOPRED if none. */
+cs_status cs_predictor_save(cs_ctx *ctx, int dim, float *weights_out, int64_t n);
+
+/* ASG-grid velocity of a mesh from its nodal velocity (DEVICE pointers):
+ * grid[c][k] = P1 interpolation of u_nodal[n_v][dim] at the centre of cell c
+ * inside the centre's host element (0 where the centre is outside the mesh),
+ * evaluated in FP32. grid_out: [prod asg_grid][dim] floats, or NULL to store
+ * it in the mesh (used by cs_predict / CS_CNN_SNS). Enqueued on stream. */
+cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal,
+                           float *grid_out, void *stream);
+
+/* Input windows at ASG cells (DEVICE pointers): out[b][k][w] = grid[cells[b]
+ * + offset(w)][k] * dt / s_k, zero outside the grid, w over the window
+ * positions (x fastest). grid = NULL uses the mesh's stored grid velocity.
+ * cells = NULL means cells 0..B-1. */
+cs_status cs_windows(cs_ctx *ctx, int32_t mesh_id, const float *grid, double dt,
+                     const int64_t *cells, int64_t B, float *out, void *stream);
+
+/* Predictor forward on explicit windows (DEVICE pointers): windows
+ * [B][dim][S^dim] -> dhat [B][dim] (cell units). Synchronous. */
+cs_status cs_predictor_forward(cs_ctx *ctx, int dim, int64_t B, const float *windows,
+                               float *dhat_out);
+
+/* Predicted displacement (cell units) at every ASG cell of a mesh from its
+ * stored grid velocity and dt (DEVICE output [prod asg_grid][dim], or NULL to
+ * store it in the mesh for cs_track_dhat(.., NULL ..)). Enqueued on stream. */
+cs_status cs_predict(cs_ctx *ctx, int32_t mesh_id, double dt, float *dhat_out, void *stream);
+
+/* Train the predictor of dimension dim on N (window, target) pairs (DEVICE
+ * windows [N][dim][S^dim], targets [N][dim] in cell units) with Adam
+ * (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error, for
+ * `steps` batches of `batch` pairs drawn without replacement per epoch from a
+ * generator seeded by `seed`. loss_out (HOST, may be NULL) receives the loss
+ * of every step. Synchronous. CS_ENOPRED if no predictor is loaded. */
+cs_status cs_predictor_train(cs_ctx *ctx, int dim, const float *windows, const float *targets,
+                             int64_t N, int64_t batch, int64_t steps, float lr, uint64_t seed,
+                             float *loss_out);
+
+/* Training pairs (Sec. 2.3: the training data are produced by the tracking
+ * itself) for n particles at positions x with velocities u (DEVICE pointers):
+ * cells_out[p] = ASG cell of x_p's origin x, windows_out[p] = the input
+ * window at that cell from the mesh's stored grid velocity (scale dt / s_k),
+ * targets_out[p][k] = (x_p,k - x_k) / s_k with x_p = x - (u * dt). The host
+ * element labels come from cs_track with CS_SNS. Enqueued on stream. */
+cs_status cs_training_pairs(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                            const double *u, double dt, float *windows_out, float *targets_out,
+                            int64_t *cells_out, void *stream);
+
+/* Gradient of the mean squared error of the predictor of dimension dim on B
+ * (window, target) pairs (DEVICE pointers; grad_out [cs_predictor_size],
+ * same layout as the weights) without updating the weights; loss_out (HOST,
+ * may be NULL). Synchronous. */
+cs_status cs_predictor_grad(cs_ctx *ctx, int dim, int64_t B, const float *windows,
+                            const float *targets, float *grad_out, float *loss_out);
+
+/* CNN-SNS start rule with a given displacement grid (DEVICE pointers): like
+ * cs_track, but the walk starts at the seed of the ASG cell of
+ * x + dhat[cell(x)] * s (falling back to the plain start where that seed is
+ * -1). dhat: [prod asg_grid][dim] floats in cell units, or NULL for the
+ * mesh's stored prediction (cs_predict). */
+cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                        const double *u, double dt, const int32_t *start, const float *dhat,
+                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                        int32_t *start_out, void *stream);
 
 /* Walk statistics of a finished cs_track (DEVICE pointers, synchronous):
  * out[0] = sum of path_len, out[1] = max path_len, out[2..5] = particles with

@@ -193,6 +193,101 @@ class Context:
             _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start"))))
         return out
 
+    # ---------------- start predictor ----------------
+    def predictor_precision(self, bf16=True):
+        self._check(self.lib.cs_predictor_precision(self.h, 1 if bf16 else 0))
+
+    def predictor_size(self, dim):
+        return int(self.lib.cs_predictor_size(dim))
+
+    def load_predictor(self, dim, weights):
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        self._check(self.lib.cs_predictor_load(self.h, dim, _ptr(w), w.size))
+
+    def save_predictor(self, dim):
+        out = np.empty(self.predictor_size(dim), dtype=np.float32)
+        self._check(self.lib.cs_predictor_save(self.h, dim, _ptr(out), out.size))
+        return out
+
+    def grid_velocity(self, mesh, u_nodal, out=None, stream=None):
+        """Resample the nodal velocity (float64 CUDA tensor) onto the ASG grid;
+        out=None stores it in the mesh and returns None."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream(u_nodal.device)
+        self._check(self.lib.cs_grid_velocity(self.h, mesh.id, _ptr(u_nodal), _ptr(out),
+                                              _stream_ptr(st)))
+        return out
+
+    def windows(self, mesh, dt, cells=None, B=None, grid=None, stream=None):
+        import torch
+        S = 9 if mesh.dim == 2 else 7
+        B = cells.shape[0] if cells is not None else B
+        out = torch.empty((B, mesh.dim) + (S,) * mesh.dim, dtype=torch.float32, device="cuda")
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.cs_windows(self.h, mesh.id, _ptr(grid), float(dt), _ptr(cells), B,
+                                        _ptr(out), _stream_ptr(st)))
+        return out
+
+    def predictor_forward(self, dim, windows):
+        import torch
+        out = torch.empty((windows.shape[0], dim), dtype=torch.float32, device=windows.device)
+        self._check(self.lib.cs_predictor_forward(self.h, dim, windows.shape[0], _ptr(windows),
+                                                  _ptr(out)))
+        return out
+
+    def predict(self, mesh, dt, out=None, stream=None):
+        """Predicted displacement (cell units) at every ASG cell."""
+        import torch
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.cs_predict(self.h, mesh.id, float(dt), _ptr(out), _stream_ptr(st)))
+        return out
+
+    def training_pairs(self, mesh, x, u, dt, stream=None):
+        import torch
+        n = x.shape[0]
+        S = 9 if mesh.dim == 2 else 7
+        win = torch.empty((n, mesh.dim) + (S,) * mesh.dim, dtype=torch.float32, device=x.device)
+        tgt = torch.empty((n, mesh.dim), dtype=torch.float32, device=x.device)
+        cells = torch.empty(n, dtype=torch.int64, device=x.device)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        self._check(self.lib.cs_training_pairs(self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt),
+                                               _ptr(win), _ptr(tgt), _ptr(cells),
+                                               _stream_ptr(st)))
+        return win, tgt, cells
+
+    def train(self, dim, windows, targets, batch=4096, steps=100, lr=1e-3, seed=0):
+        losses = np.empty(steps, dtype=np.float32)
+        self._check(self.lib.cs_predictor_train(self.h, dim, _ptr(windows), _ptr(targets),
+                                                windows.shape[0], batch, steps, float(lr),
+                                                int(seed), _ptr(losses)))
+        return losses
+
+    def predictor_grad(self, dim, windows, targets):
+        import torch
+        g = torch.empty(self.predictor_size(dim), dtype=torch.float32, device=windows.device)
+        loss = np.zeros(1, dtype=np.float32)
+        self._check(self.lib.cs_predictor_grad(self.h, dim, windows.shape[0], _ptr(windows),
+                                               _ptr(targets), _ptr(g), _ptr(loss)))
+        return g, float(loss[0])
+
+    def track_dhat(self, mesh, x, u, dt, dhat=None, start=None, out=None, start_out=False,
+                   stream=None):
+        import torch
+        n = x.shape[0]
+        dev = x.device
+        if out is None:
+            out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
+                       path_len=torch.empty(n, dtype=torch.int32, device=dev),
+                       status=torch.empty(n, dtype=torch.uint8, device=dev))
+            if start_out:
+                out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(self.lib.cs_track_dhat(
+            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(dhat),
+            _ptr(out["host"]), _ptr(out["path_len"]), _ptr(out["status"]),
+            _ptr(out.get("start")), _stream_ptr(st)))
+        return out
+
     def stats(self, path_len, status, stream=None):
         """(sum, max, count FOUND, OUTSIDE, FALLBACK, INVALID) of device outputs."""
         import torch

@@ -63,6 +63,20 @@ SIGNATURES = {
                                 _vp, _vp, _vp]),
     "cs_track_stats": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp]),
     "cs_kernel_launches": (_i64, [_vp]),
+    "cs_predictor_precision": (_i32, [_vp, ctypes.c_int]),
+    "cs_predictor_size": (_i64, [ctypes.c_int]),
+    "cs_predictor_load": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
+    "cs_predictor_save": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
+    "cs_grid_velocity": (_i32, [_vp, _i32, _vp, _vp, _vp]),
+    "cs_windows": (_i32, [_vp, _i32, _vp, _dbl, _vp, _i64, _vp, _vp]),
+    "cs_predictor_forward": (_i32, [_vp, ctypes.c_int, _i64, _vp, _vp]),
+    "cs_predict": (_i32, [_vp, _i32, _dbl, _vp, _vp]),
+    "cs_predictor_train": (_i32, [_vp, ctypes.c_int, _vp, _vp, _i64, _i64, _i64, ctypes.c_float,
+                                  ctypes.c_uint64, _vp]),
+    "cs_training_pairs": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp]),
+    "cs_predictor_grad": (_i32, [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp]),
+    "cs_track_dhat": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
+                             _vp]),
     "cs_profile_enable": (_i32, [_vp, ctypes.c_int]),
     "cs_profile_read": (_i32, [_vp, _vp, ctypes.c_int]),
 }

@@ -99,6 +99,7 @@ void cs_destroy(cs_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     for (auto &kv : ctx->meshes) free_mesh(kv.second);
+    for (auto &p : ctx->pred) cs::predictor_release(p);
     if (ctx->scratch.counters) cudaFree(ctx->scratch.counters);
     if (ctx->scratch.stats) cudaFree(ctx->scratch.stats);
     if (ctx->scratch.list) cudaFree(ctx->scratch.list);
@@ -213,8 +214,13 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         d.lo_h[k] = static_cast<float>(d.lo[k]);
         d.lo_l[k] = static_cast<float>(d.lo[k] - static_cast<double>(d.lo_h[k]));
         d.inv_sa[k] = static_cast<float>(1.0 / d.sa[k]);
+        d.inv_sb[k] = static_cast<float>(1.0 / d.sb[k]);
     }
     d.margin = H.margin;
+    for (int k = 0; k < 3; ++k) {
+        d.lo_m[k] = d.lo[k] - d.margin;
+        d.hi_m[k] = d.hi[k] + d.margin;
+    }
     d.tau = H.tau;
     d.cap = H.cap;
     d.n_asg = n_asg;
@@ -298,12 +304,35 @@ cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, con
     if (!ctx) return CS_EINVAL;
     cs::Mesh *m = find_mesh(ctx, mesh_id);
     if (!m) return fail(ctx, CS_ENOMESH, "cs_track: unknown mesh id");
-    if (n < 0 || n >= (int64_t(1) << 31) - 1)
-        return fail(ctx, CS_EINVAL, "cs_track: n out of range");
     if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS)
         return fail(ctx, CS_EINVAL, "cs_track: unknown mode");
-    if (mode == CS_CNN_SNS)
-        return fail(ctx, CS_ENOPRED, "cs_track: no predictor loaded");
+    const float *dhat = nullptr;
+    if (mode == CS_CNN_SNS) {
+        if (!ctx->pred[m->d.dim - 2].loaded)
+            return fail(ctx, CS_ENOPRED, "cs_track: no predictor loaded");
+        if (n == 0) return CS_OK;
+        if (!x || !u) return fail(ctx, CS_EINVAL, "cs_track: null pointer");
+        CS_CUDA(ctx, cudaSetDevice(ctx->device));
+        // particles at the mesh nodes: their velocities are the nodal field
+        const bool nodes = !start && n == m->d.n_v;
+        if (!nodes && !m->grid_u_valid)
+            return fail(ctx, CS_EINVAL, "cs_track: CNN-SNS needs cs_grid_velocity first");
+        cs_status rc = cs::cnn_prepare(ctx, m, nodes ? u : nullptr, dt,
+                                       static_cast<cudaStream_t>(stream), &dhat);
+        if (rc) return rc;
+    }
+    return cs::cs_track_impl(ctx, m, n, x, u, dt, start, mode, dhat, host_out, path_len_out,
+                             status_out, start_out, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+cs_status cs::cs_track_impl(cs_ctx *ctx, cs::Mesh *m, int64_t n, const double *x,
+                            const double *u, double dt, const int32_t *start, int mode,
+                            const float *dhat, int32_t *host_out, int32_t *path_len_out,
+                            uint8_t *status_out, int32_t *start_out, cudaStream_t stream) {
+    if (n < 0 || n >= (int64_t(1) << 31) - 1)
+        return fail(ctx, CS_EINVAL, "cs_track: n out of range");
     if (n == 0) return CS_OK;
     if (!x || !u || !host_out || !path_len_out || !status_out)
         return fail(ctx, CS_EINVAL, "cs_track: null pointer");
@@ -319,16 +348,17 @@ cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, con
     a.dt = dt;
     a.start_user = start;
     a.mode = mode;
-    a.dhat = nullptr;
+    a.dhat = dhat;
     a.host = host_out;
     a.path = path_len_out;
     a.status = status_out;
     a.start_out = start_out;
-    ctx->launches += cs::launch_track(m->d, a, ctx->scratch, ctx->sm_count,
-                                      static_cast<cudaStream_t>(stream), &ctx->prof);
+    ctx->launches += cs::launch_track(m->d, a, ctx->scratch, ctx->sm_count, stream, &ctx->prof);
     CS_CUDA(ctx, cudaGetLastError());
     return CS_OK;
 }
+
+extern "C" {
 
 cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
                         const double *u, double dt, const int32_t *start, int mode,

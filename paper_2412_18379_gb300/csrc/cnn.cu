@@ -1,0 +1,448 @@
+// Learned start predictor (Sec. 2.3, Algorithm 2): the velocity field on the
+// ASG grid, input windows, and the CUDA-core kernels of training (forward,
+// backward and Adam on batches of windows, BF16 operands with FP32
+// accumulation, FP32 master weights).
+//
+// Network (regressor form): a window of the grid velocity around the cell of
+// the particle, channels u_k * dt / s_k, zero outside the grid, goes through
+// valid 3x3 (3x3x3) convolutions of 32 channels with ReLU, then 32 -> 256
+// (ReLU) -> dim; the output is the particle's displacement in cell units.
+// 2-D: window 9x9, 4 convolutions; 3-D: window 7^3, 3 convolutions.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "cnn.h"
+#include "walk_common.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float bf16_round(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
+}
+
+int grid_for(int64_t n, int sm_count, int per_sm = 8) {
+    const int64_t need = (n + kThreads - 1) / kThreads;
+    return int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sm_count) * per_sm)));
+}
+
+// U[c] = P1 interpolation of the nodal velocity at the centre of ASG cell c,
+// inside the centre's host element seed[c] (FP32 evaluation of the
+// barycentric coordinates from the walk record). 0 where seed[c] = -1.
+template <int D>
+__global__ void __launch_bounds__(kThreads) resample_kernel(const DevMesh m,
+                                                            const double *__restrict__ un,
+                                                            float *__restrict__ U) {
+    using WR = typename Recs<D>::W;
+    const WR *__restrict__ rw = static_cast<const WR *>(m.recw);
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < m.n_asg;
+         c += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t s = __ldg(m.seed + c);
+        float out[D];
+        #pragma unroll
+        for (int k = 0; k < D; ++k) out[k] = 0.f;
+        if (s >= 0) {
+            WalkE<D> e;
+            load_walk(rw, s, e);
+            int64_t r = c;
+            float df[D];
+            #pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int64_t i = r % m.ga[k];
+                r /= m.ga[k];
+                df[k] = ((m.lo_h[k] - e.vh[k]) + (m.lo_l[k] - e.vl[k])) +
+                        (float(i) + 0.5f) * float(m.sa[k]);
+            }
+            float lam[D + 1];
+            float l0 = 1.f;
+            #pragma unroll
+            for (int r2 = 0; r2 < D; ++r2) {
+                float acc = 0.f;
+                #pragma unroll
+                for (int j = 0; j < D; ++j) acc = fmaf(e.m[r2 * D + j], df[j], acc);
+                lam[r2 + 1] = acc;
+                l0 -= acc;
+            }
+            lam[0] = l0;
+            #pragma unroll
+            for (int i = 0; i <= D; ++i) {
+                const int32_t v = __ldg(m.conn + int64_t(s) * (D + 1) + i);
+                #pragma unroll
+                for (int k = 0; k < D; ++k)
+                    out[k] = fmaf(lam[i], trunc_to_float(__ldg(un + int64_t(v) * D + k)), out[k]);
+            }
+        }
+        #pragma unroll
+        for (int k = 0; k < D; ++k) U[c * D + k] = out[k];
+    }
+}
+
+// windows[b][k][w] = U[cell_b + offset(w)][k] * scale_k, 0 outside the grid;
+// w runs over the S^D window positions, x fastest; offsets -S/2..S/2.
+template <int D>
+__global__ void __launch_bounds__(kThreads) window_kernel(const DevMesh m, const float *__restrict__ U,
+                                                          const int64_t *__restrict__ cells,
+                                                          int64_t cell0, int64_t B, float s0,
+                                                          float s1, float s2,
+                                                          float *__restrict__ out) {
+    constexpr int S = D == 2 ? 9 : 7;
+    constexpr int W = D == 2 ? 81 : 343;
+    const float scale[3] = {s0, s1, s2};
+    const int64_t total = B * W;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = q / W;
+        int w = int(q % W);
+        const int64_t cell = cells ? __ldg(cells + b) : cell0 + b;
+        int64_t r = cell;
+        int64_t src = 0, mul = 1;
+        bool inside = true;
+        #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int64_t ic = r % m.ga[k];
+            r /= m.ga[k];
+            const int64_t j = ic + (w % S) - S / 2;
+            w /= S;
+            inside = inside && j >= 0 && j < m.ga[k];
+            src += j * mul;
+            mul *= m.ga[k];
+        }
+        #pragma unroll
+        for (int k = 0; k < D; ++k)
+            out[(b * D + k) * W + (q % W)] = inside ? __ldg(U + src * D + k) * scale[k] : 0.f;
+    }
+}
+
+// im2col of one valid 3^D convolution: col[(b*Po + p)][i*taps + t] =
+// x(b, i, p + offset(t)); x is channels-first [B][C][Si^D] (first layer) or
+// channels-last [B][Si^D][C].
+template <int D>
+__global__ void __launch_bounds__(kThreads) im2col_kernel(const float *__restrict__ x, int64_t B,
+                                                          int C, int Si, bool chfirst,
+                                                          float *__restrict__ col) {
+    const int So = Si - 2;
+    const int taps = D == 2 ? 9 : 27;
+    int Po = So * So, Pi = Si * Si;
+    if (D == 3) {
+        Po *= So;
+        Pi *= Si;
+    }
+    const int64_t K = int64_t(C) * taps;
+    const int64_t total = B * Po * K;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t row = q / K;
+        const int kk = int(q % K);
+        const int64_t b = row / Po;
+        const int p = int(row % Po);
+        const int i = kk / taps, t = kk % taps;
+        int px = p % So, py = (p / So) % So, pz = D == 3 ? p / (So * So) : 0;
+        px += t % 3;
+        py += (t / 3) % 3;
+        pz += D == 3 ? t / 9 : 0;
+        const int pin = D == 2 ? py * Si + px : (pz * Si + py) * Si + px;
+        col[q] = chfirst ? x[(b * C + i) * Pi + pin] : x[(b * Pi + pin) * C + i];
+    }
+}
+
+// col2im (gather form): dx[b][pin][i] = sum over taps t with a valid output
+// position p = pin - offset(t) of dcol[(b*Po + p)][i*taps + t]. Channels-last.
+template <int D>
+__global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restrict__ dcol, int64_t B,
+                                                          int C, int Si, float *__restrict__ dx) {
+    const int So = Si - 2;
+    const int taps = D == 2 ? 9 : 27;
+    int Po = So * So, Pi = Si * Si;
+    if (D == 3) {
+        Po *= So;
+        Pi *= Si;
+    }
+    const int64_t total = B * Pi * C;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(q % C);
+        const int64_t bp = q / C;
+        const int pin = int(bp % Pi);
+        const int64_t b = bp / Pi;
+        const int ix = pin % Si, iy = (pin / Si) % Si, iz = D == 3 ? pin / (Si * Si) : 0;
+        float s = 0.f;
+        for (int t = 0; t < taps; ++t) {
+            const int ox = ix - t % 3, oy = iy - (t / 3) % 3, oz = D == 3 ? iz - t / 9 : 0;
+            if (ox < 0 || oy < 0 || oz < 0 || ox >= So || oy >= So || (D == 3 && oz >= So))
+                continue;
+            const int p = D == 2 ? oy * So + ox : (oz * So + oy) * So + ox;
+            s += dcol[(b * Po + p) * (int64_t(C) * taps) + int64_t(i) * taps + t];
+        }
+        dx[q] = s;
+    }
+}
+
+// C[M][N] = op(A) op(B) (+ bias[N]) with operands rounded to BF16 and FP32
+// accumulation. A is [M][K] (transA: [K][M]); B is [K][N] (transB: [N][K]).
+// 64x64 output tile, 16-deep K slabs in shared memory, 4x4 per thread.
+__global__ void __launch_bounds__(kThreads) gemm_kernel(const float *__restrict__ A,
+                                                        const float *__restrict__ Bm, float *C,
+                                                        const float *__restrict__ bias, int64_t M,
+                                                        int64_t N, int64_t K, bool transA,
+                                                        bool transB, bool accumulate,
+                                                        bool round_bf16) {
+    __shared__ float As[16][64 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t m0 = int64_t(blockIdx.y) * 64, n0 = int64_t(blockIdx.x) * 64;
+    float acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < K; k0 += 16) {
+        for (int q = threadIdx.x; q < 16 * 64; q += kThreads) {
+            const int kk = q / 64, mm = q % 64;
+            const int64_t gm = m0 + mm, gk = k0 + kk;
+            float a = 0.f;
+            if (gm < M && gk < K) a = transA ? A[gk * M + gm] : A[gm * K + gk];
+            As[kk][mm] = round_bf16 ? bf16_round(a) : a;
+            const int64_t gn = n0 + mm;
+            float bv = 0.f;
+            if (gn < N && gk < K) bv = transB ? Bm[gn * K + gk] : Bm[gk * N + gn];
+            Bs[kk][mm] = round_bf16 ? bf16_round(bv) : bv;
+        }
+        __syncthreads();
+        #pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+            #pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                a[r] = As[kk][ty * 4 + r];
+                b[r] = Bs[kk][tx * 4 + r];
+            }
+            #pragma unroll
+            for (int r = 0; r < 4; ++r)
+                #pragma unroll
+                for (int s = 0; s < 4; ++s) acc[r][s] = fmaf(a[r], b[s], acc[r][s]);
+        }
+        __syncthreads();
+    }
+    #pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gm = m0 + ty * 4 + r;
+        if (gm >= M) continue;
+        #pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const int64_t gn = n0 + tx * 4 + s;
+            if (gn >= N) continue;
+            float v = acc[r][s] + (bias ? bias[gn] : 0.f);
+            if (accumulate) v += C[gm * N + gn];
+            C[gm * N + gn] = v;
+        }
+    }
+}
+
+// y = relu(z) (elementwise), and dz = dy * (z > 0)
+__global__ void relu_kernel(const float *__restrict__ z, float *__restrict__ y, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = fmaxf(z[i], 0.f);
+}
+__global__ void relu_back_kernel(const float *__restrict__ z, float *__restrict__ dy, int64_t n) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        dy[i] = z[i] > 0.f ? dy[i] : 0.f;
+}
+
+// column sums: out[n] = sum_m x[m][n]  (bias gradients); one block per column
+__global__ void colsum_kernel(const float *__restrict__ x, int64_t M, int64_t N,
+                              float *__restrict__ out) {
+    __shared__ float red[kThreads];
+    for (int64_t n = blockIdx.x; n < N; n += gridDim.x) {
+        float s = 0.f;
+        for (int64_t m = threadIdx.x; m < M; m += blockDim.x) s += x[m * N + n];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = kThreads / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[n] = red[0];
+        __syncthreads();
+    }
+}
+
+// dL/dout of L = mean over batch and components of (out - target)^2, and the
+// per-block partial sums of the squared error.
+__global__ void mse_grad_kernel(const float *__restrict__ out, const float *__restrict__ tgt,
+                                int64_t n, float *__restrict__ g, float *__restrict__ loss) {
+    __shared__ float red[kThreads];
+    float s = 0.f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float d = out[i] - tgt[i];
+        g[i] = 2.f * d / float(n);
+        s += d * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] / float(n));
+}
+
+// Adam on the FP32 master weights (Sec. 2.3 names Adam; constants are the
+// customary ones): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// w -= lr * m/(1-b1^t) / (sqrt(v/(1-b2^t)) + eps).
+__global__ void adam_kernel(float *__restrict__ w, const float *__restrict__ g,
+                            float *__restrict__ mo, float *__restrict__ ve, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float gi = g[i];
+        const float m = b1 * mo[i] + (1.f - b1) * gi;
+        const float v = b2 * ve[i] + (1.f - b2) * gi * gi;
+        mo[i] = m;
+        ve[i] = v;
+        w[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+// Training pairs: the ASG cell of every particle's position x and its true
+// displacement in cell units, target_k = (x_p,k - x_k) / s_k with
+// x_p = x - (u * dt) (Eq. 3, first order).
+template <int D>
+__global__ void pairs_kernel(const DevMesh m, int64_t n, const double *__restrict__ x,
+                             const double *__restrict__ u, double dt, int64_t *__restrict__ cells,
+                             float *__restrict__ target) {
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+         p += int64_t(gridDim.x) * blockDim.x) {
+        double xv[D];
+        #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            xv[k] = x[p * D + k];
+            const double xp = __dsub_rn(xv[k], __dmul_rn(u[p * D + k], dt));
+            target[p * D + k] = float(__ddiv_rn(__dsub_rn(xp, xv[k]), m.sa[k]));
+        }
+        cells[p] = grid_cell<D>(xv, m.lo, m.sa, m.ga);
+    }
+}
+
+// dst[b][:] = src[idx[b]][:] for rows of `row` floats (batch gather)
+__global__ void gather_rows_kernel(const float *__restrict__ src, int64_t row,
+                                   const int64_t *__restrict__ idx, int64_t B,
+                                   float *__restrict__ dst) {
+    const int64_t total = B * row;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x)
+        dst[q] = src[__ldg(idx + q / row) * row + q % row];
+}
+
+}  // namespace
+
+int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, double dt,
+                 int64_t *cells, float *target, int sm_count, cudaStream_t st) {
+    const int g = grid_for(n, sm_count);
+    if (m.dim == 2)
+        pairs_kernel<2><<<g, kThreads, 0, st>>>(m, n, x, u, dt, cells, target);
+    else
+        pairs_kernel<3><<<g, kThreads, 0, st>>>(m, n, x, u, dt, cells, target);
+    return 1;
+}
+
+int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,
+                       int sm_count, cudaStream_t st) {
+    gather_rows_kernel<<<grid_for(B * row, sm_count, 16), kThreads, 0, st>>>(src, row, idx, B, dst);
+    return 1;
+}
+
+int launch_resample(const DevMesh &m, const double *u_nodal, float *U, int sm_count,
+                    cudaStream_t st) {
+    const int g = grid_for(m.n_asg, sm_count);
+    if (m.dim == 2)
+        resample_kernel<2><<<g, kThreads, 0, st>>>(m, u_nodal, U);
+    else
+        resample_kernel<3><<<g, kThreads, 0, st>>>(m, u_nodal, U);
+    return 1;
+}
+
+int launch_windows(const DevMesh &m, const float *U, const int64_t *cells, int64_t cell0,
+                   int64_t B, const float scale[3], float *out, int sm_count, cudaStream_t st) {
+    const int W = m.dim == 2 ? 81 : 343;
+    const int g = grid_for(B * W, sm_count);
+    if (m.dim == 2)
+        window_kernel<2><<<g, kThreads, 0, st>>>(m, U, cells, cell0, B, scale[0], scale[1], scale[2],
+                                                  out);
+    else
+        window_kernel<3><<<g, kThreads, 0, st>>>(m, U, cells, cell0, B, scale[0], scale[1], scale[2],
+                                                  out);
+    return 1;
+}
+
+int launch_im2col(int dim, const float *x, int64_t B, int C, int Si, bool chfirst, float *col,
+                  int sm_count, cudaStream_t st) {
+    const int So = Si - 2, taps = dim == 2 ? 9 : 27;
+    const int64_t Po = dim == 2 ? So * So : int64_t(So) * So * So;
+    const int g = grid_for(B * Po * C * taps, sm_count, 32);
+    if (dim == 2)
+        im2col_kernel<2><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
+    else
+        im2col_kernel<3><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
+    return 1;
+}
+
+int launch_col2im(int dim, const float *dcol, int64_t B, int C, int Si, float *dx, int sm_count,
+                  cudaStream_t st) {
+    const int64_t Pi = dim == 2 ? Si * Si : int64_t(Si) * Si * Si;
+    const int g = grid_for(B * Pi * C, sm_count, 32);
+    if (dim == 2)
+        col2im_kernel<2><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
+    else
+        col2im_kernel<3><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
+    return 1;
+}
+
+// BF16 operands (the training arithmetic) unless switched off for an
+// accuracy check; process-wide.
+static bool g_gemm_bf16 = true;
+void set_gemm_bf16(bool on) { g_gemm_bf16 = on; }
+
+int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
+                int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
+                cudaStream_t st) {
+    const dim3 grid(unsigned((N + 63) / 64), unsigned((M + 63) / 64));
+    gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, C, bias, M, N, K, transA, transB, accumulate,
+                                           g_gemm_bf16);
+    return 1;
+}
+
+int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st) {
+    relu_kernel<<<grid_for(n, sm_count, 16), kThreads, 0, st>>>(z, y, n);
+    return 1;
+}
+
+int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStream_t st) {
+    relu_back_kernel<<<grid_for(n, sm_count, 16), kThreads, 0, st>>>(z, dy, n);
+    return 1;
+}
+
+int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st) {
+    colsum_kernel<<<unsigned(std::min<int64_t>(N, 1024)), kThreads, 0, st>>>(x, M, N, out);
+    return 1;
+}
+
+int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,
+                    int sm_count, cudaStream_t st) {
+    mse_grad_kernel<<<grid_for(n, sm_count, 1), kThreads, 0, st>>>(out, tgt, n, g, loss);
+    return 1;
+}
+
+int launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,
+                int sm_count, cudaStream_t st) {
+    const double b1 = 0.9, b2 = 0.999;
+    const float c1 = float(1.0 - std::pow(b1, double(t)));
+    const float c2 = float(1.0 - std::pow(b2, double(t)));
+    adam_kernel<<<grid_for(n, sm_count, 4), kThreads, 0, st>>>(w, g, m, v, n, lr, float(b1),
+                                                                float(b2), 1e-8f, c1, c2);
+    return 1;
+}
+
+}  // namespace cs

@@ -1,0 +1,53 @@
+// Start predictor: device state and kernel launchers (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "internal.h"
+
+namespace cs {
+
+// Layer geometry of the regressor for dim 2 / 3.
+struct NetShape {
+    int dim;
+    int cin;        // input channels (= dim)
+    int S0;         // window edge (9 / 7)
+    int n_conv;     // 4 / 3
+    int ch;         // 32
+    int hidden;     // 256
+    int64_t n_params;
+    // offsets of W and b of every layer in the flat vector
+    std::vector<int64_t> w_off, b_off;
+    explicit NetShape(int d);
+    int taps() const { return dim == 2 ? 9 : 27; }
+    int64_t positions(int S) const { return dim == 2 ? int64_t(S) * S : int64_t(S) * S * S; }
+};
+
+int launch_resample(const DevMesh &m, const double *u_nodal, float *U, int sm_count,
+                    cudaStream_t st);
+int launch_windows(const DevMesh &m, const float *U, const int64_t *cells, int64_t cell0,
+                   int64_t B, const float scale[3], float *out, int sm_count, cudaStream_t st);
+int launch_im2col(int dim, const float *x, int64_t B, int C, int Si, bool chfirst, float *col,
+                  int sm_count, cudaStream_t st);
+int launch_col2im(int dim, const float *dcol, int64_t B, int C, int Si, float *dx, int sm_count,
+                  cudaStream_t st);
+int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
+                int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
+                cudaStream_t st);
+void set_gemm_bf16(bool on);
+int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st);
+int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStream_t st);
+int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st);
+int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,
+                    int sm_count, cudaStream_t st);
+int launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,
+                int sm_count, cudaStream_t st);
+int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, double dt,
+                 int64_t *cells, float *target, int sm_count, cudaStream_t st);
+int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,
+                       int sm_count, cudaStream_t st);
+
+}  // namespace cs

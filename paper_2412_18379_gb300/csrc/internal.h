@@ -68,7 +68,9 @@ struct DevMesh {
     double sb[3];
     float lo_h[3], lo_l[3];   // lo split into float hi + lo (FP32 cell filter)
     float inv_sa[3];          // 1 / sa rounded to float
+    float inv_sb[3];          // 1 / sb rounded to float
     double margin;            // bucket boxes are grown by this much
+    double lo_m[3], hi_m[3];  // lo - margin, hi + margin: no host beyond these
     double tau;               // canonicalisation threshold
     int32_t cap;              // step cap
     int64_t n_asg, n_bucket;
@@ -79,6 +81,29 @@ struct Mesh {
     cs_mesh_info info{};
     std::vector<void *> allocs;
     std::vector<int32_t> node_elem_user;  // host copy, user ids
+    float *grid_u = nullptr;              // [n_asg][dim] grid velocity (CNN input)
+    float *grid_dhat = nullptr;           // [n_asg][dim] predicted displacement
+    bool grid_u_valid = false;
+};
+
+// The start predictor of one dimension: FP32 master weights, gradients, Adam
+// state, and the activations of the last forward pass (sized for `cap`).
+struct Predictor {
+    bool loaded = false;
+    int dim = 0;
+    int64_t n = 0;
+    float *w = nullptr;
+    float *g = nullptr;
+    float *m = nullptr;
+    float *v = nullptr;
+    float *loss = nullptr;
+    int64_t t = 0;
+    int64_t cap = 0;
+    std::vector<float *> col, z, y;
+    float *z5 = nullptr, *a5 = nullptr, *out = nullptr, *gout = nullptr;
+    float *dcol = nullptr, *dy0 = nullptr, *dy1 = nullptr, *da5 = nullptr, *win = nullptr,
+          *tgt = nullptr;
+    int64_t *idx = nullptr;
 };
 
 // Device scratch owned by a context: counters and the exact-search list.
@@ -177,5 +202,18 @@ struct cs_ctx {
     int32_t next_mesh = 1;
     cs::Scratch scratch;
     cs::Profiler prof;
+    cs::Predictor pred[2];   // dim 2, dim 3
     int64_t launches = 0;
 };
+
+namespace cs {
+// shared body of cs_track / cs_track_dhat (api.cpp)
+cs_status cs_track_impl(cs_ctx *ctx, Mesh *m, int64_t n, const double *x, const double *u,
+                        double dt, const int32_t *start, int mode, const float *dhat,
+                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                        int32_t *start_out, cudaStream_t stream);
+// predictor.cpp
+void predictor_release(Predictor &P);
+cs_status cnn_prepare(cs_ctx *ctx, Mesh *m, const double *u_nodal, double dt, cudaStream_t st,
+                      const float **dhat_out);
+}  // namespace cs

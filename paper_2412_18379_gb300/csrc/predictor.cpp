@@ -1,0 +1,518 @@
+// Start predictor runtime (Sec. 2.3, Algorithm 2): weights, the forward and
+// backward passes of training as sequences of kernels (im2col, BF16-operand
+// GEMM with FP32 accumulation, bias, ReLU, col2im), Adam, the training loop,
+// grid prediction, and the C ABI entry points of the predictor.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "cnn.h"
+
+namespace cs {
+
+NetShape::NetShape(int d) : dim(d) {
+    cin = d;
+    S0 = d == 2 ? 9 : 7;
+    n_conv = d == 2 ? 4 : 3;
+    ch = 32;
+    hidden = 256;
+    int64_t o = 0;
+    int c = cin;
+    for (int l = 0; l < n_conv; ++l) {
+        w_off.push_back(o);
+        o += int64_t(ch) * c * taps();
+        b_off.push_back(o);
+        o += ch;
+        c = ch;
+    }
+    w_off.push_back(o);
+    o += int64_t(hidden) * ch;
+    b_off.push_back(o);
+    o += hidden;
+    w_off.push_back(o);
+    o += int64_t(dim) * hidden;
+    b_off.push_back(o);
+    o += dim;
+    n_params = o;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+namespace {
+
+cs_status fail(cs_ctx *ctx, cs_status code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+#define PCHK(call)                                                                       \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ctx, CS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cs_status dalloc(cs_ctx *ctx, T **p, size_t count) {
+    if (cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T)) !=
+        cudaSuccess) {
+        *p = nullptr;
+        return fail(ctx, CS_ENOMEM, "cudaMalloc failed in the predictor");
+    }
+    return CS_OK;
+}
+
+void free_workspace(Predictor &P) {
+    for (float *p : P.col) cudaFree(p);
+    for (float *p : P.z) cudaFree(p);
+    for (float *p : P.y) cudaFree(p);
+    P.col.clear();
+    P.z.clear();
+    P.y.clear();
+    float **fs[] = {&P.z5, &P.a5, &P.out, &P.gout, &P.dcol, &P.dy0, &P.dy1, &P.da5, &P.win, &P.tgt};
+    for (float **f : fs) {
+        if (*f) cudaFree(*f);
+        *f = nullptr;
+    }
+    if (P.idx) cudaFree(P.idx);
+    P.idx = nullptr;
+    P.cap = 0;
+}
+
+cs_status ensure_workspace(cs_ctx *ctx, Predictor &P, int64_t B) {
+    if (P.cap >= B) return CS_OK;
+    free_workspace(P);
+    NetShape S(P.dim);
+    int Si = S.S0, C = S.cin;
+    int64_t max_col = 0, max_dy = 0;
+    for (int l = 0; l < S.n_conv; ++l) {
+        const int So = Si - 2;
+        const int64_t Po = S.positions(So), K = int64_t(C) * S.taps();
+        float *col, *z, *y;
+        cs_status rc;
+        if ((rc = dalloc(ctx, &col, size_t(B * Po * K))) || (rc = dalloc(ctx, &z, size_t(B * Po * S.ch))) ||
+            (rc = dalloc(ctx, &y, size_t(B * Po * S.ch))))
+            return rc;
+        P.col.push_back(col);
+        P.z.push_back(z);
+        P.y.push_back(y);
+        max_col = std::max(max_col, B * Po * K);
+        if (l > 0) max_dy = std::max(max_dy, B * S.positions(Si) * S.ch);
+        max_dy = std::max(max_dy, B * Po * S.ch);
+        Si = So;
+        C = S.ch;
+    }
+    const int64_t win = int64_t(S.cin) * S.positions(S.S0);
+    cs_status rc;
+    if ((rc = dalloc(ctx, &P.z5, size_t(B * S.hidden))) || (rc = dalloc(ctx, &P.a5, size_t(B * S.hidden))) ||
+        (rc = dalloc(ctx, &P.out, size_t(B * S.dim))) || (rc = dalloc(ctx, &P.gout, size_t(B * S.dim))) ||
+        (rc = dalloc(ctx, &P.dcol, size_t(max_col))) || (rc = dalloc(ctx, &P.dy0, size_t(max_dy))) ||
+        (rc = dalloc(ctx, &P.dy1, size_t(max_dy))) || (rc = dalloc(ctx, &P.da5, size_t(B * S.hidden))) ||
+        (rc = dalloc(ctx, &P.win, size_t(B * win))) || (rc = dalloc(ctx, &P.tgt, size_t(B * S.dim))) ||
+        (rc = dalloc(ctx, &P.idx, size_t(B))))
+        return rc;
+    P.cap = B;
+    return CS_OK;
+}
+
+// forward of B windows (device, [B][cin][S0^dim]) into P.out [B][dim]
+int forward(cs_ctx *ctx, Predictor &P, int64_t B, const float *win, cudaStream_t st) {
+    NetShape S(P.dim);
+    const int sm = ctx->sm_count;
+    int launches = 0;
+    const float *x = win;
+    bool chfirst = true;
+    int C = S.cin, Si = S.S0;
+    for (int l = 0; l < S.n_conv; ++l) {
+        const int So = Si - 2;
+        const int64_t Po = S.positions(So), K = int64_t(C) * S.taps();
+        launches += launch_im2col(P.dim, x, B, C, Si, chfirst, P.col[l], sm, st);
+        launches += launch_gemm(P.col[l], P.w + S.w_off[l], P.z[l], P.w + S.b_off[l], B * Po, S.ch,
+                                K, false, true, false, st);
+        launches += launch_relu(P.z[l], P.y[l], B * Po * S.ch, sm, st);
+        x = P.y[l];
+        chfirst = false;
+        C = S.ch;
+        Si = So;
+    }
+    const int f1 = S.n_conv, f2 = S.n_conv + 1;
+    launches += launch_gemm(x, P.w + S.w_off[f1], P.z5, P.w + S.b_off[f1], B, S.hidden, S.ch,
+                            false, true, false, st);
+    launches += launch_relu(P.z5, P.a5, B * S.hidden, sm, st);
+    launches += launch_gemm(P.a5, P.w + S.w_off[f2], P.out, P.w + S.b_off[f2], B, S.dim,
+                            S.hidden, false, true, false, st);
+    return launches;
+}
+
+// gradients of the MSE of P.out against tgt into P.g; loss added to *loss
+int backward(cs_ctx *ctx, Predictor &P, int64_t B, const float *tgt, float *loss,
+             cudaStream_t st) {
+    NetShape S(P.dim);
+    const int sm = ctx->sm_count;
+    int n = 0;
+    const int f1 = S.n_conv, f2 = S.n_conv + 1;
+    n += launch_mse_grad(P.out, tgt, B * S.dim, P.gout, loss, sm, st);
+    n += launch_gemm(P.gout, P.a5, P.g + S.w_off[f2], nullptr, S.dim, S.hidden, B, true, false,
+                     false, st);
+    n += launch_colsum(P.gout, B, S.dim, P.g + S.b_off[f2], st);
+    n += launch_gemm(P.gout, P.w + S.w_off[f2], P.da5, nullptr, B, S.hidden, S.dim, false, false,
+                     false, st);
+    n += launch_relu_back(P.z5, P.da5, B * S.hidden, sm, st);
+    const float *h4 = P.y[S.n_conv - 1];
+    n += launch_gemm(P.da5, h4, P.g + S.w_off[f1], nullptr, S.hidden, S.ch, B, true, false, false,
+                     st);
+    n += launch_colsum(P.da5, B, S.hidden, P.g + S.b_off[f1], st);
+    float *dy = P.dy0, *dnext = P.dy1;
+    n += launch_gemm(P.da5, P.w + S.w_off[f1], dy, nullptr, B, S.ch, S.hidden, false, false, false,
+                     st);
+    // conv layers, last to first; edge of layer l's input
+    std::vector<int> Sin(S.n_conv);
+    int Si = S.S0;
+    for (int l = 0; l < S.n_conv; ++l) {
+        Sin[l] = Si;
+        Si -= 2;
+    }
+    for (int l = S.n_conv - 1; l >= 0; --l) {
+        const int So = Sin[l] - 2;
+        const int C = l == 0 ? S.cin : S.ch;
+        const int64_t Po = S.positions(So), K = int64_t(C) * S.taps();
+        n += launch_relu_back(P.z[l], dy, B * Po * S.ch, sm, st);
+        n += launch_gemm(dy, P.col[l], P.g + S.w_off[l], nullptr, S.ch, K, B * Po, true, false,
+                         false, st);
+        n += launch_colsum(dy, B * Po, S.ch, P.g + S.b_off[l], st);
+        if (l > 0) {
+            n += launch_gemm(dy, P.w + S.w_off[l], P.dcol, nullptr, B * Po, K, S.ch, false, false,
+                             false, st);
+            n += launch_col2im(P.dim, P.dcol, B, S.ch, Sin[l], dnext, sm, st);
+            std::swap(dy, dnext);
+        }
+    }
+    return n;
+}
+
+Predictor *get_pred(cs_ctx *ctx, int dim) {
+    if (dim != 2 && dim != 3) return nullptr;
+    return &ctx->pred[dim - 2];
+}
+
+uint64_t splitmix(uint64_t &s) {
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
+    auto it = ctx->meshes.find(id);
+    return it == ctx->meshes.end() ? nullptr : it->second;
+}
+
+cs_status ensure_mesh_grid(cs_ctx *ctx, cs::Mesh *m) {
+    const size_t n = size_t(m->d.n_asg) * m->d.dim;
+    if (!m->grid_u) {
+        cs_status rc = dalloc(ctx, &m->grid_u, n);
+        if (rc) return rc;
+        m->allocs.push_back(m->grid_u);
+    }
+    if (!m->grid_dhat) {
+        cs_status rc = dalloc(ctx, &m->grid_dhat, n);
+        if (rc) return rc;
+        m->allocs.push_back(m->grid_dhat);
+    }
+    return CS_OK;
+}
+
+}  // namespace
+
+namespace cs {
+
+void predictor_release(Predictor &P) {
+    free_workspace(P);
+    float **fs[] = {&P.w, &P.g, &P.m, &P.v, &P.loss};
+    for (float **f : fs) {
+        if (*f) cudaFree(*f);
+        *f = nullptr;
+    }
+    P.loaded = false;
+}
+
+// prediction of every ASG cell of mesh m from its stored grid velocity
+cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStream_t st) {
+    Predictor *P = get_pred(ctx, m->d.dim);
+    if (!P || !P->loaded) return fail(ctx, CS_ENOPRED, "no predictor loaded for this dimension");
+    if (!m->grid_u_valid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
+    const int64_t chunk = 8192;
+    cs_status rc = ensure_workspace(ctx, *P, chunk);
+    if (rc) return rc;
+    const int D = m->d.dim;
+    float scale[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) scale[k] = float(dt / m->d.sa[k]);
+    for (int64_t c0 = 0; c0 < m->d.n_asg; c0 += chunk) {
+        const int64_t B = std::min(chunk, m->d.n_asg - c0);
+        ctx->launches += launch_windows(m->d, m->grid_u, nullptr, c0, B, scale, P->win,
+                                        ctx->sm_count, st);
+        ctx->launches += forward(ctx, *P, B, P->win, st);
+        PCHK(cudaMemcpyAsync(dhat + c0 * D, P->out, size_t(B) * D * sizeof(float),
+                             cudaMemcpyDeviceToDevice, st));
+    }
+    return CS_OK;
+}
+
+cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt,
+                      cudaStream_t st, const float **dhat_out) {
+    cs_status rc = ensure_mesh_grid(ctx, m);
+    if (rc) return rc;
+    if (u_nodal) {
+        const int ev = ctx->prof.begin(CS_STAGE_RESAMPLE, st);
+        ctx->launches += launch_resample(m->d, u_nodal, m->grid_u, ctx->sm_count, st);
+        ctx->prof.end(ev, st);
+        m->grid_u_valid = true;
+    }
+    const int ev = ctx->prof.begin(CS_STAGE_CNN, st);
+    rc = predict_grid(ctx, m, dt, m->grid_dhat, st);
+    ctx->prof.end(ev, st);
+    if (rc) return rc;
+    *dhat_out = m->grid_dhat;
+    return CS_OK;
+}
+
+}  // namespace cs
+
+extern "C" {
+
+cs_status cs_predictor_precision(cs_ctx *ctx, int bf16) {
+    if (!ctx) return CS_EINVAL;
+    set_gemm_bf16(bf16 != 0);
+    return CS_OK;
+}
+
+int64_t cs_predictor_size(int dim) {
+    if (dim != 2 && dim != 3) return 0;
+    return NetShape(dim).n_params;
+}
+
+cs_status cs_predictor_load(cs_ctx *ctx, int dim, const float *weights, int64_t n) {
+    if (!ctx) return CS_EINVAL;
+    Predictor *P = get_pred(ctx, dim);
+    if (!P || !weights || n != cs_predictor_size(dim))
+        return fail(ctx, CS_EINVAL, "cs_predictor_load: bad dim or size (expected " +
+                                        std::to_string(cs_predictor_size(dim)) + " floats)");
+    PCHK(cudaSetDevice(ctx->device));
+    predictor_release(*P);
+    P->dim = dim;
+    P->n = n;
+    cs_status rc;
+    if ((rc = dalloc(ctx, &P->w, size_t(n))) || (rc = dalloc(ctx, &P->g, size_t(n))) ||
+        (rc = dalloc(ctx, &P->m, size_t(n))) || (rc = dalloc(ctx, &P->v, size_t(n))) ||
+        (rc = dalloc(ctx, &P->loss, 1))) {
+        predictor_release(*P);
+        return rc;
+    }
+    PCHK(cudaMemcpy(P->w, weights, size_t(n) * sizeof(float), cudaMemcpyHostToDevice));
+    PCHK(cudaMemset(P->m, 0, size_t(n) * sizeof(float)));
+    PCHK(cudaMemset(P->v, 0, size_t(n) * sizeof(float)));
+    P->t = 0;
+    P->loaded = true;
+    return CS_OK;
+}
+
+cs_status cs_predictor_save(cs_ctx *ctx, int dim, float *out, int64_t n) {
+    if (!ctx) return CS_EINVAL;
+    Predictor *P = get_pred(ctx, dim);
+    if (!P || !out || n != cs_predictor_size(dim))
+        return fail(ctx, CS_EINVAL, "cs_predictor_save: bad dim or size");
+    if (!P->loaded) return fail(ctx, CS_ENOPRED, "cs_predictor_save: no predictor loaded");
+    PCHK(cudaSetDevice(ctx->device));
+    PCHK(cudaDeviceSynchronize());
+    PCHK(cudaMemcpy(out, P->w, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal, float *grid_out,
+                           void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_grid_velocity: unknown mesh id");
+    if (!u_nodal) return fail(ctx, CS_EINVAL, "cs_grid_velocity: null velocity");
+    PCHK(cudaSetDevice(ctx->device));
+    float *dst = grid_out;
+    if (!dst) {
+        cs_status rc = ensure_mesh_grid(ctx, m);
+        if (rc) return rc;
+        dst = m->grid_u;
+        m->grid_u_valid = true;
+    }
+    ctx->launches += launch_resample(m->d, u_nodal, dst, ctx->sm_count,
+                                     static_cast<cudaStream_t>(stream));
+    PCHK(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_windows(cs_ctx *ctx, int32_t mesh_id, const float *grid, double dt,
+                     const int64_t *cells, int64_t B, float *out, void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_windows: unknown mesh id");
+    if (B < 0 || !out) return fail(ctx, CS_EINVAL, "cs_windows: bad size or null output");
+    if (!grid && !m->grid_u_valid) return fail(ctx, CS_EINVAL, "cs_windows: no grid velocity");
+    if (B == 0) return CS_OK;
+    PCHK(cudaSetDevice(ctx->device));
+    float scale[3] = {0, 0, 0};
+    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / m->d.sa[k]);
+    ctx->launches += launch_windows(m->d, grid ? grid : m->grid_u, cells, 0, B, scale, out,
+                                    ctx->sm_count, static_cast<cudaStream_t>(stream));
+    PCHK(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_predictor_forward(cs_ctx *ctx, int dim, int64_t B, const float *windows,
+                               float *dhat_out) {
+    if (!ctx) return CS_EINVAL;
+    Predictor *P = get_pred(ctx, dim);
+    if (!P || B < 0 || (B > 0 && (!windows || !dhat_out)))
+        return fail(ctx, CS_EINVAL, "cs_predictor_forward: bad arguments");
+    if (!P->loaded) return fail(ctx, CS_ENOPRED, "cs_predictor_forward: no predictor loaded");
+    PCHK(cudaSetDevice(ctx->device));
+    const int64_t chunk = 8192;
+    cs_status rc = ensure_workspace(ctx, *P, std::min<int64_t>(std::max<int64_t>(B, 1), chunk));
+    if (rc) return rc;
+    NetShape S(dim);
+    const int64_t row = int64_t(S.cin) * S.positions(S.S0);
+    for (int64_t b0 = 0; b0 < B; b0 += P->cap) {
+        const int64_t nb = std::min(P->cap, B - b0);
+        ctx->launches += forward(ctx, *P, nb, windows + b0 * row, nullptr);
+        PCHK(cudaMemcpyAsync(dhat_out + b0 * dim, P->out, size_t(nb) * dim * sizeof(float),
+                             cudaMemcpyDeviceToDevice, nullptr));
+    }
+    PCHK(cudaDeviceSynchronize());
+    return CS_OK;
+}
+
+cs_status cs_predict(cs_ctx *ctx, int32_t mesh_id, double dt, float *dhat_out, void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_predict: unknown mesh id");
+    PCHK(cudaSetDevice(ctx->device));
+    cs_status rc = ensure_mesh_grid(ctx, m);
+    if (rc) return rc;
+    rc = predict_grid(ctx, m, dt, dhat_out ? dhat_out : m->grid_dhat,
+                      static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    PCHK(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_predictor_train(cs_ctx *ctx, int dim, const float *windows, const float *targets,
+                             int64_t N, int64_t batch, int64_t steps, float lr, uint64_t seed,
+                             float *loss_out) {
+    if (!ctx) return CS_EINVAL;
+    Predictor *P = get_pred(ctx, dim);
+    if (!P || !windows || !targets || N < 1 || batch < 1 || steps < 0 || !(lr > 0.f))
+        return fail(ctx, CS_EINVAL, "cs_predictor_train: bad arguments");
+    if (!P->loaded) return fail(ctx, CS_ENOPRED, "cs_predictor_train: no predictor loaded");
+    PCHK(cudaSetDevice(ctx->device));
+    const int64_t B = std::min(batch, N);
+    cs_status rc = ensure_workspace(ctx, *P, B);
+    if (rc) return rc;
+    NetShape S(dim);
+    const int64_t row = int64_t(S.cin) * S.positions(S.S0);
+    float *losses = nullptr;
+    if ((rc = dalloc(ctx, &losses, size_t(std::max<int64_t>(steps, 1))))) return rc;
+    PCHK(cudaMemset(losses, 0, size_t(std::max<int64_t>(steps, 1)) * sizeof(float)));
+    std::vector<int64_t> perm(static_cast<size_t>(N));
+    for (int64_t i = 0; i < N; ++i) perm[i] = i;
+    uint64_t rs = seed;
+    int64_t pos = N;   // force a shuffle at the first step
+    std::vector<int64_t> idx(static_cast<size_t>(B));
+    cs_status out = CS_OK;
+    for (int64_t s = 0; s < steps; ++s) {
+        for (int64_t b = 0; b < B; ++b) {
+            if (pos >= N) {   // new epoch: Fisher-Yates shuffle
+                for (int64_t i = N - 1; i > 0; --i) std::swap(perm[i], perm[splitmix(rs) % (i + 1)]);
+                pos = 0;
+            }
+            idx[b] = perm[pos++];
+        }
+        if (cudaMemcpy(P->idx, idx.data(), size_t(B) * sizeof(int64_t), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            out = fail(ctx, CS_ECUDA, "cs_predictor_train: index copy");
+            break;
+        }
+        ctx->launches += launch_gather_rows(windows, row, P->idx, B, P->win, ctx->sm_count, nullptr);
+        ctx->launches += launch_gather_rows(targets, dim, P->idx, B, P->tgt, ctx->sm_count, nullptr);
+        ctx->launches += forward(ctx, *P, B, P->win, nullptr);
+        ctx->launches += backward(ctx, *P, B, P->tgt, losses + s, nullptr);
+        P->t += 1;
+        ctx->launches += launch_adam(P->w, P->g, P->m, P->v, P->n, lr, P->t, ctx->sm_count, nullptr);
+    }
+    if (out == CS_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess && loss_out && steps > 0)
+            e = cudaMemcpy(loss_out, losses, size_t(steps) * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) out = fail(ctx, CS_ECUDA, std::string("cs_predictor_train: ") +
+                                                            cudaGetErrorString(e));
+    }
+    cudaFree(losses);
+    return out;
+}
+
+cs_status cs_training_pairs(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                            const double *u, double dt, float *windows_out, float *targets_out,
+                            int64_t *cells_out, void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_training_pairs: unknown mesh id");
+    if (n < 0 || (n > 0 && (!x || !u || !windows_out || !targets_out || !cells_out)))
+        return fail(ctx, CS_EINVAL, "cs_training_pairs: bad arguments");
+    if (!m->grid_u_valid) return fail(ctx, CS_EINVAL, "cs_training_pairs: no grid velocity");
+    if (n == 0) return CS_OK;
+    PCHK(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ctx->launches += launch_pairs(m->d, n, x, u, dt, cells_out, targets_out, ctx->sm_count, st);
+    float scale[3] = {0, 0, 0};
+    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / m->d.sa[k]);
+    ctx->launches += launch_windows(m->d, m->grid_u, cells_out, 0, n, scale, windows_out,
+                                    ctx->sm_count, st);
+    PCHK(cudaGetLastError());
+    return CS_OK;
+}
+
+cs_status cs_predictor_grad(cs_ctx *ctx, int dim, int64_t B, const float *windows,
+                            const float *targets, float *grad_out, float *loss_out) {
+    if (!ctx) return CS_EINVAL;
+    Predictor *P = get_pred(ctx, dim);
+    if (!P || B < 1 || !windows || !targets || !grad_out)
+        return fail(ctx, CS_EINVAL, "cs_predictor_grad: bad arguments");
+    if (!P->loaded) return fail(ctx, CS_ENOPRED, "cs_predictor_grad: no predictor loaded");
+    PCHK(cudaSetDevice(ctx->device));
+    cs_status rc = ensure_workspace(ctx, *P, B);
+    if (rc) return rc;
+    PCHK(cudaMemset(P->loss, 0, sizeof(float)));
+    ctx->launches += forward(ctx, *P, B, windows, nullptr);
+    ctx->launches += backward(ctx, *P, B, targets, P->loss, nullptr);
+    PCHK(cudaDeviceSynchronize());
+    PCHK(cudaMemcpy(grad_out, P->g, size_t(P->n) * sizeof(float), cudaMemcpyDeviceToDevice));
+    if (loss_out) PCHK(cudaMemcpy(loss_out, P->loss, sizeof(float), cudaMemcpyDeviceToHost));
+    return CS_OK;
+}
+
+cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, const double *u,
+                        double dt, const int32_t *start, const float *dhat, int32_t *host_out,
+                        int32_t *path_len_out, uint8_t *status_out, int32_t *start_out,
+                        void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_dhat: unknown mesh id");
+    if (!dhat && !m->grid_dhat) return fail(ctx, CS_EINVAL, "cs_track_dhat: no displacement grid");
+    return cs_track_impl(ctx, m, n, x, u, dt, start, CS_CNN_SNS, dhat ? dhat : m->grid_dhat,
+                         host_out, path_len_out, status_out, start_out,
+                         static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -27,41 +27,138 @@ __device__ __forceinline__ int32_t exact_search_warp(const DevMesh &m, const dou
     for (int k = 0; k < D; ++k)
         outside = outside || !(xp[k] >= m.lo[k] - m.margin) || !(xp[k] <= m.hi[k] + m.margin);
     if (outside) return -1;
-    const int64_t c = grid_cell<D>(xp, m.lo, m.sb, m.gb);
+    float xh[D], xl[D];
+    #pragma unroll
+    for (int k = 0; k < D; ++k) split_double(xp[k], xh[k], xl[k]);
+    const int64_t c = grid_cell_cert<D>(xp, xh, xl, m, m.sb, m.inv_sb, m.gb);
     const int32_t b0 = __ldg(m.bstart + c), b1 = __ldg(m.bstart + c + 1);
     unsigned best = 0xffffffffu;
     for (int32_t t = b0 + lane; t < b1; t += 32) {
         const int32_t el = __ldg(m.bitems + t);
-        double lam[D + 1];
-        bary64(rx, el, xp, lam);
-        bool inside = true;
+        WalkE<D> e;
+        load_walk(rw, el, e);
+        // containment certified in FP32 when possible (see walk_common.cuh),
+        // else decided by the FP64 coordinates
+        float lf[D + 1], T[D + 1];
+        bary32<D>(e, xh, xl, lf, T);
+        bool cin = true, cout = false;
         #pragma unroll
-        for (int i = 0; i <= D; ++i) inside = inside && (lam[i] >= -CS_EPS);
-        if (inside) best = min(best, unsigned(__ldg(&rw[el].uid)));
+        for (int i = 0; i <= D; ++i) {
+            cin = cin && (lf[i] - T[i] >= kNegEpsIn);
+            cout = cout || (lf[i] + T[i] < kNegEpsOut);
+        }
+        bool inside = cin;
+        if (!cin && !cout) {
+            double lam[D + 1];
+            bary64(rx, el, xp, lam);
+            inside = true;
+            #pragma unroll
+            for (int i = 0; i <= D; ++i) inside = inside && (lam[i] >= -CS_EPS);
+        }
+        if (inside) best = min(best, unsigned(e.uid));
     }
     best = __reduce_min_sync(kFull, best);
     return best == 0xffffffffu ? -1 : int32_t(best);
 }
 
+// Monotone integer key of a non-NaN double: a < b <=> key(a) < key(b), with
+// +0 and -0 equal (exact comparisons on the integer pipe).
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    if ((b << 1) == 0) return 0x8000000000000000ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Each lane prepares one listed particle (departure point, box test, bucket
+// range) so the FP64 work runs with full warps; then the warp searches the
+// candidates of each remaining particle together.
 template <int D>
 __global__ void __launch_bounds__(256) fallback_kernel(const DevMesh m, const TrackArgs a,
                                                        const int32_t *fb_count,
                                                        const int32_t *fb_list) {
+    using WR = typename Recs<D>::W;
+    using XR = typename Recs<D>::X;
+    const WR *__restrict__ rw = static_cast<const WR *>(m.recw);
+    const XR *__restrict__ rx = static_cast<const XR *>(m.recx);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     const int32_t count = *fb_count;
-    for (int64_t w = warp; w < count; w += nwarps) {
-        const int64_t p = fb_list[w];
+    // particles per warp: spread a short list over many warps (the searches
+    // of one warp run one after another), batch a long one (full-lane FP64)
+    const int per = int(min(int64_t(32), max(int64_t(1), (count + nwarps - 1) / nwarps)));
+    for (int64_t base = warp * per; base < count; base += nwarps * per) {
+        const bool valid = lane < per && base + lane < count;
+        int64_t p = 0;
         double xp[D];
-        #pragma unroll
-        for (int k = 0; k < D; ++k)
-            xp[k] = __dsub_rn(__ldg(a.x + p * D + k), __dmul_rn(__ldg(a.u + p * D + k), a.dt));
-        const int32_t h = exact_search_warp<D>(m, xp, lane);
-        if (lane == 0) {
-            const uint8_t st = a.status[p];
-            a.host[p] = h;
-            if (st != CS_FOUND) a.status[p] = h >= 0 ? CS_FOUND_VIA_FALLBACK : CS_OUTSIDE;
+        float xh[D], xl[D];
+        int32_t b0 = 0, b1 = 0;
+        bool work = false;
+        if (valid) {
+            p = fb_list[base + lane];
+            bool outside = false;
+            #pragma unroll
+            for (int k = 0; k < D; ++k) {
+                xp[k] = __dsub_rn(__ldg(a.x + p * D + k),
+                                  __dmul_rn(__ldg(a.u + p * D + k), a.dt));
+                const unsigned long long key = order_key(xp[k]);
+                outside = outside || key < order_key(m.lo_m[k]) || key > order_key(m.hi_m[k]);
+                split_double(xp[k], xh[k], xl[k]);
+            }
+            if (outside) {
+                // no element's grown box reaches x_p: the host is -1
+                a.host[p] = -1;
+                if (a.status[p] != CS_FOUND) a.status[p] = CS_OUTSIDE;
+            } else {
+                const int64_t c = grid_cell_cert<D>(xp, xh, xl, m, m.sb, m.inv_sb, m.gb);
+                b0 = __ldg(m.bstart + c);
+                b1 = __ldg(m.bstart + c + 1);
+                work = true;
+            }
+        }
+        unsigned todo = __ballot_sync(kFull, work);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            double q[D];
+            float qh[D], ql[D];
+            #pragma unroll
+            for (int k = 0; k < D; ++k) {
+                q[k] = __shfl_sync(kFull, xp[k], j);
+                qh[k] = __shfl_sync(kFull, xh[k], j);
+                ql[k] = __shfl_sync(kFull, xl[k], j);
+            }
+            const int32_t t0 = __shfl_sync(kFull, b0, j), t1 = __shfl_sync(kFull, b1, j);
+            unsigned best = 0xffffffffu;
+            for (int32_t t = t0 + lane; t < t1; t += 32) {
+                const int32_t el = __ldg(m.bitems + t);
+                WalkE<D> e;
+                load_walk(rw, el, e);
+                float lf[D + 1], T[D + 1];
+                bary32<D>(e, qh, ql, lf, T);
+                bool cin = true, cout = false;
+                #pragma unroll
+                for (int i = 0; i <= D; ++i) {
+                    cin = cin && (lf[i] - T[i] >= kNegEpsIn);
+                    cout = cout || (lf[i] + T[i] < kNegEpsOut);
+                }
+                bool inside = cin;
+                if (!cin && !cout) {
+                    double lam[D + 1];
+                    bary64(rx, el, q, lam);
+                    inside = true;
+                    #pragma unroll
+                    for (int i = 0; i <= D; ++i) inside = inside && (lam[i] >= -CS_EPS);
+                }
+                if (inside) best = min(best, unsigned(e.uid));
+            }
+            best = __reduce_min_sync(kFull, best);
+            if (lane == j) {
+                const int32_t h = best == 0xffffffffu ? -1 : int32_t(best);
+                a.host[p] = h;
+                if (a.status[p] != CS_FOUND)
+                    a.status[p] = h >= 0 ? CS_FOUND_VIA_FALLBACK : CS_OUTSIDE;
+            }
         }
     }
 }
@@ -118,7 +215,8 @@ __global__ void __launch_bounds__(256) stats_kernel(int64_t n, const int32_t *pa
 
 int launch_fallback(const DevMesh &m, const TrackArgs &a, const int32_t *count,
                     const int32_t *list, int sm_count, cudaStream_t st, Profiler *prof) {
-    const int grid = sm_count * 4;
+    // one warp per listed particle; warps beyond the count return at once
+    const int grid = int(std::min<int64_t>(int64_t(sm_count) * 16, (a.n + 7) / 8));
     const int ev = prof ? prof->begin(CS_STAGE_FALLBACK, st) : -1;
     if (m.dim == 2)
         fallback_kernel<2><<<grid, 256, 0, st>>>(m, a, count, list);

@@ -103,7 +103,7 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) walk_kernel(const DevMesh m, const TrackArgs a,
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh m, const TrackArgs a,
                                                    int32_t *cursor, int32_t *fb_count,
                                                    int32_t *fb_list) {
     using WR = typename Recs<D>::W;

@@ -165,6 +165,20 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
     lo = __fmul_rn(sign ? -low : low, __uint_as_float(unsigned(E + 75) << 23));
 }
 
+// x truncated to float from its bit pattern (integer pipe only); magnitudes
+// below 2^-126 become 0, above the float range +-inf, NaN stays NaN.
+__device__ __forceinline__ float trunc_to_float(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
+    const int E = int((b >> 52) & 0x7ff) - 1023;
+    if (E < -126) return __uint_as_float(sign);
+    if (E > 127) {
+        const bool nan = E == 1024 && (b & 0xfffffffffffffull) != 0;
+        return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
+    }
+    return __uint_as_float(sign | (unsigned(E + 127) << 23) | unsigned((b >> 29) & 0x7fffffu));
+}
+
 __device__ __forceinline__ bool finite_bits(double x) {
     return (static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7ff0000000000000ull) !=
            0x7ff0000000000000ull;
@@ -188,27 +202,37 @@ __device__ __forceinline__ int64_t grid_cell(const double *x, const double *lo, 
 }
 
 // Same cell, certified in FP32 per axis when the rounding bound cannot move
-// the quotient across an integer; otherwise the FP64 formula.
+// the quotient across an integer; otherwise the FP64 formula. inv_s is 1/s
+// rounded to float.
 template <int D>
-__device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh, const float *xl,
-                                               const DevMesh &m) {
+__device__ __forceinline__ int64_t grid_cell_cert(const double *x, const float *xh,
+                                                  const float *xl, const DevMesh &m,
+                                                  const double *s, const float *inv_s,
+                                                  const int32_t *g) {
     int64_t c = 0;
     #pragma unroll
     for (int k = D - 1; k >= 0; --k) {
         const float df = (xh[k] - m.lo_h[k]) + (xl[k] - m.lo_l[k]);
         const float ed = delta_bound(df, xh[k], m.lo_h[k]);
-        const float q = df * m.inv_sa[k];
-        const float B = fmaf(2.0f * ed, m.inv_sa[k], fmaf(k8U, fabsf(q), kTiny));
+        const float q = df * inv_s[k];
+        const float B = fmaf(2.0f * ed, inv_s[k], fmaf(k8U, fabsf(q), kTiny));
         const float a = floorf(q - B), b = floorf(q + B);
         int64_t i;
         if (a == b && fabsf(q) < 4.0e6f) {
-            i = a < 0.f ? 0 : (a > float(m.ga[k] - 1) ? m.ga[k] - 1 : int64_t(a));
+            i = a < 0.f ? 0 : (a > float(g[k] - 1) ? g[k] - 1 : int64_t(a));
         } else {
-            i = cell_axis64(x[k], m.lo[k], m.sa[k], m.ga[k]);
+            i = cell_axis64(x[k], m.lo[k], s[k], g[k]);
         }
-        c = c * m.ga[k] + i;
+        c = c * g[k] + i;
     }
     return c;
+}
+
+// ASG cell of a point (seed grid, CNN grid)
+template <int D>
+__device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh, const float *xl,
+                                               const DevMesh &m) {
+    return grid_cell_cert<D>(x, xh, xl, m, m.sa, m.inv_sa, m.ga);
 }
 
 // Warp-aggregated append of particle p to the exact-search list.

@@ -1,0 +1,241 @@
+"""The learned start predictor on the GPU against the FP64 oracle.
+
+Tolerances. The predictor computes with BF16 operands (8 significant bits,
+relative rounding 2^-9) and FP32 accumulation. Each of the six layers rounds
+its inputs and weights once, so the output carries a relative error of order
+6 * 2 * 2^-9 ~ 2.3e-2 of its scale; tests allow 4e-2 of the output's largest
+magnitude. The grid velocity is evaluated in FP32: the cell-centre offsets
+carry ~1e-7 absolute error, the barycentric coordinates ~1e-7 / h relative,
+so 5e-4 of the largest velocity covers h >= 1e-3 with margin. Windows are
+one FP32 product: 1e-6 relative. Start elements of CNN-SNS depend on the
+BF16 prediction and may differ from the FP64 oracle's where the predicted
+point lies within the prediction error of an ASG cell boundary; hosts never do.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cnn
+from workloads import make_case
+from workloads.weights import init_weights
+from workloads.fields import fourier_modes_2d, dt_for_cfl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2412_18379_gb300 as cs
+    from paper_2412_18379_gb300 import build
+    build.build()
+    c = cs.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _oracle_grid_u(om, u_nodal):
+    cen = oracle.grid_centres(om.lo, om.hi, om.grid)
+    return oracle.p1_interpolate(om.conn, om.v0, om.M, u_nodal, cen, om.seed)
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 101}), ("abc3d", {"n_side": 13})])
+def test_grid_velocity_matches_oracle(ctx, name, kw):
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    U = torch.empty((int(np.prod(g)), c.dim), dtype=torch.float32, device="cuda")
+    ctx.grid_velocity(mesh, _dev(c.u), out=U)
+    torch.cuda.synchronize()
+    ref = _oracle_grid_u(om, c.u)
+    err = np.abs(U.cpu().numpy() - ref).max()
+    assert err <= 5e-4 * np.abs(c.u).max(), err
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 61}), ("abc3d", {"n_side": 11})])
+def test_windows_match_oracle(ctx, name, kw):
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    Uref = _oracle_grid_u(om, c.u)
+    rng = np.random.default_rng(4)
+    cells = rng.integers(0, Uref.shape[0], size=300).astype(np.int64)
+    cells[:4] = [0, Uref.shape[0] - 1, g[0] - 1, g[0]]      # corners and edges
+    w = ctx.windows(mesh, c.dt, cells=_dev(cells), grid=_dev(Uref.astype(np.float32)))
+    torch.cuda.synchronize()
+    scale = c.dt / ((om.hi - om.lo) / om.grid)
+    ref = cnn.windows(Uref.astype(np.float32).reshape(tuple(g[::-1]) + (c.dim,)), cells, c.dim,
+                      scale)
+    assert np.allclose(w.cpu().numpy(), ref, rtol=1e-6, atol=1e-7 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_and_gradient_match_oracle(ctx, dim, bf16):
+    """FP32 operands: forward and every layer's gradient within 1e-4 of the
+    FP64 oracle (FP32 accumulation over at most 4096 terms). BF16 operands
+    (the training arithmetic): forward within 4e-2 of the output scale; the
+    gradient of layer l passes through 2 * (L - l) BF16-rounded GEMM operands
+    and through the ReLU gates of a forward pass that is itself off by ~1e-2,
+    so the deepest layer is allowed 1.5e-1 relative error, others 5e-2."""
+    rng = np.random.default_rng(10 + dim)
+    flat = init_weights(dim, 7).astype(np.float64)
+    flat += 0.02 * rng.standard_normal(flat.size)
+    flat = flat.astype(np.float32)
+    ctx.predictor_precision(bf16)
+    try:
+        ctx.load_predictor(dim, flat)
+        S = cnn.patch_size(dim)
+        B = 96
+        win = rng.standard_normal((B, dim) + (S,) * dim).astype(np.float32)
+        tgt = rng.standard_normal((B, dim)).astype(np.float32)
+        params = cnn.unpack(dim, flat)
+        ref, acts = cnn.forward(dim, params, win.astype(np.float64), keep=True)
+        out = ctx.predictor_forward(dim, _dev(win)).cpu().numpy()
+        ftol = 4e-2 if bf16 else 1e-5
+        assert np.abs(out - ref).max() <= ftol * np.abs(ref).max()
+        # gradients of the MSE against the FP64 backward, layer by layer
+        gref = cnn.pack(cnn.backward(dim, params, acts, ref, tgt.astype(np.float64)))
+        g, loss = ctx.predictor_grad(dim, _dev(win), _dev(tgt))
+        g = g.cpu().numpy().astype(np.float64)
+        assert abs(loss - cnn.mse(ref, tgt)) <= ftol * cnn.mse(ref, tgt)
+        o = 0
+        for li, (_, ws, bs) in enumerate(cnn.spec(dim)):
+            n = int(np.prod(ws)) + int(np.prod(bs))
+            a, b = g[o:o + n], gref[o:o + n]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            tol = (1.5e-1 if li == 0 else 5e-2) if bf16 else 1e-4
+            assert rel <= tol, (ws, rel)
+            o += n
+    finally:
+        ctx.predictor_precision(True)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adam_step_on_device(ctx, dim):
+    """One training step over the whole batch: the update is Adam's first
+    step -lr g/(|g| + eps) of the device's own gradient on the same pairs."""
+    rng = np.random.default_rng(20 + dim)
+    flat = init_weights(dim, 8)
+    ctx.load_predictor(dim, flat)
+    S = cnn.patch_size(dim)
+    B = 64
+    win = _dev(rng.standard_normal((B, dim) + (S,) * dim).astype(np.float32))
+    tgt = _dev(rng.standard_normal((B, dim)).astype(np.float32))
+    g, _ = ctx.predictor_grad(dim, win, tgt)
+    g = g.cpu().numpy().astype(np.float64)
+    losses = ctx.train(dim, win, tgt, batch=B, steps=1, lr=1e-3, seed=3)
+    w1 = ctx.save_predictor(dim).astype(np.float64)
+    want = flat.astype(np.float64) - 1e-3 * g / (np.abs(g) + 1e-8)
+    big = np.abs(g) > 1e-6
+    assert np.allclose(w1[big], want[big], rtol=0, atol=2e-6)
+    assert np.all(np.abs(w1[~big] - flat[~big]) <= 1e-3 + 1e-6)
+    assert losses.shape == (1,) and np.isfinite(losses[0])
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 121, "cfl": 8}),
+                                     ("abc3d", {"n_side": 15, "cfl": 8})])
+def test_track_with_given_displacements(ctx, name, kw):
+    """Algorithm 2's start rule with a displacement grid drawn from a seeded
+    generator: starts, paths, hosts and statuses bit for bit."""
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    rng = np.random.default_rng(6)
+    dhat = rng.uniform(-12, 12, size=(int(np.prod(g)), c.dim)).astype(np.float32)
+    out = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=_dev(dhat), start_out=True)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.cells(c.x)])
+    start = np.where(want["path_len"] > 0, want["start"], -1)
+    for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
+                   ("status", want["status"]), ("start", start)):
+        assert np.array_equal(got[k], ref), k
+
+
+def _oracle_cnn_dhat(om, case, flat):
+    """Oracle of the predictor stage: FP64 grid velocity, windows at the
+    particles' cells, FP64 forward."""
+    U = _oracle_grid_u(om, case.u)
+    cells = om.cells(case.x)
+    scale = case.dt / ((om.hi - om.lo) / om.grid)
+    G = tuple(int(v) for v in om.grid[::-1])
+    win = cnn.windows(U.reshape(G + (case.dim,)), cells, case.dim, scale)
+    return cnn.forward(case.dim, cnn.unpack(case.dim, flat), win)
+
+
+def test_cnn_sns_matches_oracle(ctx):
+    import torch
+    c = make_case("tg2d", n_side=81, cfl=8)
+    flat = init_weights(2, 12)
+    o = cnn.spec(2)
+    fc2 = sum(int(np.prod(w)) + int(np.prod(b)) for _, w, b in o[:-1])
+    flat[fc2:] *= 0.25          # predictions of a few cells, like a trained net
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    out = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn", start_out=True)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    dref = _oracle_cnn_dhat(om, c, flat)
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dref)
+    plain = om.track(c.x, c.u, c.dt, mode="sns")
+    assert np.array_equal(got["host"], want["host"])
+    assert np.array_equal(got["host"], plain["host"])          # SNS == CNN-SNS hosts
+    assert np.array_equal(got["status"] == 1, want["status"] == 1)
+    # where the oracle's predicted point is farther from every ASG cell
+    # boundary than the BF16 error bound, the start element must agree
+    s = (om.hi - om.lo) / om.grid
+    frac = (c.x - om.lo) / s + dref
+    dist = np.abs(frac - np.round(frac)).min(axis=1)
+    safe = dist > 4e-2 * np.abs(dref).max()
+    assert safe.mean() > 0.5
+    assert np.array_equal(got["start"][safe], want["start"][safe])
+    same = got["start"] == want["start"]
+    assert np.array_equal(got["path_len"][same], want["path_len"][same])
+
+
+def test_training_gains_over_plain_sns(ctx):
+    """Pairs from plain SNS on random 8-mode fields, a short training run on
+    the GPU, then on a held-out field CNN-SNS must walk shorter paths than
+    plain SNS at CFL 8 while returning the same hosts."""
+    import torch
+    c = make_case("modes2d", n_side=101, cfl=8)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    ctx.load_predictor(2, init_weights(2, 0))
+    rng = np.random.default_rng(42)
+    x = _dev(c.x)
+    wins, tgts = [], []
+    for s in range(8):
+        u = fourier_modes_2d(c.xyz, 100 + s)
+        dt = dt_for_cfl(u, c.h, rng.uniform(2, 16))
+        ud = _dev(u)
+        ctx.grid_velocity(mesh, ud)
+        w, t, _ = ctx.training_pairs(mesh, x, ud, dt)
+        wins.append(w)
+        tgts.append(t)
+    W = torch.cat(wins).contiguous()
+    T = torch.cat(tgts).contiguous()
+    losses = ctx.train(2, W, T, batch=1024, steps=400, lr=1e-3, seed=1)
+    assert losses[-20:].mean() < 0.1 * losses[:5].mean(), (losses[:5], losses[-20:])
+    u = fourier_modes_2d(c.xyz, 900)
+    dt = dt_for_cfl(u, c.h, 8.0)
+    ud = _dev(u)
+    sns = ctx.track(mesh, x, ud, dt, mode="sns")
+    cnn_out = ctx.track(mesh, x, ud, dt, mode="cnn")
+    torch.cuda.synchronize()
+    assert torch.equal(sns["host"], cnn_out["host"])
+    m_sns = sns["path_len"].double().mean().item()
+    m_cnn = cnn_out["path_len"].double().mean().item()
+    assert m_cnn < 0.6 * m_sns, (m_sns, m_cnn)

@@ -205,3 +205,15 @@ def test_full_size_tg2d_parity(ctx):
         want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode=mode))
         _compare(got, want, "full tg2d " + mode)
     mesh.release()
+
+
+def test_full_size_abc3d_parity(ctx):
+    """The 101^3 Kuhn cube (6.0M tetrahedra) with ABC flow at CFL 8, every
+    particle, plain SNS."""
+    c = make_case("abc3d", cfl=8)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    got = _run(ctx, mesh, c, mode="sns")
+    want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode="sns"))
+    _compare(got, want, "full abc3d sns")
+    mesh.release()
