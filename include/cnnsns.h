@@ -205,6 +205,15 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double
 /* Arithmetic: BF16 operands, FP32 accumulation, FP32 master weights.       */
 /* ------------------------------------------------------------------------ */
 
+/* Engine of grid prediction (cs_predict, CS_CNN_SNS): 1 (default) = the fused
+ * tensor-core kernel (tcgen05, 2-D predictor), 0 = per-window GEMMs on CUDA
+ * cores (both dims; the 3-D predictor always uses it). */
+cs_status cs_predictor_engine(cs_ctx *ctx, int engine);
+
+/* Synchronise the device and report whether a bounded device-side wait gave
+ * up since the last call (CS_EDEVICE, message in cs_last_error) or CS_OK. */
+cs_status cs_device_status(cs_ctx *ctx);
+
 /* Operand precision of the training and window-forward GEMMs: bf16 != 0 (the
  * default) rounds operands to BF16; 0 keeps FP32 operands, for accuracy
  * checks. Process-wide (every context). */

@@ -194,6 +194,13 @@ class Context:
         return out
 
     # ---------------- start predictor ----------------
+    def predictor_engine(self, engine):
+        """'tc' (tensor-core grid kernel, 2-D) or 'window' (CUDA-core GEMMs)."""
+        self._check(self.lib.cs_predictor_engine(self.h, 1 if engine == "tc" else 0))
+
+    def device_status(self):
+        self._check(self.lib.cs_device_status(self.h))
+
     def predictor_precision(self, bf16=True):
         self._check(self.lib.cs_predictor_precision(self.h, 1 if bf16 else 0))
 

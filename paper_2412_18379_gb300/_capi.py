@@ -64,6 +64,8 @@ SIGNATURES = {
     "cs_track_stats": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp]),
     "cs_kernel_launches": (_i64, [_vp]),
     "cs_predictor_precision": (_i32, [_vp, ctypes.c_int]),
+    "cs_predictor_engine": (_i32, [_vp, ctypes.c_int]),
+    "cs_device_status": (_i32, [_vp]),
     "cs_predictor_size": (_i64, [ctypes.c_int]),
     "cs_predictor_load": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
     "cs_predictor_save": (_i32, [_vp, ctypes.c_int, _vp, _i64]),

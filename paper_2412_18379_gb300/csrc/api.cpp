@@ -100,6 +100,7 @@ void cs_destroy(cs_ctx *ctx) {
     cudaSetDevice(ctx->device);
     for (auto &kv : ctx->meshes) free_mesh(kv.second);
     for (auto &p : ctx->pred) cs::predictor_release(p);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     if (ctx->scratch.counters) cudaFree(ctx->scratch.counters);
     if (ctx->scratch.stats) cudaFree(ctx->scratch.stats);
     if (ctx->scratch.list) cudaFree(ctx->scratch.list);

@@ -104,6 +104,8 @@ struct Predictor {
     float *dcol = nullptr, *dy0 = nullptr, *dy1 = nullptr, *da5 = nullptr, *win = nullptr,
           *tgt = nullptr;
     int64_t *idx = nullptr;
+    uint8_t *packed = nullptr;   // weights in the tensor-core kernel's layout
+    bool packed_dirty = true;
 };
 
 // Device scratch owned by a context: counters and the exact-search list.
@@ -203,6 +205,8 @@ struct cs_ctx {
     cs::Scratch scratch;
     cs::Profiler prof;
     cs::Predictor pred[2];   // dim 2, dim 3
+    int engine = 1;          // grid prediction: 1 tensor cores (2-D), 0 window GEMMs
+    int *dev_err = nullptr;  // device error flag of bounded waits
     int64_t launches = 0;
 };
 

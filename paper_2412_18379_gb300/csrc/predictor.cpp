@@ -239,6 +239,9 @@ void predictor_release(Predictor &P) {
         if (*f) cudaFree(*f);
         *f = nullptr;
     }
+    if (P.packed) cudaFree(P.packed);
+    P.packed = nullptr;
+    P.packed_dirty = true;
     P.loaded = false;
 }
 
@@ -247,6 +250,25 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
     Predictor *P = get_pred(ctx, m->d.dim);
     if (!P || !P->loaded) return fail(ctx, CS_ENOPRED, "no predictor loaded for this dimension");
     if (!m->grid_u_valid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
+    if (m->d.dim == 2 && ctx->engine == 1) {
+        // tensor-core grid kernel: weights repacked after every load / training
+        if (!P->packed) {
+            cs_status rc = dalloc(ctx, &P->packed, size_t(tc_packed_bytes()));
+            if (rc) return rc;
+        }
+        if (!ctx->dev_err) {
+            cs_status rc = dalloc(ctx, &ctx->dev_err, 1);
+            if (rc) return rc;
+            PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+        }
+        if (P->packed_dirty) {
+            ctx->launches += launch_pack_tc(P->w, NetShape(2), P->packed, st);
+            P->packed_dirty = false;
+        }
+        ctx->launches += launch_cnn2d_tc(m->d, m->grid_u, dt, P->packed, dhat, ctx->dev_err,
+                                         ctx->sm_count, st);
+        return CS_OK;
+    }
     const int64_t chunk = 8192;
     cs_status rc = ensure_workspace(ctx, *P, chunk);
     if (rc) return rc;
@@ -285,6 +307,26 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt
 }  // namespace cs
 
 extern "C" {
+
+cs_status cs_predictor_engine(cs_ctx *ctx, int engine) {
+    if (!ctx || (engine != 0 && engine != 1)) return CS_EINVAL;
+    ctx->engine = engine;
+    return CS_OK;
+}
+
+cs_status cs_device_status(cs_ctx *ctx) {
+    if (!ctx) return CS_EINVAL;
+    PCHK(cudaSetDevice(ctx->device));
+    PCHK(cudaDeviceSynchronize());
+    if (!ctx->dev_err) return CS_OK;
+    int e = 0;
+    PCHK(cudaMemcpy(&e, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+        return fail(ctx, CS_EDEVICE, "a bounded device wait gave up (tensor-core predictor)");
+    }
+    return CS_OK;
+}
 
 cs_status cs_predictor_precision(cs_ctx *ctx, int bf16) {
     if (!ctx) return CS_EINVAL;
@@ -450,6 +492,7 @@ cs_status cs_predictor_train(cs_ctx *ctx, int dim, const float *windows, const f
         ctx->launches += backward(ctx, *P, B, P->tgt, losses + s, nullptr);
         P->t += 1;
         ctx->launches += launch_adam(P->w, P->g, P->m, P->v, P->n, lr, P->t, ctx->sm_count, nullptr);
+        P->packed_dirty = true;
     }
     if (out == CS_OK) {
         cudaError_t e = cudaDeviceSynchronize();

@@ -239,3 +239,45 @@ def test_training_gains_over_plain_sns(ctx):
     m_sns = sns["path_len"].double().mean().item()
     m_cnn = cnn_out["path_len"].double().mean().item()
     assert m_cnn < 0.6 * m_sns, (m_sns, m_cnn)
+
+
+@pytest.mark.parametrize("n_side", [101, 301])
+def test_tensor_core_grid_prediction(ctx, n_side):
+    """The fused tcgen05 grid kernel against the FP64 oracle (sampled cells,
+    all tile-edge and grid-edge cells included) and against the per-window
+    CUDA-core engine on every cell."""
+    import torch
+    c = make_case("tg2d", n_side=n_side, cfl=8)
+    flat = init_weights(2, 31)
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(g))
+    tc = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+    win = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predictor_engine("tc")
+    ctx.predict(mesh, c.dt, out=tc)
+    ctx.predictor_engine("window")
+    ctx.predict(mesh, c.dt, out=win)
+    ctx.predictor_engine("tc")
+    ctx.device_status()
+    tc, win = tc.cpu().numpy(), win.cpu().numpy()
+    assert np.isfinite(tc).all()
+    scale = np.abs(win).max()
+    assert np.abs(tc - win).max() <= 4e-2 * scale
+    # oracle on a sample: every cell of the first/last rows and columns, the
+    # cells next to tile edges (multiples of 24), and random cells
+    gx, gy = g
+    iy, ix = np.divmod(np.arange(n_cells), gx)
+    edge = (ix % 24 == 0) | (ix % 24 == 23) | (iy % 24 == 0) | (iy % 24 == 23) | \
+        (ix == gx - 1) | (iy == gy - 1)
+    rng = np.random.default_rng(2)
+    pick = np.unique(np.concatenate([np.nonzero(edge)[0][:3000],
+                                     rng.integers(0, n_cells, size=1500)]))
+    U = _oracle_grid_u(om, c.u)
+    s = (om.hi - om.lo) / om.grid
+    w = cnn.windows(U.reshape(gy, gx, 2), pick, 2, c.dt / s)
+    ref = cnn.forward(2, cnn.unpack(2, flat), w)
+    assert np.abs(tc[pick] - ref).max() <= 4e-2 * np.abs(ref).max()
