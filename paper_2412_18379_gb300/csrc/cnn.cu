@@ -184,28 +184,34 @@ __global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restric
 // C[M][N] = op(A) op(B) (+ bias[N]) with operands rounded to BF16 and FP32
 // accumulation. A is [M][K] (transA: [K][M]); B is [K][N] (transB: [N][K]).
 // 64x64 output tile, 16-deep K slabs in shared memory, 4x4 per thread.
+// Split-K: block z sums K-range [z*kc, (z+1)*kc) and adds into C atomically
+// (C zeroed by the launcher; the bias is added by z = 0).
 __global__ void __launch_bounds__(kThreads) gemm_kernel(const float *__restrict__ A,
                                                         const float *__restrict__ Bm, float *C,
                                                         const float *__restrict__ bias, int64_t M,
                                                         int64_t N, int64_t K, bool transA,
                                                         bool transB, bool accumulate,
-                                                        bool round_bf16) {
+                                                        bool round_bf16, int64_t kc) {
     __shared__ float As[16][64 + 4];
     __shared__ float Bs[16][64 + 4];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int64_t m0 = int64_t(blockIdx.y) * 64, n0 = int64_t(blockIdx.x) * 64;
+    const int64_t kbeg = int64_t(blockIdx.z) * kc, kend = min(K, kbeg + kc);
+    const bool split = gridDim.z > 1;
     float acc[4][4] = {};
-    for (int64_t k0 = 0; k0 < K; k0 += 16) {
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
         for (int q = threadIdx.x; q < 16 * 64; q += kThreads) {
-            const int kk = q / 64, mm = q % 64;
-            const int64_t gm = m0 + mm, gk = k0 + kk;
+            // consecutive threads read consecutive addresses of each operand
+            const int ka = transA ? q / 64 : q % 16, ma = transA ? q % 64 : q / 16;
+            const int64_t gm = m0 + ma, gka = k0 + ka;
             float a = 0.f;
-            if (gm < M && gk < K) a = transA ? A[gk * M + gm] : A[gm * K + gk];
-            As[kk][mm] = round_bf16 ? bf16_round(a) : a;
-            const int64_t gn = n0 + mm;
+            if (gm < M && gka < kend) a = transA ? A[gka * M + gm] : A[gm * K + gka];
+            As[ka][ma] = round_bf16 ? bf16_round(a) : a;
+            const int kb = transB ? q % 16 : q / 64, nb = transB ? q / 16 : q % 64;
+            const int64_t gn = n0 + nb, gkb = k0 + kb;
             float bv = 0.f;
-            if (gn < N && gk < K) bv = transB ? Bm[gn * K + gk] : Bm[gk * N + gn];
-            Bs[kk][mm] = round_bf16 ? bf16_round(bv) : bv;
+            if (gn < N && gkb < kend) bv = transB ? Bm[gn * K + gkb] : Bm[gkb * N + gn];
+            Bs[kb][nb] = round_bf16 ? bf16_round(bv) : bv;
         }
         __syncthreads();
         #pragma unroll
@@ -231,9 +237,13 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const float *__restrict_
         for (int s = 0; s < 4; ++s) {
             const int64_t gn = n0 + tx * 4 + s;
             if (gn >= N) continue;
-            float v = acc[r][s] + (bias ? bias[gn] : 0.f);
-            if (accumulate) v += C[gm * N + gn];
-            C[gm * N + gn] = v;
+            float v = acc[r][s] + (bias && blockIdx.z == 0 ? bias[gn] : 0.f);
+            if (split) {
+                atomicAdd(&C[gm * N + gn], v);
+            } else {
+                if (accumulate) v += C[gm * N + gn];
+                C[gm * N + gn] = v;
+            }
         }
     }
 }
@@ -408,10 +418,20 @@ void set_gemm_bf16(bool on) { g_gemm_bf16 = on; }
 int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
                 int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
                 cudaStream_t st) {
-    const dim3 grid(unsigned((N + 63) / 64), unsigned((M + 63) / 64));
+    // split K when the output has few tiles and K is long (weight gradients)
+    const int64_t tiles = ((N + 63) / 64) * ((M + 63) / 64);
+    int64_t splits = 1;
+    if (tiles < 512 && K > 2048) splits = std::min<int64_t>((K + 1023) / 1024, (1024 + tiles - 1) / tiles);
+    const int64_t kc = ((K + splits - 1) / splits + 15) / 16 * 16;
+    splits = (K + kc - 1) / kc;
+    int n = 1;
+    if (splits > 1 && !accumulate) {
+        cudaMemsetAsync(C, 0, size_t(M) * size_t(N) * sizeof(float), st);
+    }
+    const dim3 grid(unsigned((N + 63) / 64), unsigned((M + 63) / 64), unsigned(splits));
     gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, C, bias, M, N, K, transA, transB, accumulate,
-                                           g_gemm_bf16);
-    return 1;
+                                           g_gemm_bf16, kc);
+    return n;
 }
 
 int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st) {

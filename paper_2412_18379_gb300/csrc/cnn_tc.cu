@@ -40,8 +40,8 @@ constexpr uint32_t kTmemCols = 512;
 
 // packed weights (bytes); produced by pack_weights_kernel
 struct TcLayout {
-    static constexpr int w1 = 0;                          // fp32 [32][2][9]
-    static constexpr int b1 = w1 + 32 * 2 * 9 * 4;        // fp32 [32]
+    static constexpr int w1 = 0;                          // bf16 [9][32][8]: W1/2, channels >= 2 zero
+    static constexpr int b1 = w1 + 9 * 32 * 8 * 2;        // fp32 [32]
     static constexpr int bconv = b1 + 32 * 4;             // 3 x bf16 [9][4][32][8]
     static constexpr int bconv_bytes = 9 * 4 * 32 * 8 * 2;
     static constexpr int cb = bconv + 3 * bconv_bytes;    // fp32 [3][32] conv biases
@@ -54,8 +54,9 @@ struct TcLayout {
 };
 
 // shared memory map (bytes)
-constexpr int kSmX0 = 0;                                    // fp32 [32*32][2]
-constexpr int kSmAct0 = kSmX0 + kW * kW * 2 * 4;            // bf16 [4][1024][8]
+constexpr int kRowsX0 = 1152;                               // 32 x 32 input + shifted reads
+constexpr int kSmX0 = 0;                                    // bf16 [1152][8] (2 channels used)
+constexpr int kSmAct0 = kSmX0 + kRowsX0 * 16;               // bf16 [4][1024][8]
 constexpr int kSmAct1 = kSmAct0 + 4 * kRows * 16;
 constexpr int kSmW = kSmAct1 + 4 * kRows * 16;              // packed weights
 constexpr int kSmBar = kSmW + TcLayout::total;              // mbarrier + tmem slot
@@ -184,6 +185,22 @@ __device__ __forceinline__ void issue_conv(uint32_t tmem, const uint8_t *act, co
     }
 }
 
+// Issue the MMAs of conv1 (called by one thread): the input has one 8-channel
+// chunk (u0, u1, 0 ... 0); a K = 16 step reads that chunk twice (LBO = 0 on
+// both operands) against halved weights, so the sum is the 8-channel product.
+// 8 M-tiles cover the 30 valid rows (rows past them are garbage).
+__device__ __forceinline__ void issue_conv1(uint32_t tmem, const uint8_t *x0, const uint8_t *wb) {
+    constexpr uint32_t id = idesc_bf16(128, 32);
+    const uint32_t a0 = smem_addr(x0), b0 = smem_addr(wb);
+    for (int mt = 0; mt < 8; ++mt)
+        for (int t = 0; t < 9; ++t) {
+            const int shift = (t / 3) * kW + (t % 3);
+            const uint64_t a = sdesc(a0 + uint32_t((128 * mt + shift) * 16), 0, 128);
+            const uint64_t b = sdesc(b0 + uint32_t(t * 32 * 16), 0, 128);
+            mma_bf16(tmem + uint32_t(32 * mt), a, b, id, t > 0 ? 1u : 0u);
+        }
+}
+
 // Epilogue of a conv layer: TMEM -> +bias, ReLU -> BF16 activations.
 __device__ __forceinline__ void epilogue_conv(uint32_t tmem, uint8_t *out, const float *bias,
                                               int n_mt) {
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const DevMesh m, const float *__restrict__ U, float scale0, float scale1,
     const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    float *x0 = reinterpret_cast<float *>(smem + kSmX0);
+    uint8_t *x0 = smem + kSmX0;
     uint8_t *act0 = smem + kSmAct0;
     uint8_t *act1 = smem + kSmAct1;
     uint8_t *wsm = smem + kSmW;
@@ -231,11 +248,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         reinterpret_cast<uint4 *>(act0)[i] = make_uint4(0, 0, 0, 0);
         reinterpret_cast<uint4 *>(act1)[i] = make_uint4(0, 0, 0, 0);
     }
+    for (int i = tid; i < kRowsX0; i += kThreadsTC)
+        reinterpret_cast<uint4 *>(x0)[i] = make_uint4(0, 0, 0, 0);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const float *w1 = reinterpret_cast<const float *>(wsm + TcLayout::w1);
     const float *b1 = reinterpret_cast<const float *>(wsm + TcLayout::b1);
     const float *cb = reinterpret_cast<const float *>(wsm + TcLayout::cb);
     const float *fc1b = reinterpret_cast<const float *>(wsm + TcLayout::fc1b);
@@ -247,7 +265,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         const int tx = tile % tiles_x, ty = tile / tiles_x;
         const int cx0 = tx * kTile - 4, cy0 = ty * kTile - 4;
-        // ---- input: 32 x 32 cells, channels u_k * dt / s_k, zero outside ----
+        // ---- input: 32 x 32 cells, channels u_k * dt / s_k (BF16), zero outside ----
         for (int i = tid; i < kW * kW; i += kThreadsTC) {
             const int cx = cx0 + (i % kW), cy = cy0 + (i / kW);
             float u0 = 0.f, u1 = 0.f;
@@ -256,29 +274,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                 u0 = uv.x * scale0;
                 u1 = uv.y * scale1;
             }
-            x0[2 * i] = u0;
-            x0[2 * i + 1] = u1;
+            reinterpret_cast<uint4 *>(x0)[i] = make_uint4(pack_bf16x2(u0, u1), 0, 0, 0);
         }
+        fence_async_smem();
         __syncthreads();
-        // ---- conv1 on CUDA cores: pixels (y < 30) of the flat 32-wide grid ----
-        for (int r = tid; r < 30 * kW; r += kThreadsTC) {
-            const int y = r / kW, x = r % kW;
-            float v[32];
-            #pragma unroll
-            for (int o = 0; o < 32; ++o) v[o] = b1[o];
-            #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const int xx = x + t % 3, yy = y + t / 3;
-                if (xx >= kW) continue;   // garbage column: never feeds a valid output
-                const float i0 = x0[2 * (yy * kW + xx)], i1 = x0[2 * (yy * kW + xx) + 1];
-                #pragma unroll
-                for (int o = 0; o < 32; ++o)
-                    v[o] = fmaf(w1[(o * 2 + 1) * 9 + t], i1, fmaf(w1[(o * 2) * 9 + t], i0, v[o]));
-            }
-            #pragma unroll
-            for (int o = 0; o < 32; ++o) v[o] = fmaxf(v[o], 0.f);
-            store_act(act0, r, v);
+        // ---- conv1 on tcgen05 -> act0 ----
+        if (tid == 0) {
+            fence_after();
+            issue_conv1(tmem, x0, wsm + TcLayout::w1);
+            mma_commit(bar);
         }
+        ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
+        phase ^= 1;
+        fence_after();
+        if (ok) epilogue_conv(tmem, act0, b1, 8);
+        fence_before();
         fence_async_smem();
         __syncthreads();
         // ---- conv2, conv3, conv4 on tcgen05 ----
@@ -328,11 +338,18 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                 for (int j = 0; j < 8; ++j) {
                     float v[32];
                     tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(256 * h + 32 * j), v);
+                    const float4 *pb = reinterpret_cast<const float4 *>(fc1b + 32 * j);
+                    const float4 *p0 = reinterpret_cast<const float4 *>(fc2w + 32 * j);
+                    const float4 *p1 = reinterpret_cast<const float4 *>(fc2w + 256 + 32 * j);
                     #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const float hv = fmaxf(v[c] + fc1b[32 * j + c], 0.f);
-                        o0 = fmaf(fc2w[32 * j + c], hv, o0);
-                        o1 = fmaf(fc2w[256 + 32 * j + c], hv, o1);
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 bb = pb[c], w0 = p0[c], w1 = p1[c];
+                        const float h0 = fmaxf(v[4 * c] + bb.x, 0.f);
+                        const float h1 = fmaxf(v[4 * c + 1] + bb.y, 0.f);
+                        const float h2 = fmaxf(v[4 * c + 2] + bb.z, 0.f);
+                        const float h3 = fmaxf(v[4 * c + 3] + bb.w, 0.f);
+                        o0 = fmaf(w0.x, h0, fmaf(w0.y, h1, fmaf(w0.z, h2, fmaf(w0.w, h3, o0))));
+                        o1 = fmaf(w1.x, h0, fmaf(w1.y, h1, fmaf(w1.z, h2, fmaf(w1.w, h3, o1))));
                     }
                 }
                 const int y = row / kW, x = row % kW;
@@ -359,8 +376,12 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, uint8_t *__rest
                                     int64_t off_w4, int64_t off_b4, int64_t off_f1w,
                                     int64_t off_f1b, int64_t off_f2w, int64_t off_f2b) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    float *w1 = reinterpret_cast<float *>(out + TcLayout::w1);
-    for (int i = tid; i < 32 * 2 * 9; i += nth) w1[i] = w[off_w1 + i];
+    // conv1 W[o][i][t] (i < 2) -> [t][o][8] halved (each K step reads it twice)
+    __nv_bfloat16 *w1 = reinterpret_cast<__nv_bfloat16 *>(out + TcLayout::w1);
+    for (int e = tid; e < 9 * 32 * 8; e += nth) {
+        const int t = e / 256, o = (e / 8) % 32, j = e % 8;
+        w1[e] = __float2bfloat16_rn(j < 2 ? 0.5f * w[off_w1 + (o * 2 + j) * 9 + t] : 0.f);
+    }
     for (int i = tid; i < 32; i += nth) {
         reinterpret_cast<float *>(out + TcLayout::b1)[i] = w[off_b1 + i];
         reinterpret_cast<float *>(out + TcLayout::cb)[i] = w[off_b2 + i];
