@@ -69,8 +69,8 @@ def source_sha(files):
     return h.hexdigest()[:16]
 
 
-WALK_SOURCES = ("walk.cu", "walk_common.cuh", "internal.h")
-CNN_SOURCES = ("cnn_tc.cu", "walk_common.cuh", "internal.h")
+WALK_SOURCES = ("walk.cu", "walk_common.cuh")
+CNN_SOURCES = ("cnn_tc.cu",)
 
 
 def ncu_traffic(profile, sources):

@@ -291,6 +291,68 @@ cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
                         int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                         int32_t *start_out, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of tracking requests over resident meshes.   */
+/* (A property of the library: the paper tracks one solver step at a time.) */
+/*                                                                          */
+/* A worker thread owns `slots` CUDA streams and a device arena of           */
+/* arena_bytes. Requests wait in arrival order; the head request is admitted */
+/* as soon as a slot is free and the arena has room for its buffers (its     */
+/* HBM footprint: 2*dim*8 + 17 (+4 with starts) bytes per particle, plus the */
+/* prediction grid for CNN-SNS). Admitted requests run concurrently on their */
+/* streams; results are identical to cs_track_host on the same inputs.      */
+/* Meshes, grid velocities (cs_grid_velocity) and predictor weights must be  */
+/* resident before cs_serve_start and unchanged while serving. CNN-SNS      */
+/* requests run on the 2-D tensor-core predictor; where it is unavailable   */
+/* (3-D, no predictor, no grid velocity) they fall back to plain SNS.       */
+/* ------------------------------------------------------------------------ */
+typedef struct cs_serve_cfg {
+    int32_t slots;          /* concurrent requests on the GPU (1..64)        */
+    size_t  arena_bytes;    /* device memory for requests' buffers           */
+} cs_serve_cfg;
+
+typedef struct cs_request {
+    int32_t mesh_id;
+    int64_t n;
+    const double *x;        /* HOST [n][dim] (pinned memory overlaps best)   */
+    const double *u;        /* HOST [n][dim]                                 */
+    double dt;
+    const int32_t *start;   /* HOST [n] user ids, or NULL when n == n_v      */
+    int32_t mode;           /* CS_SNS, CS_ASG_DIRECT, CS_CNN_SNS             */
+    int32_t *host_out;      /* HOST [n], written when the request finishes   */
+    int32_t *path_len_out;  /* HOST [n]                                      */
+    uint8_t *status_out;    /* HOST [n]                                      */
+} cs_request;
+
+typedef struct cs_serve_stats {
+    int64_t completed, rejected, particles;
+    double  p50_ms, p99_ms, mean_ms, max_ms;   /* submit-to-finish latency   */
+    double  wall_s;                            /* first submit to last finish */
+    double  particles_per_s;
+    int64_t peak_bytes;                        /* arena high-water mark      */
+    int32_t max_concurrent;                    /* requests in flight at once */
+} cs_serve_stats;
+
+/* Start the worker (one server per context). CS_EBUSY if already serving. */
+cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg);
+
+/* Queue a request; returns at once with a ticket. The caller keeps the
+ * request's arrays alive until cs_serve_wait reports it finished. CS_ENOMEM
+ * if the request could never fit in the arena (counted as rejected). */
+cs_status cs_serve_submit(cs_ctx *ctx, const cs_request *req, int64_t *ticket);
+
+/* Wait up to timeout_ms for a ticket: CS_OK (then *result holds the request's
+ * status and *mode_used the start rule it ran with) or CS_EBUSY (not yet
+ * finished). A finished ticket is forgotten after it is reported. */
+cs_status cs_serve_wait(cs_ctx *ctx, int64_t ticket, int32_t timeout_ms, cs_status *result,
+                        int32_t *mode_used);
+
+/* Latency percentiles and throughput of the requests finished so far. */
+cs_status cs_serve_report(cs_ctx *ctx, cs_serve_stats *out);
+
+/* Drain the queue, stop the worker and free the serving resources. */
+cs_status cs_serve_stop(cs_ctx *ctx);
+
 /* Walk statistics of a finished cs_track (DEVICE pointers, synchronous):
  * out[0] = sum of path_len, out[1] = max path_len, out[2..5] = particles with
  * status 0..3. */

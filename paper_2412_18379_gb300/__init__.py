@@ -295,6 +295,48 @@ class Context:
             _ptr(out.get("start")), _stream_ptr(st)))
         return out
 
+    # ---------------- serving ----------------
+    def serve_start(self, slots=4, arena_bytes=2 << 30):
+        cfg = _capi.ServeCfg(slots, arena_bytes)
+        self._check(self.lib.cs_serve_start(self.h, ctypes.byref(cfg)))
+        self._requests = {}
+
+    def submit(self, mesh, x, u, dt, start=None, mode="sns"):
+        """Queue a request (host arrays, pinned torch tensors overlap best).
+        Returns (ticket, outputs); outputs are valid after wait(ticket)."""
+        import torch
+        n = x.shape[0]
+        out = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
+                   path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
+                   status=torch.empty(n, dtype=torch.uint8).pin_memory())
+        req = _capi.Request(mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+                            MODES[mode] if isinstance(mode, str) else int(mode),
+                            _ptr(out["host"]), _ptr(out["path_len"]), _ptr(out["status"]))
+        t = ctypes.c_int64()
+        self._check(self.lib.cs_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t)))
+        self._requests[t.value] = (x, u, start, out)   # keep the arrays alive
+        return t.value, out
+
+    def wait(self, ticket, timeout_ms=60000):
+        """Block until the request finishes; returns the start rule it ran with."""
+        res, mode = ctypes.c_int32(), ctypes.c_int32()
+        rc = self.lib.cs_serve_wait(self.h, ticket, int(timeout_ms), ctypes.byref(res),
+                                    ctypes.byref(mode))
+        if rc == -4:
+            raise TimeoutError("request %d still running" % ticket)
+        self._check(rc)
+        self._check(res.value)
+        self._requests.pop(ticket, None)
+        return mode.value
+
+    def serve_report(self):
+        s = _capi.ServeStats()
+        self._check(self.lib.cs_serve_report(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _capi.ServeStats._fields_}
+
+    def serve_stop(self):
+        self._check(self.lib.cs_serve_stop(self.h))
+
     def stats(self, path_len, status, stream=None):
         """(sum, max, count FOUND, OUTSIDE, FALLBACK, INVALID) of device outputs."""
         import torch

@@ -86,6 +86,32 @@ SIGNATURES = {
 STAGES = ["walk", "fallback", "resample", "cnn", "train"]
 
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("slots", _i32), ("arena_bytes", ctypes.c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("mesh_id", _i32), ("n", _i64), ("x", _vp), ("u", _vp), ("dt", _dbl),
+                ("start", _vp), ("mode", _i32), ("host_out", _vp), ("path_len_out", _vp),
+                ("status_out", _vp)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("completed", _i64), ("rejected", _i64), ("particles", _i64),
+                ("p50_ms", _dbl), ("p99_ms", _dbl), ("mean_ms", _dbl), ("max_ms", _dbl),
+                ("wall_s", _dbl), ("particles_per_s", _dbl), ("peak_bytes", _i64),
+                ("max_concurrent", _i32)]
+
+
+SIGNATURES.update({
+    "cs_serve_start": (_i32, [_vp, ctypes.POINTER(ServeCfg)]),
+    "cs_serve_submit": (_i32, [_vp, ctypes.POINTER(Request), ctypes.POINTER(_i64)]),
+    "cs_serve_wait": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "cs_serve_report": (_i32, [_vp, ctypes.POINTER(ServeStats)]),
+    "cs_serve_stop": (_i32, [_vp]),
+})
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("launches", _i64 * 8), ("ms", _dbl * 8)]
 

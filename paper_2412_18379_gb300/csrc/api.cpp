@@ -98,6 +98,7 @@ cs_status cs_create(cs_ctx **out, int cuda_device) {
 void cs_destroy(cs_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    cs::serve_release(ctx);
     for (auto &kv : ctx->meshes) free_mesh(kv.second);
     for (auto &p : ctx->pred) cs::predictor_release(p);
     if (ctx->dev_err) cudaFree(ctx->dev_err);
@@ -115,7 +116,7 @@ void cs_destroy(cs_ctx *ctx) {
 
 const char *cs_last_error(const cs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-int64_t cs_kernel_launches(const cs_ctx *ctx) { return ctx ? ctx->launches : 0; }
+int64_t cs_kernel_launches(const cs_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
 
 cs_status cs_profile_enable(cs_ctx *ctx, int on) {
     if (!ctx) return CS_EINVAL;

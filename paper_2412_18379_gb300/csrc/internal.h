@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -11,6 +12,8 @@
 #include "cnnsns.h"
 
 namespace cs {
+
+struct Server;   // serve.cpp
 
 // Every element has two records.
 //
@@ -207,7 +210,8 @@ struct cs_ctx {
     cs::Predictor pred[2];   // dim 2, dim 3
     int engine = 1;          // grid prediction: 1 tensor cores (2-D), 0 window GEMMs
     int *dev_err = nullptr;  // device error flag of bounded waits
-    int64_t launches = 0;
+    cs::Server *server = nullptr;   // serving loop (serve.cpp), if started
+    std::atomic<int64_t> launches{0};
 };
 
 namespace cs {
@@ -218,6 +222,9 @@ cs_status cs_track_impl(cs_ctx *ctx, Mesh *m, int64_t n, const double *x, const 
                         int32_t *start_out, cudaStream_t stream);
 // predictor.cpp
 void predictor_release(Predictor &P);
+cs_status predict_grid(cs_ctx *ctx, Mesh *m, double dt, float *dhat, cudaStream_t st);
+// serve.cpp
+void serve_release(cs_ctx *ctx);
 cs_status cnn_prepare(cs_ctx *ctx, Mesh *m, const double *u_nodal, double dt, cudaStream_t st,
                       const float **dhat_out);
 }  // namespace cs

@@ -1,0 +1,446 @@
+// Serving: continuous batching of tracking requests over device-resident
+// meshes, fields and predictor weights.
+//
+// A worker thread owns S slots (one CUDA stream each) and one device arena.
+// Requests queue in arrival order; whenever a slot is free and the arena has
+// room for the head request's buffers (its HBM footprint), the request is
+// admitted: its inputs are copied in, its start rule and walk run on the
+// slot's stream, its outputs are copied back and an event marks the end.
+// Requests admitted while others are in flight run concurrently on the GPU
+// (different streams). The worker polls the events, releases the memory of
+// finished requests and admits the next ones. Latency is submit-to-finish.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "cnn.h"
+#include "internal.h"
+
+namespace cs {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over one device block (offsets aligned to 256 B).
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0, peak = 0;
+    std::map<size_t, size_t> free_;   // offset -> bytes
+    bool alloc(size_t bytes, size_t &off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                off = it->first;
+                const size_t rest = it->second - bytes;
+                free_.erase(it);
+                if (rest) free_[off + bytes] = rest;
+                used += bytes;
+                peak = std::max(peak, used);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+struct Request {
+    int64_t ticket = 0;
+    cs_request r{};
+    Mesh *mesh = nullptr;
+    Clock::time_point t_submit, t_admit, t_done;
+    size_t off = 0, bytes = 0;
+    cs_status result = CS_OK;
+    bool done = false;
+    int used_mode = 0;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    int32_t *counters = nullptr;
+    Request *req = nullptr;
+};
+
+struct Server {
+    cs_ctx *ctx = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<Request *> pending;
+    std::map<int64_t, Request *> all;
+    int64_t next_ticket = 1;
+    bool stop = false;
+    // statistics
+    std::vector<double> lat_ms;
+    int64_t completed = 0, rejected = 0, particles = 0;
+    int32_t active = 0, max_active = 0;
+    Clock::time_point t_first, t_last;
+    bool any = false;
+};
+
+namespace {
+
+size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn) {
+    const int d = m.d.dim;
+    const size_t n = size_t(r.n);
+    size_t b = 0;
+    auto add = [&b](size_t x) { b += (x + 255) / 256 * 256; };
+    add(n * d * 8);                  // x
+    add(n * d * 8);                  // u
+    if (r.start) add(n * 4);         // start
+    add(n * 4);                      // host
+    add(n * 4);                      // path
+    add(n);                          // status
+    add(std::max<size_t>(n, 1) * 4); // exact-search list
+    if (cnn) add(size_t(m.d.n_asg) * d * 4);   // predicted displacement grid
+    return b;
+}
+
+// Enqueue one admitted request on its slot's stream.
+cs_status start_request(Server &S, Slot &sl, Request &q) {
+    cs_ctx *ctx = S.ctx;
+    const cs_request &r = q.r;
+    Mesh &m = *q.mesh;
+    const int d = m.d.dim;
+    const size_t n = size_t(r.n);
+    char *p = S.arena.base + q.off;
+    auto take = [&p](size_t x) {
+        char *o = p;
+        p += (x + 255) / 256 * 256;
+        return o;
+    };
+    double *x = reinterpret_cast<double *>(take(n * d * 8));
+    double *u = reinterpret_cast<double *>(take(n * d * 8));
+    int32_t *start = r.start ? reinterpret_cast<int32_t *>(take(n * 4)) : nullptr;
+    int32_t *host = reinterpret_cast<int32_t *>(take(n * 4));
+    int32_t *path = reinterpret_cast<int32_t *>(take(n * 4));
+    uint8_t *status = reinterpret_cast<uint8_t *>(take(n));
+    int32_t *list = reinterpret_cast<int32_t *>(take(std::max<size_t>(n, 1) * 4));
+    float *dhat = q.used_mode == CS_CNN_SNS ? reinterpret_cast<float *>(take(size_t(m.d.n_asg) * d * 4))
+                                            : nullptr;
+    cudaStream_t st = sl.st;
+    cudaError_t e = cudaMemcpyAsync(x, r.x, n * d * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(u, r.u, n * d * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && start)
+        e = cudaMemcpyAsync(start, r.start, n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return CS_ECUDA;
+    if (dhat) {
+        const cs_status rc = predict_grid(ctx, &m, r.dt, dhat, st);
+        if (rc) return rc;
+    }
+    TrackArgs a{};
+    a.n = r.n;
+    a.x = x;
+    a.u = u;
+    a.dt = r.dt;
+    a.start_user = start;
+    a.mode = q.used_mode;
+    a.dhat = dhat;
+    a.host = host;
+    a.path = path;
+    a.status = status;
+    a.start_out = nullptr;
+    Scratch sc;
+    sc.counters = sl.counters;
+    sc.list = list;
+    sc.list_cap = int64_t(std::max<size_t>(n, 1));
+    ctx->launches += launch_track(m.d, a, sc, ctx->sm_count, st, nullptr);
+    e = cudaMemcpyAsync(r.host_out, host, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r.path_len_out, path, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r.status_out, status, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, st);
+    return e == cudaSuccess ? CS_OK : CS_ECUDA;
+}
+
+void finish(Server &S, Slot &sl, cs_status rc) {
+    Request *q = sl.req;
+    sl.req = nullptr;
+    std::lock_guard<std::mutex> lock(S.mu);
+    S.arena.release(q->off, q->bytes);
+    q->t_done = Clock::now();
+    q->result = rc;
+    q->done = true;
+    S.active -= 1;
+    if (rc == CS_OK) {
+        S.completed += 1;
+        S.particles += q->r.n;
+        S.lat_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+        S.t_last = q->t_done;
+    }
+    S.done_cv.notify_all();
+}
+
+void worker_loop(Server *Sp) {
+    Server &S = *Sp;
+    cudaSetDevice(S.ctx->device);
+    for (;;) {
+        bool progress = false;
+        // completions
+        for (Slot &sl : S.slots) {
+            if (!sl.req) continue;
+            const cudaError_t e = cudaEventQuery(sl.ev);
+            if (e == cudaSuccess) {
+                finish(S, sl, CS_OK);
+                progress = true;
+            } else if (e != cudaErrorNotReady) {
+                finish(S, sl, CS_ECUDA);
+                progress = true;
+            }
+        }
+        // admissions, in arrival order, while a slot and memory are free
+        for (Slot &sl : S.slots) {
+            if (sl.req) continue;
+            Request *q = nullptr;
+            {
+                std::lock_guard<std::mutex> lock(S.mu);
+                if (S.pending.empty()) break;
+                Request *h = S.pending.front();
+                size_t off = 0;
+                if (!S.arena.alloc(h->bytes, off)) break;   // wait for memory
+                h->off = off;
+                S.pending.pop_front();
+                S.active += 1;
+                S.max_active = std::max(S.max_active, S.active);
+                q = h;
+            }
+            q->t_admit = Clock::now();
+            sl.req = q;
+            const cs_status rc = start_request(S, sl, *q);
+            if (rc != CS_OK) finish(S, sl, rc);
+            progress = true;
+        }
+        std::unique_lock<std::mutex> lock(S.mu);
+        bool busy = false;
+        for (const Slot &sl : S.slots) busy = busy || sl.req;
+        if (S.stop && S.pending.empty() && !busy) break;
+        if (!progress) {
+            if (busy || !S.pending.empty())
+                S.cv.wait_for(lock, std::chrono::microseconds(20));
+            else
+                S.cv.wait_for(lock, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+cs_status sfail(cs_ctx *ctx, cs_status code, const std::string &msg) {
+    ctx->err = msg;
+    return code;
+}
+
+}  // namespace
+
+void serve_release(cs_ctx *ctx) {
+    Server *S = ctx->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (Slot &sl : S->slots) {
+        if (sl.st) cudaStreamDestroy(sl.st);
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.counters) cudaFree(sl.counters);
+    }
+    if (S->arena.base) cudaFree(S->arena.base);
+    for (auto &kv : S->all) delete kv.second;
+    delete S;
+    ctx->server = nullptr;
+}
+
+}  // namespace cs
+
+using namespace cs;
+
+extern "C" {
+
+cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg) {
+    if (!ctx || !cfg || cfg->slots < 1 || cfg->slots > 64 || cfg->arena_bytes < 4096)
+        return ctx ? sfail(ctx, CS_EINVAL, "cs_serve_start: bad configuration") : CS_EINVAL;
+    if (ctx->server) return sfail(ctx, CS_EBUSY, "cs_serve_start: already serving");
+    cudaSetDevice(ctx->device);
+    Server *S = new (std::nothrow) Server();
+    if (!S) return CS_ENOMEM;
+    S->ctx = ctx;
+    if (cudaMalloc(&S->arena.base, cfg->arena_bytes) != cudaSuccess) {
+        delete S;
+        return sfail(ctx, CS_ENOMEM, "cs_serve_start: arena allocation failed");
+    }
+    S->arena.size = cfg->arena_bytes;
+    S->arena.free_[0] = cfg->arena_bytes;
+    S->slots.resize(size_t(cfg->slots));
+    for (Slot &sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&sl.counters, 16 * sizeof(int32_t)) != cudaSuccess) {
+            ctx->server = S;
+            serve_release(ctx);
+            return sfail(ctx, CS_ENOMEM, "cs_serve_start: slot resources");
+        }
+    }
+    // resident predictor weights in the tensor-core layout before any request
+    Predictor &P = ctx->pred[0];
+    if (P.loaded && ctx->engine == 1) {
+        if (!P.packed && cudaMalloc(&P.packed, size_t(tc_packed_bytes())) != cudaSuccess) {
+            ctx->server = S;
+            serve_release(ctx);
+            return sfail(ctx, CS_ENOMEM, "cs_serve_start: predictor buffer");
+        }
+        if (!ctx->dev_err) {
+            if (cudaMalloc(&ctx->dev_err, sizeof(int)) != cudaSuccess) {
+                ctx->server = S;
+                serve_release(ctx);
+                return sfail(ctx, CS_ENOMEM, "cs_serve_start: error flag");
+            }
+            cudaMemset(ctx->dev_err, 0, sizeof(int));
+        }
+        if (P.packed_dirty) {
+            ctx->launches += launch_pack_tc(P.w, NetShape(2), P.packed, nullptr);
+            P.packed_dirty = false;
+        }
+    }
+    cudaDeviceSynchronize();
+    ctx->server = S;
+    S->worker = std::thread(worker_loop, S);
+    return CS_OK;
+}
+
+cs_status cs_serve_submit(cs_ctx *ctx, const cs_request *req, int64_t *ticket) {
+    if (!ctx || !req || !ticket) return CS_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return sfail(ctx, CS_EINVAL, "cs_serve_submit: not serving");
+    auto it = ctx->meshes.find(req->mesh_id);
+    if (it == ctx->meshes.end()) return sfail(ctx, CS_ENOMESH, "cs_serve_submit: unknown mesh");
+    Mesh *m = it->second;
+    if (req->n < 1 || req->n >= (int64_t(1) << 31) - 1 || !req->x || !req->u || !req->host_out ||
+        !req->path_len_out || !req->status_out)
+        return sfail(ctx, CS_EINVAL, "cs_serve_submit: bad request");
+    if (req->mode != CS_SNS && req->mode != CS_ASG_DIRECT && req->mode != CS_CNN_SNS)
+        return sfail(ctx, CS_EINVAL, "cs_serve_submit: unknown mode");
+    if (!req->start && req->n != m->d.n_v)
+        return sfail(ctx, CS_EINVAL, "cs_serve_submit: start == NULL needs n == n_vertices");
+    // CNN-SNS where the tensor-core predictor and the mesh's grid velocity are
+    // resident; otherwise the request falls back to plain SNS
+    int mode = req->mode;
+    if (mode == CS_CNN_SNS &&
+        !(m->d.dim == 2 && ctx->pred[0].loaded && ctx->engine == 1 && m->grid_u_valid &&
+          ctx->pred[0].packed && !ctx->pred[0].packed_dirty))
+        mode = CS_SNS;
+    Request *q = new (std::nothrow) Request();
+    if (!q) return CS_ENOMEM;
+    q->r = *req;
+    q->mesh = m;
+    q->used_mode = mode;
+    q->bytes = request_bytes(*req, *m, mode == CS_CNN_SNS);
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (q->bytes > S->arena.size) {
+        const size_t need = q->bytes;
+        S->rejected += 1;
+        delete q;
+        return sfail(ctx, CS_ENOMEM, "cs_serve_submit: request needs " + std::to_string(need) +
+                                         " bytes, more than the serving arena holds (" +
+                                         std::to_string(S->arena.size) + ")");
+    }
+    q->ticket = S->next_ticket++;
+    q->t_submit = Clock::now();
+    if (!S->any) {
+        S->t_first = q->t_submit;
+        S->any = true;
+    }
+    S->pending.push_back(q);
+    S->all[q->ticket] = q;
+    *ticket = q->ticket;
+    S->cv.notify_all();
+    return CS_OK;
+}
+
+cs_status cs_serve_wait(cs_ctx *ctx, int64_t ticket, int32_t timeout_ms, cs_status *result,
+                        int32_t *mode_used) {
+    if (!ctx) return CS_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return sfail(ctx, CS_EINVAL, "cs_serve_wait: not serving");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->all.find(ticket);
+    if (it == S->all.end()) return sfail(ctx, CS_EINVAL, "cs_serve_wait: unknown ticket");
+    Request *q = it->second;
+    const bool ok = S->done_cv.wait_for(lock, std::chrono::milliseconds(std::max(0, timeout_ms)),
+                                        [q] { return q->done; });
+    if (!ok) return CS_EBUSY;   // still running
+    if (result) *result = q->result;
+    if (mode_used) *mode_used = q->used_mode;
+    S->all.erase(it);
+    delete q;
+    return CS_OK;
+}
+
+cs_status cs_serve_report(cs_ctx *ctx, cs_serve_stats *out) {
+    if (!ctx || !out) return CS_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return sfail(ctx, CS_EINVAL, "cs_serve_report: not serving");
+    std::lock_guard<std::mutex> lock(S->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->completed = S->completed;
+    out->rejected = S->rejected;
+    out->particles = S->particles;
+    out->peak_bytes = int64_t(S->arena.peak);
+    out->max_concurrent = S->max_active;
+    if (!S->lat_ms.empty()) {
+        std::vector<double> v = S->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto pct = [&v](double p) {
+            const size_t i = size_t(std::min<double>(double(v.size() - 1),
+                                                     std::ceil(p * double(v.size())) - 1));
+            return v[i];
+        };
+        out->p50_ms = pct(0.50);
+        out->p99_ms = pct(0.99);
+        out->max_ms = v.back();
+        double s = 0;
+        for (double x : v) s += x;
+        out->mean_ms = s / double(v.size());
+        const double wall =
+            std::chrono::duration<double>(S->t_last - S->t_first).count();
+        out->wall_s = wall;
+        out->particles_per_s = wall > 0 ? double(S->particles) / wall : 0.0;
+    }
+    return CS_OK;
+}
+
+cs_status cs_serve_stop(cs_ctx *ctx) {
+    if (!ctx) return CS_EINVAL;
+    if (!ctx->server) return CS_OK;
+    serve_release(ctx);
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+"""Serving: continuous batching over resident meshes, fields and predictor.
+
+Each request's result must be the same alone and in the mix (bit for bit:
+the walk is exact and the predictor deterministic), requests must overlap on
+the GPU, admission must respect the arena, and an oversized request must be
+refused with an error instead of blocking the queue.
+"""
+
+import numpy as np
+import pytest
+
+from workloads import make_case
+from workloads.weights import init_weights
+from workloads.fields import dt_for_cfl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    import paper_2412_18379_gb300 as cs
+    from paper_2412_18379_gb300 import build
+    build.build()
+    ctx = cs.Context(0)
+    ctx.load_predictor(2, init_weights(2, 5))
+    meshes = []
+    for name, kw in [("tg2d", {"n_side": 201}), ("modes2d", {"n_side": 301}),
+                     ("abc3d", {"n_side": 21})]:
+        c = make_case(name, **kw)
+        m = ctx.upload_mesh(c.xyz, c.conn)
+        if c.dim == 2:
+            ctx.grid_velocity(m, torch.from_numpy(c.u).cuda())   # resident field
+        meshes.append((c, m, m.node_start_elements()))
+    torch.cuda.synchronize()
+    yield ctx, meshes
+    ctx.close()
+
+
+def _requests(meshes, count, seed):
+    import torch
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(count):
+        c, m, node_elem = meshes[rng.integers(len(meshes))]
+        n = int(np.exp(rng.uniform(np.log(500), np.log(c.n_particles))))
+        idx = np.sort(rng.choice(c.n_particles, size=n, replace=False))
+        x = torch.from_numpy(np.ascontiguousarray(c.x[idx])).pin_memory()
+        u = torch.from_numpy(np.ascontiguousarray(c.u[idx])).pin_memory()
+        st = torch.from_numpy(np.ascontiguousarray(node_elem[idx])).pin_memory()
+        dt = dt_for_cfl(c.u, c.h, rng.uniform(1.0, 16.0))
+        mode = ["sns", "asg", "cnn"][i % 3]
+        reqs.append((m, x, u, st, dt, mode))
+    return reqs
+
+
+def _run(ctx, reqs, burst):
+    outs = [None] * len(reqs)
+    if burst:
+        tickets = [ctx.submit(m, x, u, dt, start=st, mode=mode) for m, x, u, st, dt, mode in reqs]
+        modes = [ctx.wait(t) for t, _ in tickets]
+        outs = [{k: v.numpy().copy() for k, v in o.items()} for _, o in tickets]
+    else:
+        modes = []
+        for i, (m, x, u, st, dt, mode) in enumerate(reqs):
+            t, o = ctx.submit(m, x, u, dt, start=st, mode=mode)
+            modes.append(ctx.wait(t))
+            outs[i] = {k: v.numpy().copy() for k, v in o.items()}
+    return outs, modes
+
+
+def test_results_same_alone_and_in_the_mix(setup):
+    ctx, meshes = setup
+    reqs = _requests(meshes, 36, seed=1)
+    ctx.serve_start(slots=6, arena_bytes=1 << 30)
+    try:
+        alone, modes_a = _run(ctx, reqs, burst=False)
+        mixed, modes_b = _run(ctx, reqs, burst=True)
+        rep = ctx.serve_report()
+    finally:
+        ctx.serve_stop()
+    assert modes_a == modes_b
+    for i, (a, b) in enumerate(zip(alone, mixed)):
+        for k in ("host", "path_len", "status"):
+            assert np.array_equal(a[k], b[k]), (i, k)
+    # CNN-SNS requests on the 3-D mesh fell back to plain SNS, 2-D ran CNN-SNS
+    for (m, _, _, _, _, mode), used in zip(reqs, modes_b):
+        if mode == "cnn":
+            assert used == (1 if m.dim == 2 else 0)
+    # the mix overlapped on the device and the latencies are reported
+    assert rep["completed"] == 72 and rep["rejected"] == 0
+    assert rep["max_concurrent"] > 1
+    assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+    # the serving results equal the direct host-pointer entry point
+    m, x, u, st, dt, mode = reqs[0]
+    ref = ctx.track_host(m, x.numpy(), u.numpy(), dt, start=st.numpy(), mode=mode)
+    for k in ("host", "path_len", "status"):
+        assert np.array_equal(ref[k], alone[0][k])
+
+
+def test_admission_by_footprint(setup):
+    import paper_2412_18379_gb300 as cs
+    ctx, meshes = setup
+    c, m, node_elem = meshes[0]
+    # an arena that fits about two of these requests at a time
+    n = c.n_particles
+    per = n * (2 * 2 * 8 + 4 + 4 + 4 + 1 + 4) + 8 * 256
+    ctx.serve_start(slots=8, arena_bytes=int(2.5 * per))
+    try:
+        reqs = [(m, *(__import__("torch").from_numpy(a).pin_memory()
+                      for a in (c.x, c.u, node_elem)), c.dt * (1 + i % 4), "sns")
+                for i in range(10)]
+        outs, _ = _run(ctx, reqs, burst=True)       # queues, never deadlocks
+        rep = ctx.serve_report()
+        assert rep["completed"] == 10 and rep["max_concurrent"] <= 2
+        assert rep["peak_bytes"] <= int(2.5 * per)
+        # a request that can never fit is refused at once
+        big = make_case("tg2d", n_side=401)
+        mb = ctx.upload_mesh(big.xyz, big.conn)
+        import torch
+        with pytest.raises(cs.CsError) as e:
+            ctx.submit(mb, torch.from_numpy(big.x).pin_memory(),
+                       torch.from_numpy(big.u).pin_memory(), big.dt)
+        assert e.value.code == -2
+        assert ctx.serve_report()["rejected"] == 1
+    finally:
+        ctx.serve_stop()
