@@ -35,7 +35,8 @@ namespace {
 constexpr int kTile = 24;            // output cells per tile edge
 constexpr int kW = 32;               // flat row width (= tile + 8)
 constexpr int kRows = 1024;          // pixel rows of an activation buffer
-constexpr int kThreadsTC = 256;
+constexpr int kThreadsTC = 512;      // 16 warps: 4 per TMEM lane quarter
+constexpr int kFcTiles = 5;          // 576 compacted pixels -> 5 M-tiles of fc1
 constexpr uint32_t kTmemCols = 512;
 
 // packed weights (bytes); produced by pack_weights_kernel
@@ -59,8 +60,10 @@ constexpr int kSmX0 = 0;                                    // bf16 [1152][8] (2
 constexpr int kSmAct0 = kSmX0 + kRowsX0 * 16;               // bf16 [4][1024][8]
 constexpr int kSmAct1 = kSmAct0 + 4 * kRows * 16;
 constexpr int kSmW = kSmAct1 + 4 * kRows * 16;              // packed weights
-constexpr int kSmBar = kSmW + TcLayout::total;              // mbarrier + tmem slot
+constexpr int kSmRed = kSmW + TcLayout::total;              // float2 [2][128] fc2 partials
+constexpr int kSmBar = kSmRed + 2 * 128 * 8;                // mbarrier + tmem slot
 constexpr int kSmTotal = kSmBar + 64;
+static_assert(kSmTotal <= 232448, "shared memory of one CTA");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -201,17 +204,25 @@ __device__ __forceinline__ void issue_conv1(uint32_t tmem, const uint8_t *x0, co
         }
 }
 
-// Epilogue of a conv layer: TMEM -> +bias, ReLU -> BF16 activations.
+// Epilogue of a conv layer: TMEM -> +bias, ReLU -> BF16 activations. Warp w
+// reads TMEM lane quarter w % 4 (the only one it may access) of M-tiles
+// w / 4, w / 4 + 4, ... With `compact`, pixel (y, x) goes to row y * 24 + x
+// and the garbage columns x >= 24 are dropped (input of fc1).
 __device__ __forceinline__ void epilogue_conv(uint32_t tmem, uint8_t *out, const float *bias,
-                                              int n_mt) {
+                                              int n_mt, bool compact) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = warp & 3, h = warp >> 2;
-    for (int mt = h; mt < n_mt; mt += 2) {
+    for (int mt = h; mt < n_mt; mt += kThreadsTC / 128) {
         float v[32];
         tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(32 * mt), v);
         #pragma unroll
         for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
-        store_act(out, 128 * mt + 32 * g + lane, v);
+        const int row = 128 * mt + 32 * g + lane;
+        if (!compact) {
+            store_act(out, row, v);
+        } else if (row % kW < kTile && row / kW < kTile) {
+            store_act(out, (row / kW) * kTile + row % kW, v);
+        }
     }
 }
 
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
         phase ^= 1;
         fence_after();
-        if (ok) epilogue_conv(tmem, act0, b1, 8);
+        if (ok) epilogue_conv(tmem, act0, b1, 8, false);
         fence_before();
         fence_async_smem();
         __syncthreads();
@@ -303,7 +314,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
             phase ^= 1;
             fence_after();
-            if (ok) epilogue_conv(tmem, dst, cb + 32 * l, n_mt[l]);
+            if (ok) epilogue_conv(tmem, dst, cb + 32 * l, n_mt[l], l == 2);
             fence_before();
             fence_async_smem();
             __syncthreads();
@@ -311,7 +322,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             src = dst;
             dst = tmp;
         }
-        // ---- fc1 on tcgen05 (two M-tiles of 256 columns per round), fc2 ----
+        // ---- fc1 on tcgen05 over the 576 compacted valid pixels (5 M-tiles,
+        //      two per round of 256 columns each), fc2 in the epilogue ----
         for (int round = 0; round < 3 && ok; ++round) {
             if (tid == 0) {
                 fence_after();
@@ -319,6 +331,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                 const uint32_t a0 = smem_addr(src), b0 = smem_addr(wsm + TcLayout::bfc1);
                 for (int h = 0; h < 2; ++h) {
                     const int mt = 2 * round + h;
+                    if (mt >= kFcTiles) break;
                     for (int kk = 0; kk < 2; ++kk) {
                         const uint64_t a =
                             sdesc(a0 + uint32_t((2 * kk * kRows + 128 * mt) * 16), kRows * 16, 128);
@@ -331,13 +344,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
             phase ^= 1;
             fence_after();
-            if (ok) {
-                const int g = warp & 3, h = warp >> 2;
-                const int row = 128 * (2 * round + h) + 32 * g + lane;
-                float o0 = fc2b[0], o1 = fc2b[1];
-                for (int j = 0; j < 8; ++j) {
+            // warp (g, h): M-tile 2*round + (h & 1), columns [128 (h >> 1), +128)
+            const int g = warp & 3, h = warp >> 2;
+            const int mt = 2 * round + (h & 1), half = h >> 1;
+            const int row = 128 * mt + 32 * g + lane;
+            float o0 = 0.f, o1 = 0.f;
+            if (ok && mt < kFcTiles) {
+                if (half == 0) {
+                    o0 = fc2b[0];
+                    o1 = fc2b[1];
+                }
+                for (int j = 4 * half; j < 4 * half + 4; ++j) {
                     float v[32];
-                    tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(256 * h + 32 * j), v);
+                    // M-tile (h & 1) of this round holds TMEM columns [256 (h & 1), +256)
+                    tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(256 * (h & 1) + 32 * j), v);
                     const float4 *pb = reinterpret_cast<const float4 *>(fc1b + 32 * j);
                     const float4 *p0 = reinterpret_cast<const float4 *>(fc2w + 32 * j);
                     const float4 *p1 = reinterpret_cast<const float4 *>(fc2w + 256 + 32 * j);
@@ -352,12 +372,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                         o1 = fmaf(w1.x, h0, fmaf(w1.y, h1, fmaf(w1.z, h2, fmaf(w1.w, h3, o1))));
                     }
                 }
-                const int y = row / kW, x = row % kW;
-                const int cx = tx * kTile + x, cy = ty * kTile + y;
-                if (y < kTile && x < kTile && cx < gx && cy < gy)
-                    reinterpret_cast<float2 *>(dhat)[int64_t(cy) * gx + cx] = make_float2(o0, o1);
             }
+            // the second column half hands its partial sums to the first
+            float2 *red = reinterpret_cast<float2 *>(smem + kSmRed);
+            if (half == 1) red[(h & 1) * 128 + 32 * g + lane] = make_float2(o0, o1);
             fence_before();
+            __syncthreads();
+            if (ok && half == 0 && mt < kFcTiles) {
+                const float2 p = red[(h & 1) * 128 + 32 * g + lane];
+                const int y = row / kTile, x = row % kTile;
+                const int cx = tx * kTile + x, cy = ty * kTile + y;
+                if (row < kTile * kTile && cx < gx && cy < gy)
+                    reinterpret_cast<float2 *>(dhat)[int64_t(cy) * gx + cx] =
+                        make_float2(o0 + p.x, o1 + p.y);
+            }
             __syncthreads();
         }
     }
