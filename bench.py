@@ -338,6 +338,7 @@ def main():
         dist.init_process_group("nccl")
     import paper_2412_18379_gb300 as cs
     from paper_2412_18379_gb300 import build
+    from paper_2412_18379_gb300.shard import max_over_ranks
     from workloads import make_case
 
     if rank == 0 or world == 1:
@@ -396,9 +397,7 @@ def main():
         ctx.profile(False)
         launches = ctx.launches - l0
         if dist is not None:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = max_over_ranks(total, device=dev)
             dist.barrier()
         torch.cuda.synchronize()
         st = ctx.stats(out["path_len"], out["status"])
@@ -467,9 +466,7 @@ def main():
         ctx.track_host(mesh, xh, uh, case.dt, mode=args.mode, out=hout)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, device=dev)
     e2e = {"value": world * n / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": n * dim * 16, "d2h_bytes_per_step": n * 9,
            "entry_point": "cs_track_host"}
@@ -500,7 +497,9 @@ def main():
                        "n_particles": n, "n_elements": case.n_elements,
                        "asg_grid": info["asg_grid"],
                        "l2": "flushed by a 256 MB write before every timed step",
-                       "parallelism": "replicas, particles sharded" if world > 1 else "1 GPU",
+                       "parallelism": ("%d replicas: every rank locates its own batch of %d particles "
+                                        "against its own copy of the mesh, no collective"
+                                        % (world, n)) if world > 1 else "1 GPU",
                        "arithmetic": "walk decisions FP64 (certified FP32 filter); "
                                      "predictor BF16 x BF16 -> FP32 on tcgen05"},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],
