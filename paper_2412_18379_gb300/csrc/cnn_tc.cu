@@ -7,13 +7,15 @@
 // convolutional pass over the zero-padded grid, read at c. One persistent CTA
 // per SM walks over 24 x 24-cell output tiles:
 //
-//   input   32 x 32 cells x 2 channels (tile + 4-cell halo), FP32, in smem
-//   conv1   CUDA cores, 30 x 30 x 32, ReLU, stored BF16
-//   conv2-4 tcgen05.mma kind::f16 (BF16 x BF16 -> FP32 in TMEM), implicit
-//           GEMM: M = 128 pixels, N = 32 channels, K = 16 channels of one tap;
-//           9 taps x 2 K-steps per M-tile; ReLU + BF16 in the epilogue
-//   fc1     tcgen05.mma, M = 128 pixels, N = 256, K = 32
+//   input   32 x 32 cells (tile + 4-cell halo), channels u_k dt / s_k, BF16,
+//           tap-packed: row r holds both channels of taps 0..7 at pixel r
+//   conv1   tcgen05.mma kind::f16, M = 128 pixels, N = 32: one K = 16 step
+//           for taps 0..7, one for tap 8 (a shifted read of the same rows)
+//   conv2-4 tcgen05.mma, implicit GEMM: M = 128 pixels, N = 32 channels,
+//           K = 16 channels of one tap; 9 taps x 2 K-steps per M-tile
+//   fc1     tcgen05.mma, M = 128 pixels, N = 128 (two halves of 256), K = 32
 //   fc2     CUDA cores in the fc1 epilogue (256 -> 2)
+//   (FP32 accumulators in TMEM; bias + ReLU + BF16 in the epilogues)
 //
 // Activations live in shared memory as [8-channel chunk q][pixel r][8] BF16,
 // with pixels on a flat 32-wide row-major index for every layer (columns past
@@ -21,7 +23,32 @@
 // (dy, dx) is then a shift of dy*32 + dx pixels, i.e. an offset of the MMA's
 // shared-memory descriptor: no im2col copy. The canonical no-swizzle K-major
 // layout has 8x16-byte core matrices, SBO = 128 B between 8-pixel groups and
-// LBO = 16 KiB between channel chunks.
+// LBO = 16 KiB between channel chunks. An MMA of N = 32 is bound by reading
+// its operands from shared memory (about 4 KiB of A per step), not by the
+// tensor cores' arithmetic.
+//
+// Pipeline. A tile is a sequence of 38 items (layer, M-tile): conv1 8, conv2
+// 7, conv3 7, conv4 6, fc1 5 x 2 column halves. Warp 16 issues the conv MMAs
+// and warp 18 the fc1 MMAs, each committing an item's MMAs to the item's
+// "mma" mbarrier. The 16 epilogue warps form 4 groups (one warp per TMEM lane
+// quarter): groups 0-1 take the conv items, groups 2-3 the fc1 items; a group
+// waits for the item's MMAs, runs the epilogue and counts it in the item's
+// shared-memory counter (release). Warp 19 waits for each conv item's
+// counters and releases the item to warp 16 through a named barrier, so the
+// issuing warp never loads from shared memory (such a load waits behind the
+// MMAs it has queued, and the tensor pipe drains). Warp 17 loads the next
+// tile's input while conv2..conv4 of the current one run.
+// The MMAs of item (l, m) wait only for the epilogues they read (items
+// (l-1, m) and (l-1, m+1)) and for the last user of their TMEM columns, so
+// the tensor cores run ahead of the epilogues instead of waiting for a whole
+// layer. The conv layers share TMEM columns [0, 256) (M-tile m at 32 m) and
+// fc1 owns [256, 512), so fc1 of one tile overlaps the convolutions of the
+// next. conv1..conv3 write their output over their input, in place: the rows
+// of M-tile m are read only by the MMAs of M-tiles m-1 and m, and both have
+// completed when the epilogue of m starts; conv4 writes the compacted fc1
+// input, a buffer of its own. The "mma" barrier sets alternate between even
+// and odd tiles, so a parity wait never sees a phase two tiles old; the
+// epilogue counters only grow.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -34,42 +61,85 @@ namespace {
 
 constexpr int kTile = 24;            // output cells per tile edge
 constexpr int kW = 32;               // flat row width (= tile + 8)
-constexpr int kRows = 1024;          // pixel rows of an activation buffer
-constexpr int kThreadsTC = 512;      // 16 warps: 4 per TMEM lane quarter
-constexpr int kFcTiles = 5;          // 576 compacted pixels -> 5 M-tiles of fc1
+constexpr int kRows = 1024;          // pixel rows of the activation buffer
+constexpr int kEpiWarps = 16;        // 4 groups x 4 TMEM lane quarters
+constexpr int kConvWarp = 16;        // issues the MMAs of conv1..conv4
+constexpr int kLoadWarp = 17;        // loads the tile inputs
+constexpr int kFcWarp = 18;          // issues the MMAs of fc1
+constexpr int kSchedWarp = 19;       // releases the conv items to the conv warp
+constexpr int kThreadsTC = 20 * 32;
+static_assert(kEpiWarps == kConvWarp && kLoadWarp == kConvWarp + 1 && kFcWarp == kConvWarp + 2 &&
+                  kSchedWarp == kConvWarp + 3,
+              "warp roles");
 constexpr uint32_t kTmemCols = 512;
+
+// the items of one tile
+constexpr int kItems = 38;
+constexpr int kFcTiles = 5;                  // 576 compacted pixels
+
+// first item of conv1..conv4 (l = 0..3) and fc1 (l = 4)
+__host__ __device__ constexpr int jbase(int l) {
+    return l == 0 ? 0 : l == 1 ? 8 : l == 2 ? 15 : l == 3 ? 22 : 28;
+}
+// M-tiles of conv1..conv4: 32, 28, 26, 24 pixel rows of 32
+__host__ __device__ constexpr int nmt(int l) { return l == 0 ? 8 : l == 3 ? 6 : 7; }
+static_assert(jbase(4) + 2 * kFcTiles == kItems, "item count");
 
 // packed weights (bytes); produced by pack_weights_kernel
 struct TcLayout {
-    static constexpr int w1 = 0;                          // bf16 [9][32][8]: W1/2, channels >= 2 zero
-    static constexpr int b1 = w1 + 9 * 32 * 8 * 2;        // fp32 [32]
+    static constexpr int w1 = 0;                          // bf16 [2 MMAs][2 chunks][32][8]
+    static constexpr int b1 = w1 + 2 * 2 * 32 * 8 * 2;    // fp32 [32]
     static constexpr int bconv = b1 + 32 * 4;             // 3 x bf16 [9][4][32][8]
     static constexpr int bconv_bytes = 9 * 4 * 32 * 8 * 2;
     static constexpr int cb = bconv + 3 * bconv_bytes;    // fp32 [3][32] conv biases
     static constexpr int bfc1 = cb + 3 * 32 * 4;          // bf16 [4][256][8]
     static constexpr int bfc1_bytes = 4 * 256 * 8 * 2;
-    static constexpr int fc1b = bfc1 + bfc1_bytes;        // fp32 [256]
+    static constexpr int fc1b = bfc1 + bfc1_bytes;        // fp32 [256], negated fc1 bias
     static constexpr int fc2w = fc1b + 256 * 4;           // fp32 [2][256]
-    static constexpr int fc2b = fc2w + 2 * 256 * 4;       // fp32 [2]
+    static constexpr int fc2b = fc2w + 2 * 256 * 4;       // fp32 [2], fc2 bias + W2 b1
     static constexpr int total = ((fc2b + 2 * 4) + 127) / 128 * 128;
 };
 
 // shared memory map (bytes)
-constexpr int kRowsX0 = 1152;                               // 32 x 32 input + shifted reads
-constexpr int kSmX0 = 0;                                    // bf16 [1152][8] (2 channels used)
-constexpr int kSmAct0 = kSmX0 + kRowsX0 * 16;               // bf16 [4][1024][8]
-constexpr int kSmAct1 = kSmAct0 + 4 * kRows * 16;
-constexpr int kSmW = kSmAct1 + 4 * kRows * 16;              // packed weights
-constexpr int kSmRed = kSmW + TcLayout::total;              // float2 [2][128] fc2 partials
-constexpr int kSmBar = kSmRed + 2 * 128 * 8;                // mbarrier + tmem slot
-constexpr int kSmTotal = kSmBar + 64;
+constexpr int kRowsX0 = 1096;                               // conv1 rows 0..1023 + tap-8 shift 66
+constexpr int kX0Bytes = 2 * kRowsX0 * 16;                  // bf16 [2][1096][8] tap-packed input
+constexpr int kRowsFc = kTile * kTile;                      // compacted conv4 output rows (576)
+constexpr int kSmX0 = 0;                                    // input buffer
+constexpr int kSmAct = kSmX0 + kX0Bytes;                    // bf16 [4][1024][8] conv1..conv3
+constexpr int kSmFc = kSmAct + 4 * kRows * 16;              // bf16 [4][576][8] conv4 -> fc1
+
+constexpr int kSmW = kSmFc + 4 * kRowsFc * 16;              // packed weights
+constexpr int kSmRed = kSmW + TcLayout::total;              // float2 [2][5][128] fc2 partials
+constexpr int kSmBar = kSmRed + 2 * kFcTiles * 128 * 8;
+constexpr int kBarMma = 0;                                  // [2][kItems]
+constexpr int kBarEmpty = 2 * kItems;                       // input buffer consumed by conv1
+constexpr int kBarFinal = kBarEmpty + 1;                    // [2] each issuing warp's last MMAs
+constexpr int kNumBars = kBarFinal + 2;
+constexpr int kWinRows = kW + 6;                            // window rows + zero rows
+constexpr int kSmWin = kSmBar + kNumBars * 8;               // u32 [38][32] input window (BF16 x2)
+constexpr int kSmCnt = kSmWin + kWinRows * kW * 4;          // u32 [kItems + 7] counters
+constexpr int kCntX0 = kItems;                              // counter: tile inputs loaded
+constexpr int kCntT4 = kItems + 1;                          // [6] conv4 M-tile read out of TMEM
+constexpr int kNumCnt = kCntT4 + 6;
+constexpr int kSmSlot = kSmCnt + kNumCnt * 4;               // TMEM address, abort flag
+constexpr int kSmTotal = kSmSlot + 16;
 static_assert(kSmTotal <= 232448, "shared memory of one CTA");
+// fc1 M-tile 4 reads rows 512..639 of each chunk: past row 575 it reads the
+// next chunk (or, for the last chunk, the weights that follow), garbage rows
+// whose outputs are dropped
+static_assert(kSmFc + (3 * kRowsFc + 128 * kFcTiles) * 16 <= kSmTotal, "fc1 reads in bounds");
+static_assert(kRowsX0 >= 128 * 8 + 2 * kW + 2, "conv1 reads in bounds");
+static_assert(kRowsX0 - 1 + 2 * kW + 1 < kWinRows * kW, "window reads in bounds");
+static_assert(kSmBar % 8 == 0, "mbarrier alignment");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// shared-memory matrix descriptor: no swizzle, K-major core matrices
+// shared-memory matrix descriptor: no swizzle, K-major core matrices. The
+// start address sits in the low 14 bits in 16-byte units; every operand here
+// lies below 256 KiB, so adding a 16-byte offset to a descriptor never
+// carries out of that field.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     return uint64_t((addr >> 4) & 0x3fff) | (uint64_t((lbo >> 4) & 0x3fff) << 16) |
            (uint64_t((sbo >> 4) & 0x3fff) << 32) | (uint64_t(1) << 46);
@@ -90,11 +160,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t a, uint64_t b, ui
         "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
+// arrive on `bar` once all MMAs issued so far by this thread have completed
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_addr(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -109,14 +184,80 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: false (and the error flag set) if the MMAs never complete
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+// Bounded wait for the phase of `bar` with the given parity. Gives up (false)
+// when another thread has raised the CTA's abort flag, or after 2^24 polls,
+// in which case it raises the flag and the device error flag itself.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err) {
     for (uint32_t i = 0; i < (1u << 24); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
         if (i > 64) __nanosleep(64);
     }
+    *abort_flag = 1;
     atomicExch(err, 1);
     return false;
+}
+
+// warp-uniform bounded wait: every lane polls, the warp agrees on the result
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err) {
+    return __all_sync(kFull, mbar_wait(bar, parity, abort_flag, err)) != 0;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v)
+                 : "memory");
+}
+
+// Bounded wait until the counter *cnt reaches `target` (acquire). A plain
+// shared-memory load is much cheaper than an mbarrier test, which matters on
+// the MMA-issuing warp: the tensor pipe's issue queue is shallow, so every
+// cycle that warp spends waiting is a cycle the tensor cores may idle. All
+// lanes of a converged warp load the same word in one instruction, so the
+// result is warp-uniform.
+__device__ __forceinline__ bool wait_count(const uint32_t *cnt, uint32_t target,
+                                           volatile int *abort_flag, int *err) {
+    for (uint32_t i = 0; i < (1u << 26); ++i) {
+        if (ld_acquire(cnt) >= target) return true;
+        if (*abort_flag) return false;
+        if (i > 256) __nanosleep(32);
+    }
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+// Named barrier 1 between the conv warp and the scheduler warp (64 threads),
+// with an OR over both warps' flags: both get the same answer.
+__device__ __forceinline__ bool handoff_or(bool flag) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, 64, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(r)
+        : "r"(uint32_t(flag))
+        : "memory");
+    return r != 0;
+}
+
+// true in exactly one lane of the (converged) warp
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(pred));
+    return pred != 0;
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -154,76 +295,89 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 // Store one pixel's 32 channels (ReLU already applied) into an activation
-// buffer in the chunked layout.
-__device__ __forceinline__ void store_act(uint8_t *buf, int row, const float *v) {
+// buffer in the chunked layout ([4 chunks][rows][8] BF16).
+template <int ROWS>
+__device__ __forceinline__ void store_act(uint8_t *buf, int row, const uint32_t *hv) {
     #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint4 w;
-        w.x = pack_bf16x2(v[8 * q + 0], v[8 * q + 1]);
-        w.y = pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
-        w.z = pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
-        w.w = pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
-        *reinterpret_cast<uint4 *>(buf + (size_t(q) * kRows + row) * 16) = w;
+    for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(buf + (size_t(q) * ROWS + row) * 16) =
+            make_uint4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+}
+
+// hv = BF16 pairs of ReLU(v + bias) over 32 channels. The bias is added in FP32
+// pairs and ReLU taken on the rounded BF16 pairs: rounding to nearest is
+// monotone and keeps 0, so this equals rounding ReLU(v + bias).
+__device__ __forceinline__ void bias_relu_bf16(const float *v, const float *bias, uint32_t *hv) {
+    const __nv_bfloat162 zero = __float2bfloat162_rn(0.f);
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float4 b = reinterpret_cast<const float4 *>(bias)[e];
+        const float2 s0 = __fadd2_rn(make_float2(v[4 * e], v[4 * e + 1]), make_float2(b.x, b.y));
+        const float2 s1 = __fadd2_rn(make_float2(v[4 * e + 2], v[4 * e + 3]), make_float2(b.z, b.w));
+        const __nv_bfloat162 h0 = __hmax2(__floats2bfloat162_rn(s0.x, s0.y), zero);
+        const __nv_bfloat162 h1 = __hmax2(__floats2bfloat162_rn(s1.x, s1.y), zero);
+        hv[2 * e] = *reinterpret_cast<const uint32_t *>(&h0);
+        hv[2 * e + 1] = *reinterpret_cast<const uint32_t *>(&h1);
     }
 }
 
-// Issue the MMAs of one 3x3 convolution layer (called by one thread):
-// n_mt M-tiles of 128 pixels, TMEM columns [32*mt, 32*mt + 32).
-__device__ __forceinline__ void issue_conv(uint32_t tmem, const uint8_t *act, const uint8_t *wb,
-                                           int n_mt) {
-    constexpr uint32_t id = idesc_bf16(128, 32);
-    const uint32_t a0 = smem_addr(act), b0 = smem_addr(wb);
-    for (int mt = 0; mt < n_mt; ++mt) {
-        uint32_t acc = 0;
-        for (int t = 0; t < 9; ++t) {
-            const int shift = (t / 3) * kW + (t % 3);
-            for (int kk = 0; kk < 2; ++kk) {
-                const uint64_t a = sdesc(a0 + uint32_t((2 * kk * kRows + 128 * mt + shift) * 16),
-                                         kRows * 16, 128);
-                const uint64_t b = sdesc(b0 + uint32_t(((t * 4 + 2 * kk) * 32) * 16), 32 * 16, 128);
-                mma_bf16(tmem + uint32_t(32 * mt), a, b, id, acc);
-                acc = 1;
-            }
-        }
-    }
+// TMEM columns of an item: every conv layer uses [32 m, +32) for M-tile m
+// (so conv M-tile m of layer l reuses the columns of layer l - 1, whose
+// epilogue it waits for anyway); fc1 column half h uses [256 + 128 h, +128).
+__device__ __forceinline__ uint32_t item_col(int l, int m) {
+    return l < 4 ? uint32_t(32 * m) : uint32_t(256 + 128 * (m & 1));
 }
 
-// Issue the MMAs of conv1 (called by one thread): the input has one 8-channel
-// chunk (u0, u1, 0 ... 0); a K = 16 step reads that chunk twice (LBO = 0 on
-// both operands) against halved weights, so the sum is the 8-channel product.
-// 8 M-tiles cover the 30 valid rows (rows past them are garbage).
-__device__ __forceinline__ void issue_conv1(uint32_t tmem, const uint8_t *x0, const uint8_t *wb) {
-    constexpr uint32_t id = idesc_bf16(128, 32);
-    const uint32_t a0 = smem_addr(x0), b0 = smem_addr(wb);
-    for (int mt = 0; mt < 8; ++mt)
-        for (int t = 0; t < 9; ++t) {
-            const int shift = (t / 3) * kW + (t % 3);
-            const uint64_t a = sdesc(a0 + uint32_t((128 * mt + shift) * 16), 0, 128);
-            const uint64_t b = sdesc(b0 + uint32_t(t * 32 * 16), 0, 128);
-            mma_bf16(tmem + uint32_t(32 * mt), a, b, id, t > 0 ? 1u : 0u);
-        }
+// conv4 M-tiles whose compacted rows [96 m, 96 m + 96) feed fc1 M-tile f,
+// i.e. rows [128 f, 128 f + 128): m in [fc_lo(f), fc_hi(f)]
+__host__ __device__ constexpr int fc_lo(int f) { return (128 * f) / 96; }
+__host__ __device__ constexpr int fc_hi(int f) {
+    return (128 * f + 127) / 96 < 5 ? (128 * f + 127) / 96 : 5;
 }
 
-// Epilogue of a conv layer: TMEM -> +bias, ReLU -> BF16 activations. Warp w
-// reads TMEM lane quarter w % 4 (the only one it may access) of M-tiles
-// w / 4, w / 4 + 4, ... With `compact`, pixel (y, x) goes to row y * 24 + x
-// and the garbage columns x >= 24 are dropped (input of fc1).
-__device__ __forceinline__ void epilogue_conv(uint32_t tmem, uint8_t *out, const float *bias,
-                                              int n_mt, bool compact) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = warp & 3, h = warp >> 2;
-    for (int mt = h; mt < n_mt; mt += kThreadsTC / 128) {
-        float v[32];
-        tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(32 * mt), v);
+__device__ __forceinline__ void item_decode(int j, int &l, int &m) {
+    l = j < jbase(1) ? 0 : j < jbase(2) ? 1 : j < jbase(3) ? 2 : j < jbase(4) ? 3 : 4;
+    m = j - jbase(l);
+}
+
+// MMAs of M-tile m of conv layer l (l >= 1): 9 taps x 2 K-steps, accumulate
+// into TMEM columns [col, col + 32).
+__device__ __forceinline__ void issue_conv(uint32_t dcol, uint64_t adesc, uint64_t bdesc, int m) {
+    constexpr uint32_t id = idesc_bf16(128, 32);
+    #pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        const int shift = (t / 3) * kW + (t % 3);
         #pragma unroll
-        for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + bias[c], 0.f);
-        const int row = 128 * mt + 32 * g + lane;
-        if (!compact) {
-            store_act(out, row, v);
-        } else if (row % kW < kTile && row / kW < kTile) {
-            store_act(out, (row / kW) * kTile + row % kW, v);
+        for (int kk = 0; kk < 2; ++kk) {
+            // offsets in 16-byte units: A chunk pair kk, pixel row 128 m + shift;
+            // B tap t, chunk pair kk (32 rows of 16 B per chunk)
+            const uint64_t a = adesc + uint64_t(2 * kk * kRows + 128 * m + shift);
+            const uint64_t b = bdesc + uint64_t((t * 4 + 2 * kk) * 32);
+            mma_bf16(dcol, a, b, id, (t | kk) != 0 ? 1u : 0u);
         }
     }
+}
+
+// MMAs of M-tile m of conv1 on the tap-packed input: row r holds, in K order,
+// channels (u0, u1) of taps 0..7 at pixel r (shifts 0, 1, 2, 32, 33, 34, 64,
+// 65). One K = 16 step covers taps 0..7; a second reads the rows 66 pixels
+// further on, whose first tap is tap 8 of pixel r, against weights that are
+// zero past K = 2.
+__device__ __forceinline__ void issue_conv1(uint32_t dcol, uint64_t adesc, uint64_t bdesc, int m) {
+    constexpr uint32_t id = idesc_bf16(128, 32);
+    mma_bf16(dcol, adesc + uint64_t(128 * m), bdesc, id, 0u);
+    mma_bf16(dcol, adesc + uint64_t(128 * m + 2 * kW + 2), bdesc + uint64_t(2 * 32), id, 1u);
+}
+
+// MMAs of column half h of fc1 M-tile f: 128 compacted pixels x 128 features,
+// K = 32 in two steps.
+__device__ __forceinline__ void issue_fc1(uint32_t dcol, uint64_t adesc, uint64_t bdesc, int f,
+                                          int h) {
+    constexpr uint32_t id = idesc_bf16(128, 128);
+    #pragma unroll
+    for (int kk = 0; kk < 2; ++kk)
+        mma_bf16(dcol, adesc + uint64_t(2 * kk * kRowsFc + 128 * f),
+                 bdesc + uint64_t(2 * kk * 256 + 128 * h), id, uint32_t(kk));
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
@@ -231,21 +385,33 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *x0 = smem + kSmX0;
-    uint8_t *act0 = smem + kSmAct0;
-    uint8_t *act1 = smem + kSmAct1;
+    uint8_t *act = smem + kSmAct;
+    uint8_t *fcin = smem + kSmFc;
     uint8_t *wsm = smem + kSmW;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kSmBar);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmBar + 8);
+    float2 *red = reinterpret_cast<float2 *>(smem + kSmRed);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmSlot);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kSmSlot + 4);
+    // epi_cnt[j] counts the epilogues of item j finished over this CTA's tiles,
+    // 4 per tile (one per lane-quarter warp): item j of local tile k is done
+    // once epi_cnt[j] >= 4 (k + 1)
+    uint32_t *epi_cnt = reinterpret_cast<uint32_t *>(smem + kSmCnt);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gx = m.ga[0], gy = m.ga[1];
     const int tiles_x = (gx + kTile - 1) / kTile, tiles_y = (gy + kTile - 1) / kTile;
     const int n_tiles = tiles_x * tiles_y;
 
-    // weights into shared memory (once per CTA)
+    // weights into shared memory (once per CTA), zeroed buffers, barriers
     for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(wsm)[i] = reinterpret_cast<const uint4 *>(packed)[i];
+    for (int i = tid; i < kSmW / 16; i += kThreadsTC)
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kWinRows * kW; i += kThreadsTC)
+        reinterpret_cast<uint32_t *>(smem + kSmWin)[i] = 0u;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+        for (int i = 0; i < kNumBars; ++i) mbar_init(bars + i, 1u);
+        for (int i = 0; i < kNumCnt; ++i) epi_cnt[i] = 0;
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -254,139 +420,258 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // zero the activation rows past the computed pixels (read only by garbage)
-    for (int i = tid; i < 4 * kRows; i += kThreadsTC) {
-        reinterpret_cast<uint4 *>(act0)[i] = make_uint4(0, 0, 0, 0);
-        reinterpret_cast<uint4 *>(act1)[i] = make_uint4(0, 0, 0, 0);
-    }
-    for (int i = tid; i < kRowsX0; i += kThreadsTC)
-        reinterpret_cast<uint4 *>(x0)[i] = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    const float *b1 = reinterpret_cast<const float *>(wsm + TcLayout::b1);
-    const float *cb = reinterpret_cast<const float *>(wsm + TcLayout::cb);
-    const float *fc1b = reinterpret_cast<const float *>(wsm + TcLayout::fc1b);
-    const float *fc2w = reinterpret_cast<const float *>(wsm + TcLayout::fc2w);
-    const float *fc2b = reinterpret_cast<const float *>(wsm + TcLayout::fc2b);
-    uint32_t phase = 0;
-    bool ok = true;
+    uint64_t *bar_mma = bars + kBarMma;
 
-    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-        const int tx = tile % tiles_x, ty = tile / tiles_x;
-        const int cx0 = tx * kTile - 4, cy0 = ty * kTile - 4;
-        // ---- input: 32 x 32 cells, channels u_k * dt / s_k (BF16), zero outside ----
-        for (int i = tid; i < kW * kW; i += kThreadsTC) {
-            const int cx = cx0 + (i % kW), cy = cy0 + (i / kW);
-            float u0 = 0.f, u1 = 0.f;
-            if (cx >= 0 && cx < gx && cy >= 0 && cy < gy) {
-                const float2 uv = __ldg(reinterpret_cast<const float2 *>(U) + int64_t(cy) * gx + cx);
-                u0 = uv.x * scale0;
-                u1 = uv.y * scale1;
+    if (warp == kLoadWarp) {
+        // ---- inputs: 32 x 32 cells, channels u_k dt / s_k (BF16), zero outside.
+        //      One buffer: tile k + 1 is loaded while conv2..conv4 of tile k run ----
+        for (int k = 0;; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= n_tiles) break;
+            if (k >= 1 &&
+                !warp_wait(bars + kBarEmpty, uint32_t(k - 1) & 1u, abort_flag, err))
+                break;
+            const int tx = tile % tiles_x, ty = tile / tiles_x;
+            const int cx0 = tx * kTile - 4, cy0 = ty * kTile - 4;
+            // the 32 x 32 window, scaled, as BF16 pairs; rows 32.. stay zero
+            uint32_t *win = reinterpret_cast<uint32_t *>(smem + kSmWin);
+            #pragma unroll 8
+            for (int y = 0; y < kW; ++y) {
+                const int cx = cx0 + lane, cy = cy0 + y;
+                float2 uv = make_float2(0.f, 0.f);
+                if (cx >= 0 && cx < gx && cy >= 0 && cy < gy)
+                    uv = __ldg(reinterpret_cast<const float2 *>(U) + int64_t(cy) * gx + cx);
+                win[y * kW + lane] = pack_bf16x2(uv.x * scale0, uv.y * scale1);
             }
-            reinterpret_cast<uint4 *>(x0)[i] = make_uint4(pack_bf16x2(u0, u1), 0, 0, 0);
+            __syncwarp();
+            // tap-packed rows: taps 0..7 of pixel r are pixels r + 32 dy + dx
+            uint4 *xv = reinterpret_cast<uint4 *>(x0);
+            #pragma unroll 2
+            for (int r = lane; r < kRowsX0; r += kW) {
+                const uint32_t *p = win + r;
+                xv[r] = make_uint4(p[0], p[1], p[2], p[kW]);
+                xv[kRowsX0 + r] = make_uint4(p[kW + 1], p[kW + 2], p[2 * kW], p[2 * kW + 1]);
+            }
+            __syncwarp();
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) red_release_add(epi_cnt + kCntX0, 1u);
         }
-        fence_async_smem();
-        __syncthreads();
-        // ---- conv1 on tcgen05 -> act0 ----
-        if (tid == 0) {
-            fence_after();
-            issue_conv1(tmem, x0, wsm + TcLayout::w1);
-            mma_commit(bar);
-        }
-        ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
-        phase ^= 1;
-        fence_after();
-        if (ok) epilogue_conv(tmem, act0, b1, 8, false);
-        fence_before();
-        fence_async_smem();
-        __syncthreads();
-        // ---- conv2, conv3, conv4 on tcgen05 ----
-        const int n_mt[3] = {7, 7, 6};      // 28, 26, 24 valid rows of 32 pixels
-        uint8_t *src = act0, *dst = act1;
-        for (int l = 0; l < 3 && ok; ++l) {
-            if (tid == 0) {
+    } else if (warp == kConvWarp) {
+        // ---- conv MMAs: the whole warp runs the schedule (descriptors and
+        //      waits stay warp-uniform), one elected lane issues ----
+        const uint64_t d_act = sdesc(smem_addr(act), kRows * 16, 128);
+        const uint64_t d_x0 = sdesc(smem_addr(x0), kRowsX0 * 16, 128);
+        const uint64_t d_w1 = sdesc(smem_addr(wsm + TcLayout::w1), 32 * 16, 128);
+        const uint64_t d_wc = sdesc(smem_addr(wsm + TcLayout::bconv), 32 * 16, 128);
+        const bool leader = elect_one();
+        // The scheduler warp waits for each item's dependencies and releases it
+        // through named barrier 1: a shared-memory load issued here would wait
+        // behind the MMAs this warp has queued, and the tensor pipe would drain.
+        bool stop = false;
+        for (int k = 0; !stop; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= n_tiles) break;
+            uint64_t *mma_s = bar_mma + (k & 1) * kItems;
+            for (int c = 0; c < jbase(4); ++c) {
+                stop = handoff_or(false);
+                if (stop) break;
+                int l, mt;
+                item_decode(c, l, mt);
                 fence_after();
-                issue_conv(tmem, src, wsm + TcLayout::bconv + l * TcLayout::bconv_bytes, n_mt[l]);
-                mma_commit(bar);
+                if (leader) {
+                    if (l == 0) {
+                        issue_conv1(tmem + uint32_t(32 * mt), d_x0, d_w1, mt);
+                    } else {
+                        const uint64_t d_w = d_wc + uint64_t((l - 1) * (TcLayout::bconv_bytes / 16));
+                        issue_conv(tmem + uint32_t(32 * mt), d_act, d_w, mt);
+                    }
+                    mma_commit(mma_s + c);
+                    if (c == nmt(0) - 1) mma_commit(bars + kBarEmpty);   // input buffer free again
+                }
+                __syncwarp();
             }
-            ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
-            phase ^= 1;
+        }
+        // wait (bounded) for this warp's MMAs in flight before TMEM is released
+        if (leader) {
+            mma_commit(bars + kBarFinal);
+            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + kBarFinal, 0); ++i)
+                if (i > 64) __nanosleep(64);
+        }
+        __syncwarp();
+    } else if (warp == kFcWarp) {
+        // ---- fc1 MMAs, half h of M-tile f into columns [256 + 128 h, +128): they
+        //      run while the next tile's convolutions use columns [0, 256) ----
+        const uint64_t d_fc = sdesc(smem_addr(fcin), kRowsFc * 16, 128);
+        const uint64_t d_fc1 = sdesc(smem_addr(wsm + TcLayout::bfc1), 256 * 16, 128);
+        const bool leader = elect_one();
+        bool ok = true;
+        for (int k = 0; ok; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= n_tiles) break;
+            uint64_t *mma_s = bar_mma + (k & 1) * kItems;
+            const uint32_t done = 4u * uint32_t(k + 1);
+            const uint32_t done_p = 4u * uint32_t(k);
+            for (int f = 0; f < kFcTiles && ok; ++f) {
+                for (int h = 0; h < 2 && ok; ++h) {
+                    // input: the conv4 M-tiles that wrote compacted rows [128 f, +128)
+                    for (int q = fc_lo(f); q <= fc_hi(f) && ok && h == 0; ++q)
+                        ok = wait_count(epi_cnt + jbase(3) + q, done, abort_flag, err);
+                    // columns: last used by M-tile f - 1 (same half) or the previous tile's M-tile 4
+                    if (ok && f > 0)
+                        ok = wait_count(epi_cnt + jbase(4) + 2 * (f - 1) + h, done, abort_flag, err);
+                    else if (ok && k > 0)
+                        ok = wait_count(epi_cnt + jbase(4) + 8 + h, done_p, abort_flag, err);
+                    if (!ok) break;
+                    fence_after();
+                    if (leader) {
+                        issue_fc1(tmem + item_col(4, h), d_fc, d_fc1, f, h);
+                        mma_commit(mma_s + jbase(4) + 2 * f + h);
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (leader) {
+            mma_commit(bars + kBarFinal + 1);
+            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + kBarFinal + 1, 0); ++i)
+                if (i > 64) __nanosleep(64);
+        }
+        __syncwarp();
+    } else if (warp == kSchedWarp) {
+        // ---- releases conv item c of tile k to the conv warp once its inputs
+        //      are ready: conv1 M-tile mt needs the tile's input and its TMEM
+        //      columns back from the previous tile (conv4 for mt <= 5, conv3 for
+        //      mt = 6, conv1 for mt = 7); conv2..conv4 M-tile mt needs the
+        //      previous layer's M-tiles mt and mt + 1 ----
+        bool ok = true, stop = false;
+        for (int k = 0; !stop; ++k) {
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= n_tiles) break;
+            for (int c = 0; c < jbase(4); ++c) {
+                int l, mt;
+                item_decode(c, l, mt);
+                if (ok && l == 0) {
+                    if (k > 0) {
+                        const int jl = mt <= 5 ? kCntT4 + mt : mt == 6 ? jbase(2) + 6 : jbase(0) + 7;
+                        ok = wait_count(epi_cnt + jl, 4u * uint32_t(k), abort_flag, err);
+                    }
+                    if (ok && mt == 0)
+                        ok = wait_count(epi_cnt + kCntX0, uint32_t(k + 1), abort_flag, err);
+                } else if (ok) {
+                    const uint32_t done = 4u * uint32_t(k + 1);
+                    ok = wait_count(epi_cnt + jbase(l - 1) + mt, done, abort_flag, err);
+                    if (ok && mt + 1 < nmt(l - 1))
+                        ok = wait_count(epi_cnt + jbase(l - 1) + mt + 1, done, abort_flag, err);
+                }
+                stop = handoff_or(!ok || *abort_flag != 0);
+                if (stop) break;
+            }
+        }
+    } else {
+        // ---- epilogues: groups 0 and 1 take the conv items of the CTA's sequence
+        //      alternately, groups 2 and 3 the fc1 items, so a conv epilogue never
+        //      queues behind the longer fc1 epilogues of the previous tile ----
+        const int g = warp >> 2, q = warp & 3;
+        constexpr int kConvItems = jbase(4), kFcItems = kItems - jbase(4);
+        const float *b1 = reinterpret_cast<const float *>(wsm + TcLayout::b1);
+        const float *cb = reinterpret_cast<const float *>(wsm + TcLayout::cb);
+        const float *fc1b = reinterpret_cast<const float *>(wsm + TcLayout::fc1b);
+        const float *fc2w = reinterpret_cast<const float *>(wsm + TcLayout::fc2w);
+        const float *fc2b = reinterpret_cast<const float *>(wsm + TcLayout::fc2b);
+        const uint32_t tq = tmem + (uint32_t(32 * q) << 16);     // this warp's lane quarter
+        for (int n = g & 1;; n += 2) {
+            const int k = g < 2 ? n / kConvItems : n / kFcItems;
+            const int j = g < 2 ? n - k * kConvItems : jbase(4) + n - k * kFcItems;
+            const int tile = blockIdx.x + k * gridDim.x;
+            if (tile >= n_tiles) break;
+            const int s = k & 1;
+            const uint32_t par = uint32_t(k >> 1) & 1u;
+            if (!__all_sync(kFull, mbar_wait(bar_mma + s * kItems + j, par, abort_flag, err)))
+                break;
             fence_after();
-            if (ok) epilogue_conv(tmem, dst, cb + 32 * l, n_mt[l], l == 2);
+            int l, mt;
+            item_decode(j, l, mt);
+            if (l < 4) {
+                float v[32];
+                tmem_ld32(tq + item_col(l, mt), v);
+                if (l == 3) {
+                    // conv4's columns are free for the next tile's conv1 now
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) red_release_add(epi_cnt + kCntT4 + mt, 1u);
+                }
+                uint32_t hv[16];
+                bias_relu_bf16(v, l == 0 ? b1 : cb + 32 * (l - 1), hv);
+                const int row = 128 * mt + 32 * q + lane;
+                if (l < 3) {
+                    store_act<kRows>(act, row, hv);
+                } else {
+                    // conv4: pixel (y, x) -> compacted row 24 y + x of the fc1 input,
+                    // once the previous tile's fc1 M-tiles that read rows [96 mt, +96)
+                    // are done (their epilogues end long before, so this is one load)
+                    bool ok = true;
+                    for (int f = (96 * mt) / 128; f <= (96 * mt + 95) / 128 && ok && k > 0; ++f)
+                        ok = wait_count(epi_cnt + jbase(4) + 2 * f + 1, 4u * uint32_t(k), abort_flag,
+                                        err);
+                    if (!ok) break;
+                    if (row % kW < kTile && row / kW < kTile)
+                        store_act<kRowsFc>(fcin, (row / kW) * kTile + row % kW, hv);
+                }
+            } else {
+                // fc1 half h of M-tile f: 128 features, their part of fc2. With the
+                // packed weights holding -b1 and the fc2 bias plus W2 b1,
+                // W2 ReLU(z + b1) = W2 max(z, -b1) + W2 b1 costs one max and one
+                // paired FMA per feature and output.
+                const int f = mt >> 1, h = mt & 1;
+                float2 a0 = make_float2(h == 0 ? fc2b[0] : 0.f, 0.f), b0 = make_float2(0.f, 0.f);
+                float2 a1 = make_float2(h == 0 ? fc2b[1] : 0.f, 0.f), b1v = make_float2(0.f, 0.f);
+                #pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    float v[32];
+                    tmem_ld32(tq + item_col(4, h) + uint32_t(32 * c), v);   // one wait per 32 columns
+                    const int n0 = 128 * h + 32 * c;
+                    const float4 *pb = reinterpret_cast<const float4 *>(fc1b + n0);   // -b1
+                    const float4 *p0 = reinterpret_cast<const float4 *>(fc2w + n0);
+                    const float4 *p1 = reinterpret_cast<const float4 *>(fc2w + 256 + n0);
+                    #pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float4 nb = pb[e], w0 = p0[e], w1 = p1[e];
+                        const float2 h01 = make_float2(fmaxf(v[4 * e], nb.x), fmaxf(v[4 * e + 1], nb.y));
+                        const float2 h23 =
+                            make_float2(fmaxf(v[4 * e + 2], nb.z), fmaxf(v[4 * e + 3], nb.w));
+                        a0 = __ffma2_rn(make_float2(w0.x, w0.y), h01, a0);
+                        b0 = __ffma2_rn(make_float2(w0.z, w0.w), h23, b0);
+                        a1 = __ffma2_rn(make_float2(w1.x, w1.y), h01, a1);
+                        b1v = __ffma2_rn(make_float2(w1.z, w1.w), h23, b1v);
+                    }
+                }
+                const float o0 = (a0.x + a0.y) + (b0.x + b0.y), o1 = (a1.x + a1.y) + (b1v.x + b1v.y);
+                float2 *slot = red + (s * kFcTiles + f) * 128 + 32 * q + lane;
+                if (h == 0) {
+                    *slot = make_float2(o0, o1);
+                } else {
+                    // the first half (the previous item) left its partial sums in `slot`
+                    if (!wait_count(epi_cnt + j - 1, 4u * uint32_t(k + 1), abort_flag, err)) break;
+                    const float2 p = *slot;
+                    const int row = 128 * f + 32 * q + lane;
+                    const int y = row / kTile, x = row % kTile;
+                    const int tx = tile % tiles_x, ty = tile / tiles_x;
+                    const int cx = tx * kTile + x, cy = ty * kTile + y;
+                    if (row < kTile * kTile && cx < gx && cy < gy)
+                        reinterpret_cast<float2 *>(dhat)[int64_t(cy) * gx + cx] =
+                            make_float2(p.x + o0, p.y + o1);
+                }
+            }
             fence_before();
             fence_async_smem();
-            __syncthreads();
-            uint8_t *tmp = src;
-            src = dst;
-            dst = tmp;
-        }
-        // ---- fc1 on tcgen05 over the 576 compacted valid pixels (5 M-tiles,
-        //      two per round of 256 columns each), fc2 in the epilogue ----
-        for (int round = 0; round < 3 && ok; ++round) {
-            if (tid == 0) {
-                fence_after();
-                constexpr uint32_t id = idesc_bf16(128, 256);
-                const uint32_t a0 = smem_addr(src), b0 = smem_addr(wsm + TcLayout::bfc1);
-                for (int h = 0; h < 2; ++h) {
-                    const int mt = 2 * round + h;
-                    if (mt >= kFcTiles) break;
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t a =
-                            sdesc(a0 + uint32_t((2 * kk * kRows + 128 * mt) * 16), kRows * 16, 128);
-                        const uint64_t b = sdesc(b0 + uint32_t(2 * kk * 256 * 16), 256 * 16, 128);
-                        mma_bf16(tmem + uint32_t(256 * h), a, b, id, kk);
-                    }
-                }
-                mma_commit(bar);
-            }
-            ok = __syncthreads_and(mbar_wait(bar, phase, err)) != 0;   // uniform
-            phase ^= 1;
-            fence_after();
-            // warp (g, h): M-tile 2*round + (h & 1), columns [128 (h >> 1), +128)
-            const int g = warp & 3, h = warp >> 2;
-            const int mt = 2 * round + (h & 1), half = h >> 1;
-            const int row = 128 * mt + 32 * g + lane;
-            float o0 = 0.f, o1 = 0.f;
-            if (ok && mt < kFcTiles) {
-                if (half == 0) {
-                    o0 = fc2b[0];
-                    o1 = fc2b[1];
-                }
-                for (int j = 4 * half; j < 4 * half + 4; ++j) {
-                    float v[32];
-                    // M-tile (h & 1) of this round holds TMEM columns [256 (h & 1), +256)
-                    tmem_ld32(tmem + (uint32_t(32 * g) << 16) + uint32_t(256 * (h & 1) + 32 * j), v);
-                    const float4 *pb = reinterpret_cast<const float4 *>(fc1b + 32 * j);
-                    const float4 *p0 = reinterpret_cast<const float4 *>(fc2w + 32 * j);
-                    const float4 *p1 = reinterpret_cast<const float4 *>(fc2w + 256 + 32 * j);
-                    #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float4 bb = pb[c], w0 = p0[c], w1 = p1[c];
-                        const float h0 = fmaxf(v[4 * c] + bb.x, 0.f);
-                        const float h1 = fmaxf(v[4 * c + 1] + bb.y, 0.f);
-                        const float h2 = fmaxf(v[4 * c + 2] + bb.z, 0.f);
-                        const float h3 = fmaxf(v[4 * c + 3] + bb.w, 0.f);
-                        o0 = fmaf(w0.x, h0, fmaf(w0.y, h1, fmaf(w0.z, h2, fmaf(w0.w, h3, o0))));
-                        o1 = fmaf(w1.x, h0, fmaf(w1.y, h1, fmaf(w1.z, h2, fmaf(w1.w, h3, o1))));
-                    }
-                }
-            }
-            // the second column half hands its partial sums to the first
-            float2 *red = reinterpret_cast<float2 *>(smem + kSmRed);
-            if (half == 1) red[(h & 1) * 128 + 32 * g + lane] = make_float2(o0, o1);
-            fence_before();
-            __syncthreads();
-            if (ok && half == 0 && mt < kFcTiles) {
-                const float2 p = red[(h & 1) * 128 + 32 * g + lane];
-                const int y = row / kTile, x = row % kTile;
-                const int cx = tx * kTile + x, cy = ty * kTile + y;
-                if (row < kTile * kTile && cx < gx && cy < gy)
-                    reinterpret_cast<float2 *>(dhat)[int64_t(cy) * gx + cx] =
-                        make_float2(o0 + p.x, o1 + p.y);
-            }
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) red_release_add(epi_cnt + j, 1u);
         }
     }
     fence_before();
@@ -404,11 +689,14 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, uint8_t *__rest
                                     int64_t off_w4, int64_t off_b4, int64_t off_f1w,
                                     int64_t off_f1b, int64_t off_f2w, int64_t off_f2b) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    // conv1 W[o][i][t] (i < 2) -> [t][o][8] halved (each K step reads it twice)
+    // conv1 W[o][i][t] -> [mma][chunk][o][8]; K index kk = 8 chunk + j is
+    // (tap kk / 2, channel kk % 2) for MMA 0 (taps 0..7), (tap 8, channel kk)
+    // for kk < 2 in MMA 1 and zero past it
     __nv_bfloat16 *w1 = reinterpret_cast<__nv_bfloat16 *>(out + TcLayout::w1);
-    for (int e = tid; e < 9 * 32 * 8; e += nth) {
-        const int t = e / 256, o = (e / 8) % 32, j = e % 8;
-        w1[e] = __float2bfloat16_rn(j < 2 ? 0.5f * w[off_w1 + (o * 2 + j) * 9 + t] : 0.f);
+    for (int e = tid; e < 2 * 2 * 32 * 8; e += nth) {
+        const int mm = e / 512, o = (e / 8) % 32, kk = 8 * ((e / 256) % 2) + e % 8;
+        const int t = mm == 0 ? kk / 2 : 8, i = kk % 2;
+        w1[e] = __float2bfloat16_rn(mm == 0 || kk < 2 ? w[off_w1 + (o * 2 + i) * 9 + t] : 0.f);
     }
     for (int i = tid; i < 32; i += nth) {
         reinterpret_cast<float *>(out + TcLayout::b1)[i] = w[off_b1 + i];
@@ -434,11 +722,16 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, uint8_t *__rest
         f1[((k / 8) * 256 + n) * 8 + (k % 8)] = __float2bfloat16_rn(w[off_f1w + e]);
     }
     for (int i = tid; i < 256; i += nth) {
-        reinterpret_cast<float *>(out + TcLayout::fc1b)[i] = w[off_f1b + i];
+        reinterpret_cast<float *>(out + TcLayout::fc1b)[i] = -w[off_f1b + i];
         reinterpret_cast<float *>(out + TcLayout::fc2w)[i] = w[off_f2w + i];
         reinterpret_cast<float *>(out + TcLayout::fc2w)[256 + i] = w[off_f2w + 256 + i];
     }
-    if (tid < 2) reinterpret_cast<float *>(out + TcLayout::fc2b)[tid] = w[off_f2b + tid];
+    // fc2 bias plus W2 b1 (the epilogue evaluates W2 max(z, -b1))
+    if (tid < 2) {
+        double acc = w[off_f2b + tid];
+        for (int n = 0; n < 256; ++n) acc += double(w[off_f2w + tid * 256 + n]) * w[off_f1b + n];
+        reinterpret_cast<float *>(out + TcLayout::fc2b)[tid] = float(acc);
+    }
 }
 
 }  // namespace
