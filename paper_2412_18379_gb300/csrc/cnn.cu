@@ -30,50 +30,66 @@ int grid_for(int64_t n, int sm_count, int per_sm = 8) {
     return int(std::max<int64_t>(1, std::min<int64_t>(need, int64_t(sm_count) * per_sm)));
 }
 
-// U[c] = P1 interpolation of the nodal velocity at the centre of ASG cell c,
-// inside the centre's host element seed[c] (FP32 evaluation of the
-// barycentric coordinates from the walk record). 0 where seed[c] = -1.
+// The P1 interpolation at the ASG cell centres as a static table, built once
+// per mesh: node[c][i] = vertex i of the host element seed[c] of the centre of
+// cell c, w[c][i] = its barycentric coordinate (FP64 from the exact record,
+// rounded to float); node[c][0] = -1 where the centre has no host.
 template <int D>
-__global__ void __launch_bounds__(kThreads) resample_kernel(const DevMesh m,
-                                                            const double *__restrict__ un,
-                                                            float *__restrict__ U) {
-    using WR = typename Recs<D>::W;
-    const WR *__restrict__ rw = static_cast<const WR *>(m.recw);
+__global__ void __launch_bounds__(kThreads) interp_table_kernel(const DevMesh m,
+                                                                int32_t *__restrict__ node,
+                                                                float *__restrict__ w) {
+    using XR = typename Recs<D>::X;
+    const XR *__restrict__ rx = static_cast<const XR *>(m.recx);
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < m.n_asg;
          c += int64_t(gridDim.x) * blockDim.x) {
-        const int32_t s = __ldg(m.seed + c);
+        const int32_t s = m.seed[c];
+        if (s < 0) {
+            #pragma unroll
+            for (int i = 0; i <= D; ++i) {
+                node[c * (D + 1) + i] = -1;
+                w[c * (D + 1) + i] = 0.f;
+            }
+            continue;
+        }
+        double x[D];
+        int64_t r = c;
+        #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int64_t i = r % m.ga[k];
+            r /= m.ga[k];
+            x[k] = __dadd_rn(m.lo[k], __dmul_rn(double(i) + 0.5, m.sa[k]));
+        }
+        double lam[D + 1];
+        bary64(rx, s, x, lam);
+        #pragma unroll
+        for (int i = 0; i <= D; ++i) {
+            node[c * (D + 1) + i] = m.conn[int64_t(s) * (D + 1) + i];
+            w[c * (D + 1) + i] = float(lam[i]);
+        }
+    }
+}
+
+// U[c] = P1 interpolation of the nodal velocity at the centre of ASG cell c
+// through the static table (FP32); 0 where the centre has no host.
+template <int D>
+__global__ void __launch_bounds__(kThreads) resample_kernel(int64_t n_asg,
+                                                            const int32_t *__restrict__ node,
+                                                            const float *__restrict__ w,
+                                                            const double *__restrict__ un,
+                                                            float *__restrict__ U) {
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < n_asg;
+         c += int64_t(gridDim.x) * blockDim.x) {
         float out[D];
         #pragma unroll
         for (int k = 0; k < D; ++k) out[k] = 0.f;
-        if (s >= 0) {
-            WalkE<D> e;
-            load_walk(rw, s, e);
-            int64_t r = c;
-            float df[D];
-            #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const int64_t i = r % m.ga[k];
-                r /= m.ga[k];
-                df[k] = ((m.lo_h[k] - e.vh[k]) + (m.lo_l[k] - e.vl[k])) +
-                        (float(i) + 0.5f) * float(m.sa[k]);
-            }
-            float lam[D + 1];
-            float l0 = 1.f;
-            #pragma unroll
-            for (int r2 = 0; r2 < D; ++r2) {
-                float acc = 0.f;
-                #pragma unroll
-                for (int j = 0; j < D; ++j) acc = fmaf(e.m[r2 * D + j], df[j], acc);
-                lam[r2 + 1] = acc;
-                l0 -= acc;
-            }
-            lam[0] = l0;
+        if (__ldg(node + c * (D + 1)) >= 0) {
             #pragma unroll
             for (int i = 0; i <= D; ++i) {
-                const int32_t v = __ldg(m.conn + int64_t(s) * (D + 1) + i);
+                const int32_t v = __ldg(node + c * (D + 1) + i);
+                const float wi = __ldg(w + c * (D + 1) + i);
                 #pragma unroll
                 for (int k = 0; k < D; ++k)
-                    out[k] = fmaf(lam[i], trunc_to_float(__ldg(un + int64_t(v) * D + k)), out[k]);
+                    out[k] = fmaf(wi, trunc_to_float(__ldg(un + int64_t(v) * D + k)), out[k]);
             }
         }
         #pragma unroll
@@ -364,13 +380,23 @@ int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_
     return 1;
 }
 
-int launch_resample(const DevMesh &m, const double *u_nodal, float *U, int sm_count,
-                    cudaStream_t st) {
+int launch_interp_table(const DevMesh &m, int32_t *node, float *w, int sm_count,
+                        cudaStream_t st) {
     const int g = grid_for(m.n_asg, sm_count);
     if (m.dim == 2)
-        resample_kernel<2><<<g, kThreads, 0, st>>>(m, u_nodal, U);
+        interp_table_kernel<2><<<g, kThreads, 0, st>>>(m, node, w);
     else
-        resample_kernel<3><<<g, kThreads, 0, st>>>(m, u_nodal, U);
+        interp_table_kernel<3><<<g, kThreads, 0, st>>>(m, node, w);
+    return 1;
+}
+
+int launch_resample(const DevMesh &m, const int32_t *node, const float *w, const double *u_nodal,
+                    float *U, int sm_count, cudaStream_t st) {
+    const int g = grid_for(m.n_asg, sm_count);
+    if (m.dim == 2)
+        resample_kernel<2><<<g, kThreads, 0, st>>>(m.n_asg, node, w, u_nodal, U);
+    else
+        resample_kernel<3><<<g, kThreads, 0, st>>>(m.n_asg, node, w, u_nodal, U);
     return 1;
 }
 

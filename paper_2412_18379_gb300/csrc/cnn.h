@@ -26,8 +26,10 @@ struct NetShape {
     int64_t positions(int S) const { return dim == 2 ? int64_t(S) * S : int64_t(S) * S * S; }
 };
 
-int launch_resample(const DevMesh &m, const double *u_nodal, float *U, int sm_count,
-                    cudaStream_t st);
+int launch_interp_table(const DevMesh &m, int32_t *node, float *w, int sm_count,
+                        cudaStream_t st);
+int launch_resample(const DevMesh &m, const int32_t *node, const float *w, const double *u_nodal,
+                    float *U, int sm_count, cudaStream_t st);
 int launch_windows(const DevMesh &m, const float *U, const int64_t *cells, int64_t cell0,
                    int64_t B, const float scale[3], float *out, int sm_count, cudaStream_t st);
 int launch_im2col(int dim, const float *x, int64_t B, int C, int Si, bool chfirst, float *col,

@@ -86,6 +86,8 @@ struct Mesh {
     std::vector<int32_t> node_elem_user;  // host copy, user ids
     float *grid_u = nullptr;              // [n_asg][dim] grid velocity (CNN input)
     float *grid_dhat = nullptr;           // [n_asg][dim] predicted displacement
+    int32_t *interp_node = nullptr;       // [n_asg][dim+1] P1 interpolation at cell centres:
+    float *interp_w = nullptr;            //   host vertices and weights (static per mesh)
     bool grid_u_valid = false;
 };
 

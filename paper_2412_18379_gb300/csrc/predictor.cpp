@@ -213,6 +213,20 @@ cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
     return it == ctx->meshes.end() ? nullptr : it->second;
 }
 
+// The static P1 interpolation table of the ASG cell centres (built once).
+cs_status ensure_interp(cs_ctx *ctx, cs::Mesh *m, cudaStream_t st) {
+    if (m->interp_node) return CS_OK;
+    const size_t n = size_t(m->d.n_asg) * (m->d.dim + 1);
+    cs_status rc = dalloc(ctx, &m->interp_node, n);
+    if (rc) return rc;
+    m->allocs.push_back(m->interp_node);
+    rc = dalloc(ctx, &m->interp_w, n);
+    if (rc) return rc;
+    m->allocs.push_back(m->interp_w);
+    ctx->launches += launch_interp_table(m->d, m->interp_node, m->interp_w, ctx->sm_count, st);
+    return CS_OK;
+}
+
 cs_status ensure_mesh_grid(cs_ctx *ctx, cs::Mesh *m) {
     const size_t n = size_t(m->d.n_asg) * m->d.dim;
     if (!m->grid_u) {
@@ -291,8 +305,11 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt
     cs_status rc = ensure_mesh_grid(ctx, m);
     if (rc) return rc;
     if (u_nodal) {
+        rc = ensure_interp(ctx, m, st);
+        if (rc) return rc;
         const int ev = ctx->prof.begin(CS_STAGE_RESAMPLE, st);
-        ctx->launches += launch_resample(m->d, u_nodal, m->grid_u, ctx->sm_count, st);
+        ctx->launches += launch_resample(m->d, m->interp_node, m->interp_w, u_nodal, m->grid_u,
+                                         ctx->sm_count, st);
         ctx->prof.end(ev, st);
         m->grid_u_valid = true;
     }
@@ -390,8 +407,10 @@ cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal, 
         dst = m->grid_u;
         m->grid_u_valid = true;
     }
-    ctx->launches += launch_resample(m->d, u_nodal, dst, ctx->sm_count,
-                                     static_cast<cudaStream_t>(stream));
+    cs_status rc = ensure_interp(ctx, m, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    ctx->launches += launch_resample(m->d, m->interp_node, m->interp_w, u_nodal, dst,
+                                     ctx->sm_count, static_cast<cudaStream_t>(stream));
     PCHK(cudaGetLastError());
     return CS_OK;
 }
