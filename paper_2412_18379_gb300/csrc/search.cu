@@ -215,8 +215,21 @@ __global__ void __launch_bounds__(256) stats_kernel(int64_t n, const int32_t *pa
 
 int launch_fallback(const DevMesh &m, const TrackArgs &a, const int32_t *count,
                     const int32_t *list, int sm_count, cudaStream_t st, Profiler *prof) {
-    // one warp per listed particle; warps beyond the count return at once
-    const int grid = int(std::min<int64_t>(int64_t(sm_count) * 16, (a.n + 7) / 8));
+    // The list is usually empty or nearly so (it holds particles within tau of
+    // a face, walks that left the mesh or hit the cap), and its length is only
+    // known on the device: one wave of resident blocks, which the kernel's
+    // grid-stride loop spreads over any length, costs least to launch.
+    static int occ[2] = {0, 0};
+    int &o = occ[m.dim == 2 ? 0 : 1];
+    if (o == 0) {
+        if (m.dim == 2)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fallback_kernel<2>, 256, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fallback_kernel<3>, 256, 0);
+        o = std::max(o, 1);
+    }
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count) * o,
+                                                                (a.n + 7) / 8)));
     const int ev = prof ? prof->begin(CS_STAGE_FALLBACK, st) : -1;
     if (m.dim == 2)
         fallback_kernel<2><<<grid, 256, 0, st>>>(m, a, count, list);

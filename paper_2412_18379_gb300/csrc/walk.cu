@@ -199,11 +199,22 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
             }
             carg = carg && nmin == 1;
 
+            // near: another element may contain x_p too, so the exact search
+            // picks the lowest id. Not when the only face within tau is on the
+            // mesh boundary: no element lies across it, and x_p is at least
+            // tau inside every other face.
             bool inside, near = false;
             if (cin) {
                 inside = true;
+                int nnear = 0;
+                bool inner = false;
                 #pragma unroll
-                for (int i = 0; i <= D; ++i) near = near || (lf[i] - T[i] < tau_f);
+                for (int i = 0; i <= D; ++i) {
+                    const bool ni = lf[i] - T[i] < tau_f;
+                    nnear += ni;
+                    inner = inner || (ni && e.nbr[i] >= 0);
+                }
+                near = nnear > 1 || inner;
             } else if (cout && carg) {
                 inside = false;
             } else {
@@ -214,8 +225,15 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
                 #pragma unroll
                 for (int i = 0; i <= D; ++i) inside = inside && (lam[i] >= -CS_EPS);
                 if (inside) {
+                    int nnear = 0;
+                    bool inner = false;
                     #pragma unroll
-                    for (int i = 0; i <= D; ++i) near = near || (lam[i] < m.tau);
+                    for (int i = 0; i <= D; ++i) {
+                        const bool ni = lam[i] < m.tau;
+                        nnear += ni;
+                        inner = inner || (ni && e.nbr[i] >= 0);
+                    }
+                    near = nnear > 1 || inner;
                 } else {
                     // argmin, lowest index on equal minima (Eq. 5)
                     double lmin = lam[0];
