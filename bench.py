@@ -241,7 +241,7 @@ def train_predictor(ctx, mesh, case, n_fields, steps, batch, seed):
                 "hosts_identical": agree}}
 
 
-def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed):
+def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed, pred_stride):
     """Poisson stream of tracking requests over resident meshes (a scaled
     version of the serving workload: 2 triangle meshes of 2.0M and 0.2M
     elements, 2 tetrahedral meshes of 0.75M and 2.06M, 8-mode fields, CFL
@@ -263,6 +263,8 @@ def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed):
         else:
             c = make_case(name, **kw)
             m = ctx.upload_mesh(c.xyz, c.conn)
+            if c.dim == 2:
+                m.set_predictor_grid(pred_stride)
             u = (fourier_modes_2d if c.dim == 2 else fourier_modes_3d)(c.xyz, 77 + i)
         if c.dim == 2:
             ctx.grid_velocity(m, torch.from_numpy(u).cuda())
@@ -309,6 +311,8 @@ def main():
     ap.add_argument("--workload", default="tg2d", choices=sorted(WORKLOADS))
     ap.add_argument("--cfl", type=float, default=8.0)
     ap.add_argument("--mode", default="cnn", choices=["sns", "asg", "cnn"])
+    ap.add_argument("--pred-stride", type=int, default=3,
+                    help="ASG cells per predictor cell and axis (odd; 2-D meshes)")
     ap.add_argument("--train-fields", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
@@ -350,6 +354,8 @@ def main():
     dim = case.dim
     ctx = cs.Context(lrank)
     mesh = ctx.upload_mesh(case.xyz, case.conn)
+    if dim == 2:
+        mesh.set_predictor_grid(args.pred_stride)
     info = mesh.info()
     dev = torch.device("cuda", lrank)
 
@@ -439,7 +445,7 @@ def main():
     rooflines = {"walk": walk_roof}
     cnn_l, cnn_ms = main_prof.get("cnn", (0, 0.0))
     if cnn_l and dim == 2:
-        flops = CNN_FLOP_PER_CELL_2D * int(np.prod(info["asg_grid"]))
+        flops = CNN_FLOP_PER_CELL_2D * int(np.prod(info["pred_grid"]))
         ach = flops / (cnn_ms / cnn_l * 1e-3) / 1e12
         rooflines["cnn"] = {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
                             "unit": "TFLOP/s", "frac": ach / bf16_peak,
@@ -474,7 +480,7 @@ def main():
     serving = None
     if not args.quick and dim == 2 and args.serve_requests > 0:
         serving = serve_bench(ctx, mesh, case, args.serve_requests, args.serve_rate,
-                              args.serve_slots, seed=100 + rank)
+                              args.serve_slots, seed=100 + rank, pred_stride=args.pred_stride)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -496,6 +502,8 @@ def main():
                                 "asg": "ASG-direct"}[args.mode],
                        "n_particles": n, "n_elements": case.n_elements,
                        "asg_grid": info["asg_grid"],
+                       "predictor_grid": {"stride": info["pred_stride"],
+                                          "cells": info["pred_grid"]},
                        "l2": "flushed by a 256 MB write before every timed step",
                        "parallelism": ("%d replicas: every rank locates its own batch of %d particles "
                                         "against its own copy of the mesh, no collective"

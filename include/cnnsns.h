@@ -73,7 +73,7 @@ typedef struct cs_mesh_info {
     int32_t dim;
     int64_t n_vertices;
     int64_t n_elements;
-    int32_t asg_grid[3];        /* ASG cells per axis (seed grid, CNN grid)  */
+    int32_t asg_grid[3];        /* ASG cells per axis (seed grid)            */
     int32_t bucket_grid[3];     /* cells per axis of the exact-search index  */
     int64_t bucket_items;       /* total entries of the exact-search index   */
     double  lo[3], hi[3];       /* bounding box of the vertices              */
@@ -81,6 +81,8 @@ typedef struct cs_mesh_info {
     int32_t step_cap;           /* walk stops after this many evaluations    */
     int32_t record_bytes;       /* bytes of one element record (64 or 128)   */
     size_t  device_bytes;       /* device memory held by this mesh           */
+    int32_t pred_stride;        /* ASG cells per predictor cell and axis     */
+    int32_t pred_grid[3];       /* predictor cells per axis (see below)      */
 } cs_mesh_info;
 
 /* Create a context on CUDA device `cuda_device`. */
@@ -130,7 +132,7 @@ cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
  *   mode: CS_SNS, CS_ASG_DIRECT or CS_CNN_SNS. CS_CNN_SNS needs a loaded
  *         predictor (cs_predictor_load). When start == NULL and the particles
  *         are the mesh nodes, u is the nodal field: the call resamples it to
- *         the ASG grid, runs the predictor and walks (Algorithm 2). Otherwise
+ *         the predictor grid, runs the predictor and walks (Algorithm 2). Otherwise
  *         it uses the grid velocity stored by cs_grid_velocity.
  *   host_out[n]  user id of the host of x_p, or -1.
  *   path_len_out[n]  I_t of Algorithm 1 (elements evaluated, start included).
@@ -190,12 +192,13 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double
 /* ------------------------------------------------------------------------ */
 /* Learned start predictor (Sec. 2.3 and Algorithm 2).                       */
 /*                                                                          */
-/* Regressor form: a window of the ASG-grid velocity around the cell of the  */
-/* particle (channels u_k * dt / s_k, zero outside the grid; 2-D 9x9, 3-D   */
+/* Regressor form: a window of the predictor-grid velocity (cs_predictor_  */
+/* grid) around the cell of the particle (channels u_k * dt / s_k, s_k the  */
+/* predictor cell size, zero outside the grid; 2-D 9x9, 3-D                 */
 /* 7x7x7) goes through valid 3x3 (3x3x3) convolutions of 32 channels with    */
 /* ReLU (2-D: 4 layers, 3-D: 3 layers), then fully connected 32 -> 256      */
-/* (ReLU) -> dim. The output is the displacement in ASG cell units; the walk */
-/* then starts at the seed of the cell of x + displacement * s (Algorithm 2: */
+/* (ReLU) -> dim. The output is the displacement in predictor cell units;  */
+/* the walk then starts at the ASG seed of x + displacement * s (Alg. 2:    */
 /* the prediction K_p replaces K_m as the origin of the walk).              */
 /*                                                                          */
 /* Weights: a flat float32 vector; for each conv layer W[32][C_in][taps]     */
@@ -229,15 +232,32 @@ cs_status cs_predictor_load(cs_ctx *ctx, int dim, const float *weights, int64_t 
 /* Copy the current FP32 master weights to HOST memory. CS_ENOPRED if none. */
 cs_status cs_predictor_save(cs_ctx *ctx, int dim, float *weights_out, int64_t n);
 
-/* ASG-grid velocity of a mesh from its nodal velocity (DEVICE pointers):
- * grid[c][k] = P1 interpolation of u_nodal[n_v][dim] at the centre of cell c
- * inside the centre's host element (0 where the centre is outside the mesh),
- * evaluated in FP32. grid_out: [prod asg_grid][dim] floats, or NULL to store
- * it in the mesh (used by cs_predict / CS_CNN_SNS). Enqueued on stream. */
+/*
+ * The grid the start predictor runs on (Sec. 2.3: the ASG pools the mesh into
+ * Cartesian cells that hold several elements each). stride (odd, >= 1) ASG
+ * cells per predictor cell and axis; predictor cell I spans ASG cells
+ * stride*I .. stride*I + stride - 1 and shares its centre with the middle one.
+ * pred_grid[k] = asg_grid[k] / stride (rounded down); a point past the last
+ * whole cell belongs to the last. The grid velocity, the predictor's windows
+ * and outputs (in predictor-cell units), the training pairs and the start
+ * rule of CS_CNN_SNS (cell of x, then x + d_hat * cell size) all use this grid;
+ * the start element is still looked up in the ASG seed grid. Default 1 (the
+ * ASG grid itself). Drops the mesh's stored grid velocity and predictions.
+ * Not while serving (CS_EBUSY). Errors: CS_EINVAL (even stride, or larger
+ * than asg_grid on some axis), CS_ENOMESH, CS_ENOMEM.
+ */
+cs_status cs_predictor_grid(cs_ctx *ctx, int32_t mesh_id, int32_t stride);
+
+/* Predictor-grid velocity of a mesh from its nodal velocity (DEVICE
+ * pointers): grid[c][k] = P1 interpolation of u_nodal[n_v][dim] at the centre
+ * of predictor cell c inside the centre's host element (0 where the centre is
+ * outside the mesh), in FP32 with weights from the FP64 barycentric
+ * coordinates. grid_out: [prod pred_grid][dim] floats, or NULL to store it in
+ * the mesh (used by cs_predict / CS_CNN_SNS). Enqueued on stream. */
 cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal,
                            float *grid_out, void *stream);
 
-/* Input windows at ASG cells (DEVICE pointers): out[b][k][w] = grid[cells[b]
+/* Input windows at predictor cells (DEVICE): out[b][k][w] = grid[cells[b]
  * + offset(w)][k] * dt / s_k, zero outside the grid, w over the window
  * positions (x fastest). grid = NULL uses the mesh's stored grid velocity.
  * cells = NULL means cells 0..B-1. */
@@ -249,8 +269,8 @@ cs_status cs_windows(cs_ctx *ctx, int32_t mesh_id, const float *grid, double dt,
 cs_status cs_predictor_forward(cs_ctx *ctx, int dim, int64_t B, const float *windows,
                                float *dhat_out);
 
-/* Predicted displacement (cell units) at every ASG cell of a mesh from its
- * stored grid velocity and dt (DEVICE output [prod asg_grid][dim], or NULL to
+/* Predicted displacement (cell units) at every predictor cell of a mesh from
+ * its stored grid velocity and dt (DEVICE output [prod pred_grid][dim], or NULL to
  * store it in the mesh for cs_track_dhat(.., NULL ..)). Enqueued on stream. */
 cs_status cs_predict(cs_ctx *ctx, int32_t mesh_id, double dt, float *dhat_out, void *stream);
 
@@ -266,7 +286,7 @@ cs_status cs_predictor_train(cs_ctx *ctx, int dim, const float *windows, const f
 
 /* Training pairs (Sec. 2.3: the training data are produced by the tracking
  * itself) for n particles at positions x with velocities u (DEVICE pointers):
- * cells_out[p] = ASG cell of x_p's origin x, windows_out[p] = the input
+ * cells_out[p] = predictor cell of x_p's origin x, windows_out[p] = the input
  * window at that cell from the mesh's stored grid velocity (scale dt / s_k),
  * targets_out[p][k] = (x_p,k - x_k) / s_k with x_p = x - (u * dt). The host
  * element labels come from cs_track with CS_SNS. Enqueued on stream. */
@@ -283,8 +303,9 @@ cs_status cs_predictor_grad(cs_ctx *ctx, int dim, int64_t B, const float *window
 
 /* CNN-SNS start rule with a given displacement grid (DEVICE pointers): like
  * cs_track, but the walk starts at the seed of the ASG cell of
- * x + dhat[cell(x)] * s (falling back to the plain start where that seed is
- * -1). dhat: [prod asg_grid][dim] floats in cell units, or NULL for the
+ * x + dhat[pcell(x)] * s, pcell and s the predictor cell and cell size
+ * (falling back to the plain start where that seed is -1).
+ * dhat: [prod pred_grid][dim] floats in predictor cell units, or NULL for the
  * mesh's stored prediction (cs_predict). */
 cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
                         const double *u, double dt, const int32_t *start, const float *dhat,
@@ -370,8 +391,8 @@ typedef struct cs_profile {
 } cs_profile;
 #define CS_STAGE_WALK      0   /* departure + start + Algorithm 1 walk       */
 #define CS_STAGE_FALLBACK  1   /* exact search / canonicalisation            */
-#define CS_STAGE_RESAMPLE  2   /* nodal velocity -> ASG grid                 */
-#define CS_STAGE_CNN       3   /* CNN forward over the ASG grid              */
+#define CS_STAGE_RESAMPLE  2   /* nodal velocity -> predictor grid           */
+#define CS_STAGE_CNN       3   /* CNN forward over the predictor grid        */
 #define CS_STAGE_TRAIN     4   /* one training step (forward+backward+Adam)  */
 
 /* Turn event timing on (1) or off (0). */

@@ -227,7 +227,7 @@ class Mesh:
     """The oracle's own view of a mesh: neighbours, inverse-affine form,
     plain-SNS starts and the ASG seed grid (host of every cell centre)."""
 
-    def __init__(self, xyz, conn, grid=None, brute_limit=20000):
+    def __init__(self, xyz, conn, grid=None, brute_limit=20000, pred_stride=1):
         self.xyz = _f(xyz)
         self.conn = _i(conn)
         self.dim = self.xyz.shape[1]
@@ -243,6 +243,36 @@ class Mesh:
             grid = default_grid(self.n_v, self.dim)
         self.grid = _i(np.broadcast_to(np.asarray(grid), (self.dim,)))
         self._seed = None
+        self.set_pred_stride(pred_stride)
+
+    def set_pred_stride(self, p):
+        """The predictor grid (Sec. 2.3: the ASG pools several elements into
+        each Cartesian cell): cells of p^d ASG cells, p odd, aligned at lo;
+        grid // p cells per axis of size ((hi - lo) / grid) * p. A point past
+        the last whole cell belongs to the last one."""
+        if p < 1 or p % 2 == 0:
+            raise ValueError("predictor stride must be odd and >= 1")
+        self.pred_stride = int(p)
+        self.pgrid = np.maximum(self.grid // p, 1).astype(np.int32)
+        self.ps = ((self.hi - self.lo) / self.grid) * float(p)
+
+    def pred_centres(self):
+        """Centres lo + (i + 0.5) * ps of the predictor cells, x fastest."""
+        axes = [(np.arange(g) + 0.5) * s for g, s in zip(self.pgrid, self.ps)]
+        mesh = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+        return np.stack([self.lo[k] + mesh[k].ravel() for k in range(self.dim)], axis=1)
+
+    def pred_cells(self, pts):
+        """Predictor cell of each point: floor((x - lo) / ps) per axis, clamped
+        to [0, pgrid - 1] (NaN -> 0), flattened x fastest."""
+        pts = _f(pts)
+        t = np.floor((pts - self.lo) / self.ps)
+        t = np.where(t >= 0.0, t, 0.0)
+        t = np.minimum(t, (self.pgrid - 1).astype(np.float64)).astype(np.int64)
+        c = np.zeros(pts.shape[0], dtype=np.int64)
+        for k in range(self.dim - 1, -1, -1):
+            c = c * int(self.pgrid[k]) + t[:, k]
+        return c
 
     def locate(self, pts, eps=EPS):
         if self.brute:
@@ -268,7 +298,8 @@ class Mesh:
 
         mode 'sns': start = the given start (user ids) or the node's element;
         'asg': start = seed grid cell of x_p itself; 'cnn': start = seed grid
-        cell of x + dhat * s (dhat in cell units). A seed of -1 falls back to
+        cell of x + dhat * ps (dhat per particle, in predictor cell units, ps
+        the predictor cell size). A seed of -1 falls back to
         the plain start. Returns dict of host, path_len, status, start, xp."""
         x, u = _f(x), _f(u)
         n = x.shape[0]
@@ -286,8 +317,8 @@ class Mesh:
             s = self.seed[c]
             st = np.where(s >= 0, s, plain).astype(np.int32)
         elif mode == "cnn":
-            s_cell = (self.hi - self.lo) / self.grid
-            y = x + (np.asarray(dhat, dtype=np.float32).astype(np.float64) * s_cell)
+            # dhat: per particle, in predictor cell units
+            y = x + (np.asarray(dhat, dtype=np.float32).astype(np.float64) * self.ps)
             c = self.cells(y)
             s = self.seed[c]
             st = np.where(s >= 0, s, plain).astype(np.int32)

@@ -50,7 +50,13 @@ class Mesh:
                     asg_grid=list(inf.asg_grid[:d]), bucket_grid=list(inf.bucket_grid[:d]),
                     bucket_items=inf.bucket_items, lo=list(inf.lo[:d]), hi=list(inf.hi[:d]),
                     tau=inf.tau, step_cap=inf.step_cap, record_bytes=inf.record_bytes,
-                    device_bytes=inf.device_bytes)
+                    device_bytes=inf.device_bytes, pred_stride=inf.pred_stride,
+                    pred_grid=list(inf.pred_grid[:d]))
+
+    def set_predictor_grid(self, stride):
+        """Run the start predictor on cells of stride^dim ASG cells (odd
+        stride; 1 = the ASG grid). Drops the stored grid velocity."""
+        self.ctx._check(self.ctx.lib.cs_predictor_grid(self.ctx.h, self.id, int(stride)))
 
     def node_start_elements(self):
         out = np.empty(self.n_vertices, dtype=np.int32)

@@ -41,6 +41,8 @@ class MeshInfo(ctypes.Structure):
         ("step_cap", _i32),
         ("record_bytes", _i32),
         ("device_bytes", ctypes.c_size_t),
+        ("pred_stride", _i32),
+        ("pred_grid", _i32 * 3),
     ]
 
 
@@ -69,6 +71,7 @@ SIGNATURES = {
     "cs_predictor_size": (_i64, [ctypes.c_int]),
     "cs_predictor_load": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
     "cs_predictor_save": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
+    "cs_predictor_grid": (_i32, [_vp, _i32, _i32]),
     "cs_grid_velocity": (_i32, [_vp, _i32, _vp, _vp, _vp]),
     "cs_windows": (_i32, [_vp, _i32, _vp, _dbl, _vp, _i64, _vp, _vp]),
     "cs_predictor_forward": (_i32, [_vp, ctypes.c_int, _i64, _vp, _vp]),

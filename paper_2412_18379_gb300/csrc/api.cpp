@@ -227,6 +227,15 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     d.cap = H.cap;
     d.n_asg = n_asg;
     d.n_bucket = n_b;
+    // predictor grid: the ASG grid itself until cs_predictor_grid changes it
+    d.pstride = 1;
+    for (int k = 0; k < 3; ++k) {
+        d.pga[k] = d.ga[k];
+        d.psa[k] = d.sa[k];
+        d.pinv_sa[k] = d.inv_sa[k];
+    }
+    d.n_pasg = n_asg;
+    d.pseed = seed;
 
     ctx->launches += cs::launch_seed_grid(d, seed, ctx->sm_count, nullptr);
     cudaError_t e = cudaDeviceSynchronize();
@@ -240,8 +249,10 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     I.dim = dim;
     I.n_vertices = n_v;
     I.n_elements = n_e;
+    I.pred_stride = 1;
     for (int k = 0; k < 3; ++k) {
         I.asg_grid[k] = d.ga[k];
+        I.pred_grid[k] = d.pga[k];
         I.bucket_grid[k] = d.gb[k];
         I.lo[k] = d.lo[k];
         I.hi[k] = d.hi[k];

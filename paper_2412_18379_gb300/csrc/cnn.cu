@@ -69,6 +69,24 @@ __global__ void __launch_bounds__(kThreads) interp_table_kernel(const DevMesh m,
     }
 }
 
+// pseed[c] = seed of the middle ASG cell of predictor cell c: with an odd
+// stride p, predictor cell I spans ASG cells p I .. p I + p - 1 per axis and
+// shares its centre with ASG cell p I + (p - 1) / 2.
+__global__ void __launch_bounds__(kThreads) pred_seed_kernel(const DevMesh m,
+                                                             int32_t *__restrict__ pseed) {
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < m.n_pasg;
+         c += int64_t(gridDim.x) * blockDim.x) {
+        int64_t r = c, fine = 0, mul = 1;
+        for (int k = 0; k < m.dim; ++k) {
+            const int64_t i = r % m.pga[k];
+            r /= m.pga[k];
+            fine += (i * m.pstride + (m.pstride - 1) / 2) * mul;
+            mul *= m.ga[k];
+        }
+        pseed[c] = __ldg(m.seed + fine);
+    }
+}
+
 // U[c] = P1 interpolation of the nodal velocity at the centre of ASG cell c
 // through the static table (FP32); 0 where the centre has no host.
 template <int D>
@@ -377,6 +395,11 @@ int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, 
 int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,
                        int sm_count, cudaStream_t st) {
     gather_rows_kernel<<<grid_for(B * row, sm_count, 16), kThreads, 0, st>>>(src, row, idx, B, dst);
+    return 1;
+}
+
+int launch_pred_seed(const DevMesh &m, int32_t *pseed, int sm_count, cudaStream_t st) {
+    pred_seed_kernel<<<grid_for(m.n_pasg, sm_count), kThreads, 0, st>>>(m, pseed);
     return 1;
 }
 

@@ -26,6 +26,7 @@ struct NetShape {
     int64_t positions(int S) const { return dim == 2 ? int64_t(S) * S : int64_t(S) * S * S; }
 };
 
+int launch_pred_seed(const DevMesh &m, int32_t *pseed, int sm_count, cudaStream_t st);
 int launch_interp_table(const DevMesh &m, int32_t *node, float *w, int sm_count,
                         cudaStream_t st);
 int launch_resample(const DevMesh &m, const int32_t *node, const float *w, const double *u_nodal,

@@ -77,7 +77,29 @@ struct DevMesh {
     double tau;               // canonicalisation threshold
     int32_t cap;              // step cap
     int64_t n_asg, n_bucket;
+    // predictor grid: cells of pstride^dim ASG cells (pstride odd), aligned at
+    // lo; a point past the last whole cell belongs to the last one
+    int32_t pstride;          // 1: the ASG grid itself
+    int32_t pga[3];           // ga / pstride (at least 1)
+    double psa[3];            // sa * pstride
+    float pinv_sa[3];         // 1 / psa rounded to float
+    int64_t n_pasg;
+    const int32_t *pseed;     // [n_pasg] host of each cell centre (the seed of its middle ASG cell)
 };
+
+// The mesh as the start predictor sees it: the predictor grid in place of the
+// ASG grid (cell geometry, cell count and centre hosts); everything else the same.
+inline DevMesh pred_view(const DevMesh &d) {
+    DevMesh v = d;
+    for (int k = 0; k < 3; ++k) {
+        v.ga[k] = d.pga[k];
+        v.sa[k] = d.psa[k];
+        v.inv_sa[k] = d.pinv_sa[k];
+    }
+    v.n_asg = d.n_pasg;
+    v.seed = d.pseed;
+    return v;
+}
 
 struct Mesh {
     DevMesh d{};

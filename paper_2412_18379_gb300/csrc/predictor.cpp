@@ -216,19 +216,19 @@ cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
 // The static P1 interpolation table of the ASG cell centres (built once).
 cs_status ensure_interp(cs_ctx *ctx, cs::Mesh *m, cudaStream_t st) {
     if (m->interp_node) return CS_OK;
-    const size_t n = size_t(m->d.n_asg) * (m->d.dim + 1);
+    const size_t n = size_t(pred_view(m->d).n_asg) * (m->d.dim + 1);
     cs_status rc = dalloc(ctx, &m->interp_node, n);
     if (rc) return rc;
     m->allocs.push_back(m->interp_node);
     rc = dalloc(ctx, &m->interp_w, n);
     if (rc) return rc;
     m->allocs.push_back(m->interp_w);
-    ctx->launches += launch_interp_table(m->d, m->interp_node, m->interp_w, ctx->sm_count, st);
+    ctx->launches += launch_interp_table(pred_view(m->d), m->interp_node, m->interp_w, ctx->sm_count, st);
     return CS_OK;
 }
 
 cs_status ensure_mesh_grid(cs_ctx *ctx, cs::Mesh *m) {
-    const size_t n = size_t(m->d.n_asg) * m->d.dim;
+    const size_t n = size_t(pred_view(m->d).n_asg) * m->d.dim;
     if (!m->grid_u) {
         cs_status rc = dalloc(ctx, &m->grid_u, n);
         if (rc) return rc;
@@ -279,7 +279,7 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
             ctx->launches += launch_pack_tc(P->w, NetShape(2), P->packed, st);
             P->packed_dirty = false;
         }
-        ctx->launches += launch_cnn2d_tc(m->d, m->grid_u, dt, P->packed, dhat, ctx->dev_err,
+        ctx->launches += launch_cnn2d_tc(pred_view(m->d), m->grid_u, dt, P->packed, dhat, ctx->dev_err,
                                          ctx->sm_count, st);
         return CS_OK;
     }
@@ -288,10 +288,10 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
     if (rc) return rc;
     const int D = m->d.dim;
     float scale[3] = {0, 0, 0};
-    for (int k = 0; k < D; ++k) scale[k] = float(dt / m->d.sa[k]);
-    for (int64_t c0 = 0; c0 < m->d.n_asg; c0 += chunk) {
-        const int64_t B = std::min(chunk, m->d.n_asg - c0);
-        ctx->launches += launch_windows(m->d, m->grid_u, nullptr, c0, B, scale, P->win,
+    for (int k = 0; k < D; ++k) scale[k] = float(dt / pred_view(m->d).sa[k]);
+    for (int64_t c0 = 0; c0 < pred_view(m->d).n_asg; c0 += chunk) {
+        const int64_t B = std::min(chunk, pred_view(m->d).n_asg - c0);
+        ctx->launches += launch_windows(pred_view(m->d), m->grid_u, nullptr, c0, B, scale, P->win,
                                         ctx->sm_count, st);
         ctx->launches += forward(ctx, *P, B, P->win, st);
         PCHK(cudaMemcpyAsync(dhat + c0 * D, P->out, size_t(B) * D * sizeof(float),
@@ -308,7 +308,7 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt
         rc = ensure_interp(ctx, m, st);
         if (rc) return rc;
         const int ev = ctx->prof.begin(CS_STAGE_RESAMPLE, st);
-        ctx->launches += launch_resample(m->d, m->interp_node, m->interp_w, u_nodal, m->grid_u,
+        ctx->launches += launch_resample(pred_view(m->d), m->interp_node, m->interp_w, u_nodal, m->grid_u,
                                          ctx->sm_count, st);
         ctx->prof.end(ev, st);
         m->grid_u_valid = true;
@@ -393,6 +393,58 @@ cs_status cs_predictor_save(cs_ctx *ctx, int dim, float *out, int64_t n) {
     return CS_OK;
 }
 
+cs_status cs_predictor_grid(cs_ctx *ctx, int32_t mesh_id, int32_t stride) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_predictor_grid: unknown mesh id");
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_predictor_grid: stop serving first");
+    cs::DevMesh &d = m->d;
+    if (stride < 1 || stride % 2 == 0)
+        return fail(ctx, CS_EINVAL, "cs_predictor_grid: the stride must be odd and >= 1");
+    for (int k = 0; k < d.dim; ++k)
+        if (d.ga[k] < stride)
+            return fail(ctx, CS_EINVAL, "cs_predictor_grid: stride larger than the ASG grid");
+    PCHK(cudaSetDevice(ctx->device));
+    PCHK(cudaDeviceSynchronize());
+    // drop the buffers of the old predictor grid (its centre hosts, grid
+    // velocity, predictions and interpolation table)
+    void *old[] = {d.pseed == d.seed ? nullptr : const_cast<int32_t *>(d.pseed), m->grid_u,
+                   m->grid_dhat, m->interp_node, m->interp_w};
+    for (void *q : old) {
+        if (!q) continue;
+        auto it = std::find(m->allocs.begin(), m->allocs.end(), q);
+        if (it != m->allocs.end()) m->allocs.erase(it);
+        cudaFree(q);
+    }
+    m->grid_u = m->grid_dhat = nullptr;
+    m->interp_node = nullptr;
+    m->interp_w = nullptr;
+    m->grid_u_valid = false;
+    d.pstride = stride;
+    int64_t n = 1;
+    for (int k = 0; k < 3; ++k) {
+        d.pga[k] = k < d.dim ? d.ga[k] / stride : 1;
+        d.psa[k] = k < d.dim ? d.sa[k] * double(stride) : 1.0;
+        d.pinv_sa[k] = static_cast<float>(1.0 / d.psa[k]);
+        n *= d.pga[k];
+        m->info.pred_grid[k] = d.pga[k];
+    }
+    d.n_pasg = n;
+    m->info.pred_stride = stride;
+    if (stride == 1) {
+        d.pseed = d.seed;
+        return CS_OK;
+    }
+    int32_t *ps = nullptr;
+    cs_status rc = dalloc(ctx, &ps, size_t(n));
+    if (rc) return rc;
+    m->allocs.push_back(ps);
+    d.pseed = ps;
+    ctx->launches += launch_pred_seed(d, ps, ctx->sm_count, nullptr);
+    PCHK(cudaGetLastError());
+    return CS_OK;
+}
+
 cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal, float *grid_out,
                            void *stream) {
     if (!ctx) return CS_EINVAL;
@@ -409,7 +461,7 @@ cs_status cs_grid_velocity(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal, 
     }
     cs_status rc = ensure_interp(ctx, m, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
-    ctx->launches += launch_resample(m->d, m->interp_node, m->interp_w, u_nodal, dst,
+    ctx->launches += launch_resample(pred_view(m->d), m->interp_node, m->interp_w, u_nodal, dst,
                                      ctx->sm_count, static_cast<cudaStream_t>(stream));
     PCHK(cudaGetLastError());
     return CS_OK;
@@ -425,8 +477,8 @@ cs_status cs_windows(cs_ctx *ctx, int32_t mesh_id, const float *grid, double dt,
     if (B == 0) return CS_OK;
     PCHK(cudaSetDevice(ctx->device));
     float scale[3] = {0, 0, 0};
-    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / m->d.sa[k]);
-    ctx->launches += launch_windows(m->d, grid ? grid : m->grid_u, cells, 0, B, scale, out,
+    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / pred_view(m->d).sa[k]);
+    ctx->launches += launch_windows(pred_view(m->d), grid ? grid : m->grid_u, cells, 0, B, scale, out,
                                     ctx->sm_count, static_cast<cudaStream_t>(stream));
     PCHK(cudaGetLastError());
     return CS_OK;
@@ -536,10 +588,10 @@ cs_status cs_training_pairs(cs_ctx *ctx, int32_t mesh_id, int64_t n, const doubl
     if (n == 0) return CS_OK;
     PCHK(cudaSetDevice(ctx->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ctx->launches += launch_pairs(m->d, n, x, u, dt, cells_out, targets_out, ctx->sm_count, st);
+    ctx->launches += launch_pairs(pred_view(m->d), n, x, u, dt, cells_out, targets_out, ctx->sm_count, st);
     float scale[3] = {0, 0, 0};
-    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / m->d.sa[k]);
-    ctx->launches += launch_windows(m->d, m->grid_u, cells_out, 0, n, scale, windows_out,
+    for (int k = 0; k < m->d.dim; ++k) scale[k] = float(dt / pred_view(m->d).sa[k]);
+    ctx->launches += launch_windows(pred_view(m->d), m->grid_u, cells_out, 0, n, scale, windows_out,
                                     ctx->sm_count, st);
     PCHK(cudaGetLastError());
     return CS_OK;

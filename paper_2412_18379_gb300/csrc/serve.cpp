@@ -121,7 +121,7 @@ size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn) {
     add(n * 4);                      // path
     add(n);                          // status
     add(std::max<size_t>(n, 1) * 4); // exact-search list
-    if (cnn) add(size_t(m.d.n_asg) * d * 4);   // predicted displacement grid
+    if (cnn) add(size_t(m.d.n_pasg) * d * 4);  // predicted displacement grid
     return b;
 }
 
@@ -145,7 +145,7 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     int32_t *path = reinterpret_cast<int32_t *>(take(n * 4));
     uint8_t *status = reinterpret_cast<uint8_t *>(take(n));
     int32_t *list = reinterpret_cast<int32_t *>(take(std::max<size_t>(n, 1) * 4));
-    float *dhat = q.used_mode == CS_CNN_SNS ? reinterpret_cast<float *>(take(size_t(m.d.n_asg) * d * 4))
+    float *dhat = q.used_mode == CS_CNN_SNS ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4))
                                             : nullptr;
     cudaStream_t st = sl.st;
     cudaError_t e = cudaMemcpyAsync(x, r.x, n * d * 8, cudaMemcpyHostToDevice, st);

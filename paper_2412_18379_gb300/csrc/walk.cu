@@ -66,11 +66,12 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
                 x0[k] = __ldg(a.x + pp * D + k);
                 split_double(x0[k], h0[k], l0[k]);
             }
-            const int64_t c0 = grid_cell_f<D>(x0, h0, l0, m);
+            // predictor cell of x, then the ASG seed of x + dhat * (predictor cell size)
+            const int64_t c0 = grid_cell_cert<D>(x0, h0, l0, m, m.psa, m.pinv_sa, m.pga);
             #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const double dh = double(__ldg(a.dhat + c0 * D + k));
-                y[k] = __dadd_rn(x0[k], __dmul_rn(dh, m.sa[k]));
+                y[k] = __dadd_rn(x0[k], __dmul_rn(dh, m.psa[k]));
                 split_double(y[k], yh[k], yl[k]);
             }
             const int32_t sd = __ldg(m.seed + grid_cell_f<D>(y, yh, yl, m));

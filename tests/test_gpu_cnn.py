@@ -284,3 +284,127 @@ def test_tensor_core_grid_prediction(ctx, n_side):
     # roundings of 2^-9 on each of two operands, 7 * 2 * 2^-9 ~ 2.7e-2 of the
     # output scale, with the worst of ~4k cells allowed 6e-2
     assert np.abs(tc[pick] - ref).max() <= 6e-2 * np.abs(ref).max()
+
+
+# ---- the predictor grid: cells of 3^d ASG cells ----------------------------
+
+def _oracle_pred_u(om, u_nodal):
+    """FP64 P1 velocity at the predictor-cell centres, hosts by exact search."""
+    cen = om.pred_centres()
+    return oracle.p1_interpolate(om.conn, om.v0, om.M, u_nodal, cen, om.locate(cen))
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 101}), ("abc3d", {"n_side": 13})])
+def test_predictor_grid_velocity(ctx, name, kw):
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    inf = mesh.info()
+    om = oracle.Mesh(c.xyz, c.conn, grid=inf["asg_grid"], pred_stride=3)
+    assert inf["pred_stride"] == 3 and inf["pred_grid"] == list(om.pgrid)
+    U = torch.empty((int(np.prod(om.pgrid)), c.dim), dtype=torch.float32, device="cuda")
+    ctx.grid_velocity(mesh, _dev(c.u), out=U)
+    torch.cuda.synchronize()
+    err = np.abs(U.cpu().numpy() - _oracle_pred_u(om, c.u)).max()
+    assert err <= 5e-4 * np.abs(c.u).max(), err
+    with pytest.raises(Exception):
+        mesh.set_predictor_grid(2)
+
+
+@pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 121, "cfl": 8}),
+                                     ("abc3d", {"n_side": 15, "cfl": 8})])
+def test_track_with_displacements_on_predictor_grid(ctx, name, kw):
+    """Algorithm 2's start rule on a stride-3 predictor grid: predictor cell of
+    x, x + dhat * (predictor cell size), then the ASG seed there. Bit for bit."""
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
+    rng = np.random.default_rng(16)
+    dhat = rng.uniform(-4, 4, size=(int(np.prod(om.pgrid)), c.dim)).astype(np.float32)
+    out = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=_dev(dhat), start_out=True)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.pred_cells(c.x)])
+    start = np.where(want["path_len"] > 0, want["start"], -1)
+    for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
+                   ("status", want["status"]), ("start", start)):
+        assert np.array_equal(got[k], ref), k
+
+
+def test_training_pairs_on_predictor_grid(ctx):
+    import torch
+    c = make_case("tg2d", n_side=91, cfl=6)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    win, tgt, cells = ctx.training_pairs(mesh, _dev(c.x), _dev(c.u), c.dt)
+    torch.cuda.synchronize()
+    assert np.array_equal(cells.cpu().numpy(), om.pred_cells(c.x))
+    xp = c.x - c.u * c.dt
+    assert np.array_equal(tgt.cpu().numpy(), ((xp - c.x) / om.ps).astype(np.float32))
+    U = _oracle_pred_u(om, c.u)
+    ref = cnn.windows(U.reshape(tuple(int(v) for v in om.pgrid[::-1]) + (2,)),
+                      om.pred_cells(c.x), 2, c.dt / om.ps)
+    assert np.abs(win.cpu().numpy() - ref).max() <= 5e-4 * np.abs(ref).max()
+
+
+def test_tensor_core_on_predictor_grid(ctx):
+    """The tcgen05 grid kernel over a stride-3 predictor grid (100 x 100 cells)
+    against the per-window engine on every cell and the FP64 oracle on a sample."""
+    import torch
+    c = make_case("tg2d", n_side=301, cfl=8)
+    flat = init_weights(2, 33)
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(om.pgrid))
+    tc = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+    win = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predictor_engine("tc")
+    ctx.predict(mesh, c.dt, out=tc)
+    ctx.predictor_engine("window")
+    ctx.predict(mesh, c.dt, out=win)
+    ctx.predictor_engine("tc")
+    ctx.device_status()
+    tc, win = tc.cpu().numpy(), win.cpu().numpy()
+    assert np.isfinite(tc).all()
+    assert np.abs(tc - win).max() <= 4e-2 * np.abs(win).max()
+    rng = np.random.default_rng(3)
+    pick = np.unique(np.concatenate([np.arange(0, n_cells, 97), rng.integers(0, n_cells, 800)]))
+    U = _oracle_pred_u(om, c.u)
+    gx, gy = (int(v) for v in om.pgrid)
+    w = cnn.windows(U.reshape(gy, gx, 2), pick, 2, c.dt / om.ps)
+    ref = cnn.forward(2, cnn.unpack(2, flat), w)
+    assert np.abs(tc[pick] - ref).max() <= 6e-2 * np.abs(ref).max()
+
+
+def test_cnn_sns_on_predictor_grid_keeps_hosts(ctx):
+    """CNN-SNS with the predictor on a stride-3 grid: the same hosts as plain
+    SNS (the start only changes the path), and the oracle's start rule."""
+    import torch
+    c = make_case("tg2d", n_side=121, cfl=8)
+    flat = init_weights(2, 12)
+    o = cnn.spec(2)
+    fc2 = sum(int(np.prod(w)) + int(np.prod(b)) for _, w, b in o[:-1])
+    flat[fc2:] *= 0.25
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    out = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn", start_out=True)
+    dhat = torch.empty((int(np.prod(mesh.info()["pred_grid"])), 2), dtype=torch.float32,
+                       device="cuda")
+    ctx.predict(mesh, c.dt, out=dhat)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    plain = om.track(c.x, c.u, c.dt, mode="sns")
+    assert np.array_equal(got["host"], plain["host"])
+    for k in ("host", "path_len", "status"):
+        assert np.array_equal(got[k], want[k]), k
