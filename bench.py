@@ -311,7 +311,7 @@ def main():
     ap.add_argument("--workload", default="tg2d", choices=sorted(WORKLOADS))
     ap.add_argument("--cfl", type=float, default=8.0)
     ap.add_argument("--mode", default="cnn", choices=["sns", "asg", "cnn"])
-    ap.add_argument("--pred-stride", type=int, default=3,
+    ap.add_argument("--pred-stride", type=int, default=5,
                     help="ASG cells per predictor cell and axis (odd; 2-D meshes)")
     ap.add_argument("--train-fields", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
