@@ -312,7 +312,7 @@ def main():
     ap.add_argument("--cfl", type=float, default=8.0)
     ap.add_argument("--mode", default="cnn", choices=["sns", "asg", "cnn"])
     ap.add_argument("--pred-stride", type=int, default=5,
-                    help="ASG cells per predictor cell and axis (odd; 2-D meshes)")
+                    help="ASG cells per predictor cell and axis (odd)")
     ap.add_argument("--train-fields", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
@@ -354,15 +354,11 @@ def main():
     dim = case.dim
     ctx = cs.Context(lrank)
     mesh = ctx.upload_mesh(case.xyz, case.conn)
-    if dim == 2:
-        mesh.set_predictor_grid(args.pred_stride)
+    mesh.set_predictor_grid(args.pred_stride)
     info = mesh.info()
     dev = torch.device("cuda", lrank)
 
-    if dim == 3 and args.mode == "cnn":
-        # the 3-D predictor runs on CUDA-core window GEMMs only: not timed here
-        args.mode = "sns"
-    modes = [args.mode] if args.quick else (["sns", "asg", "cnn"] if dim == 2 else ["sns", "asg"])
+    modes = [args.mode] if args.quick else ["sns", "asg", "cnn"]
     training = None
     if "cnn" in modes:
         training = train_predictor(ctx, mesh, case, args.train_fields, args.train_steps,
@@ -508,8 +504,9 @@ def main():
                        "parallelism": ("%d replicas: every rank locates its own batch of %d particles "
                                         "against its own copy of the mesh, no collective"
                                         % (world, n)) if world > 1 else "1 GPU",
-                       "arithmetic": "walk decisions FP64 (certified FP32 filter); "
-                                     "predictor BF16 x BF16 -> FP32 on tcgen05"},
+                       "arithmetic": "walk decisions FP64 (certified FP32 filter); " + (
+                           "predictor BF16 x BF16 -> FP32 on tcgen05" if dim == 2 else
+                           "predictor BF16-operand window GEMMs, FP32 accumulation, CUDA cores")},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],
             "modes": results, "training": training, "serving": serving,
             "rooflines": rooflines,

@@ -208,9 +208,11 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double
 /* Arithmetic: BF16 operands, FP32 accumulation, FP32 master weights.       */
 /* ------------------------------------------------------------------------ */
 
-/* Engine of grid prediction (cs_predict, CS_CNN_SNS): 1 (default) = the fused
- * tensor-core kernel (tcgen05, 2-D predictor), 0 = per-window GEMMs on CUDA
- * cores (both dims; the 3-D predictor always uses it). */
+/* Engine of grid prediction (cs_predict, CS_CNN_SNS): 1 (default) = fully
+ * convolutional over the predictor grid: the fused tensor-core kernel
+ * (tcgen05) in 2-D, cubic tiles of im2col + GEMM layers on CUDA cores in 3-D;
+ * 0 = every cell's own window through the same GEMM layers (both dims; the
+ * reference the grid engines are tested against). */
 cs_status cs_predictor_engine(cs_ctx *ctx, int engine);
 
 /* Synchronise the device and report whether a bounded device-side wait gave

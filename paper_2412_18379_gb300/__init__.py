@@ -201,8 +201,10 @@ class Context:
 
     # ---------------- start predictor ----------------
     def predictor_engine(self, engine):
-        """'tc' (tensor-core grid kernel, 2-D) or 'window' (CUDA-core GEMMs)."""
-        self._check(self.lib.cs_predictor_engine(self.h, 1 if engine == "tc" else 0))
+        """'grid' (alias 'tc'): fully convolutional over the predictor grid
+        (tensor cores in 2-D, CUDA-core tiles in 3-D); 'window': every cell's
+        own window through CUDA-core GEMMs."""
+        self._check(self.lib.cs_predictor_engine(self.h, 1 if engine in ("tc", "grid") else 0))
 
     def device_status(self):
         self._check(self.lib.cs_device_status(self.h))

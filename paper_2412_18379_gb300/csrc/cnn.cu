@@ -151,6 +151,76 @@ __global__ void __launch_bounds__(kThreads) window_kernel(const DevMesh m, const
     }
 }
 
+// Fully convolutional evaluation over the grid (the "tile engine"): the grid
+// is cut into cubic tiles of T^D cells; tile b's input is the block of side
+// T + 2 R (R = number of 3^D convolutions) around it, channels u_k * scale_k,
+// zero outside the grid, in the channel-first window layout [b][k][S^D]. The
+// valid convolutions then leave exactly the tile's T^D cells, and cell c's
+// value equals that of the window of side 2 R + 1 centred at c.
+template <int D>
+__global__ void __launch_bounds__(kThreads) tile_input_kernel(const DevMesh m,
+                                                              const float *__restrict__ U, int T,
+                                                              int R, int tx, int ty, int64_t t0,
+                                                              int64_t B, float s0, float s1,
+                                                              float s2, float *__restrict__ out) {
+    const int S = T + 2 * R;
+    const int64_t P = D == 2 ? int64_t(S) * S : int64_t(S) * S * S;
+    const float scale[3] = {s0, s1, s2};
+    const int64_t total = B * P;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = q / P;
+        const int64_t p = q % P;
+        const int64_t tile = t0 + b;
+        const int tc[3] = {int(tile % tx), int((tile / tx) % ty), int(tile / (int64_t(tx) * ty))};
+        const int pc[3] = {int(p % S), int((p / S) % S), D == 3 ? int(p / (int64_t(S) * S)) : 0};
+        bool inside = true;
+        int64_t cell = 0, mul = 1;
+        #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int j = tc[k] * T + pc[k] - R;
+            inside = inside && j >= 0 && j < m.ga[k];
+            cell += int64_t(j) * mul;
+            mul *= m.ga[k];
+        }
+        #pragma unroll
+        for (int k = 0; k < D; ++k)
+            out[(b * D + k) * P + p] = inside ? __ldg(U + cell * D + k) * scale[k] : 0.f;
+    }
+}
+
+// dhat[cell] = row (b, position) of the tile engine's output, for the cells
+// of tile t0 + b that lie inside the grid.
+template <int D>
+__global__ void __launch_bounds__(kThreads) tile_scatter_kernel(const DevMesh m, int T, int tx,
+                                                                int ty, int64_t t0, int64_t B,
+                                                                const float *__restrict__ rows,
+                                                                float *__restrict__ dhat) {
+    const int64_t P = D == 2 ? int64_t(T) * T : int64_t(T) * T * T;
+    const int64_t total = B * P;
+    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
+         q += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t b = q / P;
+        const int64_t p = q % P;
+        const int64_t tile = t0 + b;
+        const int tc[3] = {int(tile % tx), int((tile / tx) % ty), int(tile / (int64_t(tx) * ty))};
+        const int pc[3] = {int(p % T), int((p / T) % T), D == 3 ? int(p / (int64_t(T) * T)) : 0};
+        bool inside = true;
+        int64_t cell = 0, mul = 1;
+        #pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int j = tc[k] * T + pc[k];
+            inside = inside && j < m.ga[k];
+            cell += int64_t(j) * mul;
+            mul *= m.ga[k];
+        }
+        if (inside) {
+            #pragma unroll
+            for (int k = 0; k < D; ++k) dhat[cell * D + k] = rows[q * D + k];
+        }
+    }
+}
+
 // im2col of one valid 3^D convolution: col[(b*Po + p)][i*taps + t] =
 // x(b, i, p + offset(t)); x is channels-first [B][C][Si^D] (first layer) or
 // channels-last [B][Si^D][C].
@@ -395,6 +465,32 @@ int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, 
 int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,
                        int sm_count, cudaStream_t st) {
     gather_rows_kernel<<<grid_for(B * row, sm_count, 16), kThreads, 0, st>>>(src, row, idx, B, dst);
+    return 1;
+}
+
+int launch_tile_input(const DevMesh &m, const float *U, int T, int R, int tx, int ty, int64_t t0,
+                      int64_t B, const float scale[3], float *out, int sm_count,
+                      cudaStream_t st) {
+    const int64_t S = T + 2 * R;
+    const int64_t P = m.dim == 2 ? S * S : S * S * S;
+    const int g = grid_for(B * P, sm_count, 32);
+    if (m.dim == 2)
+        tile_input_kernel<2><<<g, kThreads, 0, st>>>(m, U, T, R, tx, ty, t0, B, scale[0],
+                                                     scale[1], scale[2], out);
+    else
+        tile_input_kernel<3><<<g, kThreads, 0, st>>>(m, U, T, R, tx, ty, t0, B, scale[0],
+                                                     scale[1], scale[2], out);
+    return 1;
+}
+
+int launch_tile_scatter(const DevMesh &m, int T, int tx, int ty, int64_t t0, int64_t B,
+                        const float *rows, float *dhat, int sm_count, cudaStream_t st) {
+    const int64_t P = m.dim == 2 ? int64_t(T) * T : int64_t(T) * T * T;
+    const int g = grid_for(B * P, sm_count, 32);
+    if (m.dim == 2)
+        tile_scatter_kernel<2><<<g, kThreads, 0, st>>>(m, T, tx, ty, t0, B, rows, dhat);
+    else
+        tile_scatter_kernel<3><<<g, kThreads, 0, st>>>(m, T, tx, ty, t0, B, rows, dhat);
     return 1;
 }
 

@@ -26,6 +26,10 @@ struct NetShape {
     int64_t positions(int S) const { return dim == 2 ? int64_t(S) * S : int64_t(S) * S * S; }
 };
 
+int launch_tile_input(const DevMesh &m, const float *U, int T, int R, int tx, int ty, int64_t t0,
+                      int64_t B, const float scale[3], float *out, int sm_count, cudaStream_t st);
+int launch_tile_scatter(const DevMesh &m, int T, int tx, int ty, int64_t t0, int64_t B,
+                        const float *rows, float *dhat, int sm_count, cudaStream_t st);
 int launch_pred_seed(const DevMesh &m, int32_t *pseed, int sm_count, cudaStream_t st);
 int launch_interp_table(const DevMesh &m, int32_t *node, float *w, int sm_count,
                         cudaStream_t st);

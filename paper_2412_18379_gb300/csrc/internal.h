@@ -131,6 +131,8 @@ struct Predictor {
     float *dcol = nullptr, *dy0 = nullptr, *dy1 = nullptr, *da5 = nullptr, *win = nullptr,
           *tgt = nullptr;
     int64_t *idx = nullptr;
+    std::vector<float *> tiles;  // workspace of the tile engine (fully convolutional)
+    int64_t tiles_key = -1;      // (tile side, tiles per pass) it was sized for
     uint8_t *packed = nullptr;   // weights in the tensor-core kernel's layout
     bool packed_dirty = true;
 };

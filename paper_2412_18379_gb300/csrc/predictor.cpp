@@ -83,6 +83,9 @@ void free_workspace(Predictor &P) {
     if (P.idx) cudaFree(P.idx);
     P.idx = nullptr;
     P.cap = 0;
+    for (float *p : P.tiles) cudaFree(p);
+    P.tiles.clear();
+    P.tiles_key = -1;
 }
 
 cs_status ensure_workspace(cs_ctx *ctx, Predictor &P, int64_t B) {
@@ -259,6 +262,92 @@ void predictor_release(Predictor &P) {
     P.loaded = false;
 }
 
+// Fully convolutional prediction over the predictor grid on CUDA cores: the
+// grid is cut into cubic tiles of T^D cells, each evaluated as one window of
+// side T + 2 R (the im2col + GEMM layers of the window engine), so the
+// convolutions are shared between neighbouring cells instead of being
+// recomputed for each cell's own window.
+cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float *dhat,
+                        cudaStream_t st) {
+    const DevMesh pv = pred_view(m->d);
+    const int D = pv.dim;
+    NetShape S(D);
+    const int R = S.n_conv;
+    int T = 1, nt[3] = {1, 1, 1};
+    for (int k = 0; k < D; ++k) {
+        const int n = (pv.ga[k] + 23) / 24;            // tiles of at most 24 cells per axis
+        T = std::max(T, (pv.ga[k] + n - 1) / n);
+    }
+    for (int k = 0; k < D; ++k) nt[k] = (pv.ga[k] + T - 1) / T;
+    const int64_t n_tiles = int64_t(nt[0]) * nt[1] * nt[2];
+    // buffer sizes per tile: input, then (col, z, y) per conv layer, z5, a5, out
+    std::vector<int64_t> per;
+    int Si = T + 2 * R, C = S.cin;
+    per.push_back(int64_t(C) * S.positions(Si));
+    for (int l = 0; l < S.n_conv; ++l) {
+        const int64_t Po = S.positions(Si - 2), K = int64_t(C) * S.taps();
+        per.push_back(Po * K);
+        per.push_back(Po * S.ch);
+        per.push_back(Po * S.ch);
+        Si -= 2;
+        C = S.ch;
+    }
+    const int64_t P_out = S.positions(T);
+    per.push_back(P_out * S.hidden);
+    per.push_back(P_out * S.hidden);
+    per.push_back(P_out * D);
+    int64_t tile_floats = 0;
+    for (int64_t v : per) tile_floats += v;
+    const int64_t Bt = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t(1) << 28) / tile_floats));
+    const int64_t key = int64_t(T) * 1000000 + Bt * 10 + D;
+    if (P.tiles_key != key) {
+        for (float *p : P.tiles) cudaFree(p);
+        P.tiles.clear();
+        P.tiles_key = -1;
+        for (int64_t v : per) {
+            float *b = nullptr;
+            cs_status rc = dalloc(ctx, &b, size_t(v * Bt));
+            if (rc) return rc;
+            P.tiles.push_back(b);
+        }
+        P.tiles_key = key;
+    }
+    float scale[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) scale[k] = float(dt / pv.sa[k]);
+    const int sm = ctx->sm_count;
+    for (int64_t t0 = 0; t0 < n_tiles; t0 += Bt) {
+        const int64_t B = std::min(Bt, n_tiles - t0);
+        ctx->launches += launch_tile_input(pv, m->grid_u, T, R, nt[0], nt[1], t0, B, scale,
+                                           P.tiles[0], sm, st);
+        const float *x = P.tiles[0];
+        bool chfirst = true;
+        int Ci = S.cin, Sl = T + 2 * R;
+        for (int l = 0; l < S.n_conv; ++l) {
+            const int64_t Po = S.positions(Sl - 2), K = int64_t(Ci) * S.taps();
+            float *col = P.tiles[1 + 3 * l], *z = P.tiles[2 + 3 * l], *y = P.tiles[3 + 3 * l];
+            ctx->launches += launch_im2col(D, x, B, Ci, Sl, chfirst, col, sm, st);
+            ctx->launches += launch_gemm(col, P.w + S.w_off[l], z, P.w + S.b_off[l], B * Po, S.ch, K,
+                                         false, true, false, st);
+            ctx->launches += launch_relu(z, y, B * Po * S.ch, sm, st);
+            x = y;
+            chfirst = false;
+            Ci = S.ch;
+            Sl -= 2;
+        }
+        const int f1 = S.n_conv, f2 = S.n_conv + 1;
+        float *z5 = P.tiles[1 + 3 * S.n_conv], *a5 = P.tiles[2 + 3 * S.n_conv],
+              *out = P.tiles[3 + 3 * S.n_conv];
+        const int64_t M = B * P_out;
+        ctx->launches += launch_gemm(x, P.w + S.w_off[f1], z5, P.w + S.b_off[f1], M, S.hidden, S.ch,
+                                     false, true, false, st);
+        ctx->launches += launch_relu(z5, a5, M * S.hidden, sm, st);
+        ctx->launches += launch_gemm(a5, P.w + S.w_off[f2], out, P.w + S.b_off[f2], M, D, S.hidden,
+                                     false, true, false, st);
+        ctx->launches += launch_tile_scatter(pv, T, nt[0], nt[1], t0, B, out, dhat, sm, st);
+    }
+    return CS_OK;
+}
+
 // prediction of every ASG cell of mesh m from its stored grid velocity
 cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStream_t st) {
     Predictor *P = get_pred(ctx, m->d.dim);
@@ -283,6 +372,7 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
                                          ctx->sm_count, st);
         return CS_OK;
     }
+    if (m->d.dim == 3 && ctx->engine == 1) return predict_tiles(ctx, *P, m, dt, dhat, st);
     const int64_t chunk = 8192;
     cs_status rc = ensure_workspace(ctx, *P, chunk);
     if (rc) return rc;

@@ -408,3 +408,64 @@ def test_cnn_sns_on_predictor_grid_keeps_hosts(ctx):
     assert np.array_equal(got["host"], plain["host"])
     for k in ("host", "path_len", "status"):
         assert np.array_equal(got[k], want[k]), k
+
+
+@pytest.mark.parametrize("n_side,stride", [(13, 1), (31, 3), (53, 1)])
+def test_tile_engine_3d_matches_windows(ctx, n_side, stride):
+    """The 3-D fully convolutional tile engine against the per-window engine on
+    every predictor cell (one tile, and several tiles with a ragged last one),
+    and the per-window engine against the FP64 oracle on a sample."""
+    import torch
+    c = make_case("abc3d", n_side=n_side, cfl=6)
+    flat = init_weights(3, 41)
+    ctx.load_predictor(3, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(stride)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=stride)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(om.pgrid))
+    tile = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
+    win = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predictor_engine("tc")
+    ctx.predict(mesh, c.dt, out=tile)
+    ctx.predictor_engine("window")
+    ctx.predict(mesh, c.dt, out=win)
+    ctx.predictor_engine("tc")
+    torch.cuda.synchronize()
+    tile, win = tile.cpu().numpy(), win.cpu().numpy()
+    assert np.isfinite(tile).all()
+    # same GEMM layers on the same BF16 operands, summed in the same K order
+    assert np.abs(tile - win).max() <= 1e-5 * np.abs(win).max()
+    rng = np.random.default_rng(7)
+    pick = np.unique(np.concatenate([[0, n_cells - 1], rng.integers(0, n_cells, 200)]))
+    U = _oracle_pred_u(om, c.u)
+    w = cnn.windows(U.reshape(tuple(int(v) for v in om.pgrid[::-1]) + (3,)), pick, 3,
+                    c.dt / om.ps)
+    ref = cnn.forward(3, cnn.unpack(3, flat), w)
+    assert np.abs(win[pick] - ref).max() <= 5e-2 * np.abs(ref).max()
+
+
+def test_cnn_sns_3d_on_tiles_keeps_hosts(ctx):
+    """3-D CNN-SNS through the tile engine: hosts equal plain SNS and the
+    oracle's start rule, bit for bit, on the engine's own predictions."""
+    import torch
+    c = make_case("abc3d", n_side=21, cfl=8)
+    flat = init_weights(3, 12)
+    o = cnn.spec(3)
+    fc2 = sum(int(np.prod(w)) + int(np.prod(b)) for _, w, b in o[:-1])
+    flat[fc2:] *= 0.25
+    ctx.load_predictor(3, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    out = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn")
+    dhat = torch.empty((int(np.prod(mesh.info()["pred_grid"])), 3), dtype=torch.float32,
+                       device="cuda")
+    ctx.predict(mesh, c.dt, out=dhat)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    plain = om.track(c.x, c.u, c.dt, mode="sns")
+    assert np.array_equal(got["host"], plain["host"])
+    for k in ("host", "path_len", "status"):
+        assert np.array_equal(got[k], want[k]), k
