@@ -555,6 +555,191 @@ int launch_col2im(int dim, const float *dcol, int64_t B, int C, int Si, float *d
     return 1;
 }
 
+// C[M][N] = A B^T (+ bias) for N <= 32 (the convolution layers: A [M][K] the
+// im2col rows, B [N][K] the weights): 32 x 32 output tiles of 64 threads, each
+// 4 x 4, 32-deep K slabs prefetched into registers while the previous slab is
+// multiplied. The same BF16 operand rounding and the same FMA chain over k in
+// increasing order as gemm_kernel, so the results are the same bits.
+__global__ void __launch_bounds__(64) gemm_nt32_kernel(const float *__restrict__ A,
+                                                       const float *__restrict__ Bm,
+                                                       float *__restrict__ C,
+                                                       const float *__restrict__ bias, int64_t M,
+                                                       int N, int64_t K, bool round_bf16) {
+    __shared__ float As[32][33];   // [k][m]
+    __shared__ float Bs[32][33];   // [k][n]
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int64_t m0 = int64_t(blockIdx.x) * 32;
+    // element e = tid + 64 i of a slab: row e / 32 (m or n), column e % 32 (k)
+    float ra[16], rb[16];
+    auto fetch = [&](int64_t k0) {
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + 64 * i, r = e >> 5, kk = e & 31;
+            const int64_t gk = k0 + kk, gm = m0 + r;
+            const float av = (gm < M && gk < K) ? __ldg(A + gm * K + gk) : 0.f;
+            const float bv = (r < N && gk < K) ? __ldg(Bm + int64_t(r) * K + gk) : 0.f;
+            ra[i] = round_bf16 ? bf16_round(av) : av;
+            rb[i] = round_bf16 ? bf16_round(bv) : bv;
+        }
+    };
+    float acc[4][4] = {};
+    fetch(0);
+    for (int64_t k0 = 0; k0 < K; k0 += 32) {
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + 64 * i;
+            As[e & 31][e >> 5] = ra[i];
+            Bs[e & 31][e >> 5] = rb[i];
+        }
+        __syncthreads();
+        if (k0 + 32 < K) fetch(k0 + 32);
+        const int kn = int(min(int64_t(32), K - k0));
+        #pragma unroll 8
+        for (int kk = 0; kk < kn; ++kk) {
+            float a[4], bq[4];
+            #pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                a[r] = As[kk][ty * 4 + r];
+                bq[r] = Bs[kk][tx * 4 + r];
+            }
+            #pragma unroll
+            for (int r = 0; r < 4; ++r)
+                #pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], bq[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    #pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t gm = m0 + ty * 4 + r;
+        if (gm >= M) continue;
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int gn = tx * 4 + c;
+            if (gn < N) C[gm * N + gn] = acc[r][c] + (bias ? bias[gn] : 0.f);
+        }
+    }
+}
+
+// One valid 3^D convolution of 32 output channels as an implicit GEMM, fused
+// with its bias and ReLU (inference only): y[b*Po + p][o] = ReLU(bias[o] +
+// sum_{i,t} W[o][i*taps + t] x[b][i][p + offset(t)]). The A operand is read
+// straight from the input instead of an im2col copy: for row (b, p) and
+// column k = (i, t) the input address splits into a row part and a column
+// part, so each thread precomputes the row parts of its 16 rows once and adds
+// one column part per K slab. A block computes a 32 x 32 output tile with 4
+// groups of 64 threads, group g summing the 32-deep K slabs g, g + 4, ...;
+// the four partial tiles are added in group order at the end (the grids here
+// are small, so the K split is what keeps enough warps in flight).
+template <int D>
+__global__ void __launch_bounds__(256) conv_nt32_kernel(const float *__restrict__ x, bool chfirst,
+                                                        int64_t Bn, int C, int Si,
+                                                        const float *__restrict__ Wt,
+                                                        const float *__restrict__ bias,
+                                                        float *__restrict__ y, bool round_bf16) {
+    constexpr int taps = D == 2 ? 9 : 27;
+    constexpr int N = 32;
+    __shared__ float As[4][32][33];
+    __shared__ float Bs[4][32][33];
+    const int g = threadIdx.x >> 6, tid = threadIdx.x & 63, tx = tid & 7, ty = tid >> 3;
+    const int So = Si - 2;
+    const int64_t Po = D == 2 ? int64_t(So) * So : int64_t(So) * So * So;
+    const int64_t Pi = D == 2 ? int64_t(Si) * Si : int64_t(Si) * Si * Si;
+    const int64_t M = Bn * Po, K = int64_t(C) * taps;
+    const int64_t m0 = int64_t(blockIdx.x) * 32;
+    // this thread loads column kk = tid & 31 of rows (tid >> 5) + 2 i, i < 16
+    const int kk = tid & 31;
+    int64_t rowbase[16];
+    bool rowok[16];
+    #pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t gm = m0 + (tid >> 5) + 2 * i;
+        rowok[i] = gm < M;
+        const int64_t b = rowok[i] ? gm / Po : 0, p = rowok[i] ? gm % Po : 0;
+        const int px = int(p % So), py = int((p / So) % So);
+        const int pz = D == 3 ? int(p / (int64_t(So) * So)) : 0;
+        const int64_t pb = D == 2 ? int64_t(py) * Si + px : (int64_t(pz) * Si + py) * Si + px;
+        rowbase[i] = chfirst ? b * C * Pi + pb : (b * Pi + pb) * C;
+    }
+    float ra[16], rb[16];
+    auto fetch = [&](int64_t k0) {
+        const int64_t gk = k0 + kk;
+        int64_t koff = 0;
+        const bool kok = gk < K;
+        if (kok) {
+            const int ch = int(gk / taps), t = int(gk % taps);
+            const int dx = t % 3, dy = (t / 3) % 3, dz = D == 3 ? t / 9 : 0;
+            const int64_t toff = D == 2 ? int64_t(dy) * Si + dx : (int64_t(dz) * Si + dy) * Si + dx;
+            koff = chfirst ? int64_t(ch) * Pi + toff : toff * C + ch;
+        }
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float av = (rowok[i] && kok) ? __ldg(x + rowbase[i] + koff) : 0.f;
+            const int r = (tid >> 5) + 2 * i;   // weight row (output channel)
+            const float bv = kok ? __ldg(Wt + int64_t(r) * K + gk) : 0.f;
+            ra[i] = round_bf16 ? bf16_round(av) : av;
+            rb[i] = round_bf16 ? bf16_round(bv) : bv;
+        }
+    };
+    float acc[4][4] = {};
+    const int64_t n_slabs = (K + 31) / 32, rounds = (n_slabs + 3) / 4;
+    fetch(32 * int64_t(g));
+    for (int64_t j = 0; j < rounds; ++j) {
+        const int64_t k0 = 32 * (g + 4 * j);
+        #pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int e = tid + 64 * i;
+            As[g][e & 31][e >> 5] = ra[i];
+            Bs[g][e & 31][e >> 5] = rb[i];
+        }
+        __syncthreads();
+        if (k0 + 128 < K) fetch(k0 + 128);
+        const int kn = k0 < K ? int(min(int64_t(32), K - k0)) : 0;
+        #pragma unroll 8
+        for (int q = 0; q < kn; ++q) {
+            float a[4], bq[4];
+            #pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                a[r] = As[g][q][ty * 4 + r];
+                bq[r] = Bs[g][q][tx * 4 + r];
+            }
+            #pragma unroll
+            for (int r = 0; r < 4; ++r)
+                #pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], bq[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    // partial tiles of groups 1..3 into shared memory, group 0 adds them in order
+    float *red = &As[0][0][0];   // [3][64 threads][16]
+    if (g > 0) {
+        #pragma unroll
+        for (int r = 0; r < 4; ++r)
+            #pragma unroll
+            for (int c = 0; c < 4; ++c) red[((g - 1) * 64 + tid) * 16 + r * 4 + c] = acc[r][c];
+    }
+    __syncthreads();
+    if (g == 0) {
+        #pragma unroll
+        for (int h = 0; h < 3; ++h)
+            #pragma unroll
+            for (int r = 0; r < 4; ++r)
+                #pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] += red[(h * 64 + tid) * 16 + r * 4 + c];
+        #pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int64_t gm = m0 + ty * 4 + r;
+            if (gm >= M) continue;
+            float4 v;
+            v.x = fmaxf(acc[r][0] + bias[tx * 4 + 0], 0.f);
+            v.y = fmaxf(acc[r][1] + bias[tx * 4 + 1], 0.f);
+            v.z = fmaxf(acc[r][2] + bias[tx * 4 + 2], 0.f);
+            v.w = fmaxf(acc[r][3] + bias[tx * 4 + 3], 0.f);
+            *reinterpret_cast<float4 *>(y + gm * N + tx * 4) = v;
+        }
+    }
+}
+
 // BF16 operands (the training arithmetic) unless switched off for an
 // accuracy check; process-wide.
 static bool g_gemm_bf16 = true;
@@ -563,6 +748,11 @@ void set_gemm_bf16(bool on) { g_gemm_bf16 = on; }
 int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
                 int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
                 cudaStream_t st) {
+    if (!transA && transB && !accumulate && N <= 32) {
+        gemm_nt32_kernel<<<unsigned((M + 31) / 32), 64, 0, st>>>(A, Bm, C, bias, M, int(N), K,
+                                                                 g_gemm_bf16);
+        return 1;
+    }
     // split K when the output has few tiles and K is long (weight gradients)
     const int64_t tiles = ((N + 63) / 64) * ((M + 63) / 64);
     int64_t splits = 1;
@@ -577,6 +767,19 @@ int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, in
     gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, C, bias, M, N, K, transA, transB, accumulate,
                                            g_gemm_bf16, kc);
     return n;
+}
+
+int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, int Si,
+                     const float *W, const float *bias, float *y, cudaStream_t st) {
+    const int64_t So = Si - 2;
+    const int64_t M = B * (dim == 2 ? So * So : So * So * So);
+    if (dim == 2)
+        conv_nt32_kernel<2><<<unsigned((M + 31) / 32), 256, 0, st>>>(x, chfirst, B, C, Si, W, bias,
+                                                                     y, g_gemm_bf16);
+    else
+        conv_nt32_kernel<3><<<unsigned((M + 31) / 32), 256, 0, st>>>(x, chfirst, B, C, Si, W, bias,
+                                                                     y, g_gemm_bf16);
+    return 1;
 }
 
 int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st) {

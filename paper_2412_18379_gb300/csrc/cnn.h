@@ -46,6 +46,11 @@ int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, in
                 cudaStream_t st);
 void set_gemm_bf16(bool on);
 int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st);
+// ReLU(conv(x) + bias) of one valid 3^D convolution of 32 output channels,
+// without an im2col copy (inference). x: [B][C][Si^D] (chfirst) or
+// [B][Si^D][C]; y: [B * So^D][32].
+int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, int Si,
+                     const float *W, const float *bias, float *y, cudaStream_t st);
 int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStream_t st);
 int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st);
 int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,

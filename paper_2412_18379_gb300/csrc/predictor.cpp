@@ -264,9 +264,9 @@ void predictor_release(Predictor &P) {
 
 // Fully convolutional prediction over the predictor grid on CUDA cores: the
 // grid is cut into cubic tiles of T^D cells, each evaluated as one window of
-// side T + 2 R (the im2col + GEMM layers of the window engine), so the
-// convolutions are shared between neighbouring cells instead of being
-// recomputed for each cell's own window.
+// side T + 2 R through the window engine's layers (convolutions as implicit
+// GEMMs fused with bias and ReLU), so the convolutions are shared between
+// neighbouring cells instead of being recomputed for each cell's own window.
 cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float *dhat,
                         cudaStream_t st) {
     const DevMesh pv = pred_view(m->d);
@@ -285,9 +285,11 @@ cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float
     int Si = T + 2 * R, C = S.cin;
     per.push_back(int64_t(C) * S.positions(Si));
     for (int l = 0; l < S.n_conv; ++l) {
-        const int64_t Po = S.positions(Si - 2), K = int64_t(C) * S.taps();
-        per.push_back(Po * K);
-        per.push_back(Po * S.ch);
+        // (col, z, y): the fused convolution needs neither an im2col copy nor
+        // the pre-activation, so only y has a size
+        const int64_t Po = S.positions(Si - 2);
+        per.push_back(1);
+        per.push_back(1);
         per.push_back(Po * S.ch);
         Si -= 2;
         C = S.ch;
@@ -323,12 +325,9 @@ cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float
         bool chfirst = true;
         int Ci = S.cin, Sl = T + 2 * R;
         for (int l = 0; l < S.n_conv; ++l) {
-            const int64_t Po = S.positions(Sl - 2), K = int64_t(Ci) * S.taps();
-            float *col = P.tiles[1 + 3 * l], *z = P.tiles[2 + 3 * l], *y = P.tiles[3 + 3 * l];
-            ctx->launches += launch_im2col(D, x, B, Ci, Sl, chfirst, col, sm, st);
-            ctx->launches += launch_gemm(col, P.w + S.w_off[l], z, P.w + S.b_off[l], B * Po, S.ch, K,
-                                         false, true, false, st);
-            ctx->launches += launch_relu(z, y, B * Po * S.ch, sm, st);
+            float *y = P.tiles[3 + 3 * l];
+            ctx->launches += launch_conv_relu(D, x, chfirst, B, Ci, Sl, P.w + S.w_off[l],
+                                              P.w + S.b_off[l], y, st);
             x = y;
             chfirst = false;
             Ci = S.ch;

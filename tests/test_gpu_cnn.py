@@ -434,8 +434,12 @@ def test_tile_engine_3d_matches_windows(ctx, n_side, stride):
     torch.cuda.synchronize()
     tile, win = tile.cpu().numpy(), win.cpu().numpy()
     assert np.isfinite(tile).all()
-    # same GEMM layers on the same BF16 operands, summed in the same K order
-    assert np.abs(tile - win).max() <= 1e-5 * np.abs(win).max()
+    # the same layers on the same BF16 operands, but the tile engine's
+    # convolutions add their K range as four partial sums: the FP32
+    # reassociation can move an activation across a BF16 rounding boundary
+    # before the next layer, a 2^-8 relative change of that input (1.2e-3 of
+    # the output scale measured); the bound leaves room for a few such flips
+    assert np.abs(tile - win).max() <= 1e-2 * np.abs(win).max()
     rng = np.random.default_rng(7)
     pick = np.unique(np.concatenate([[0, n_cells - 1], rng.integers(0, n_cells, 200)]))
     U = _oracle_pred_u(om, c.u)
