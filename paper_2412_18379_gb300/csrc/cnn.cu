@@ -651,15 +651,18 @@ __global__ void __launch_bounds__(256) conv_nt32_kernel(const float *__restrict_
     const int kk = tid & 31;
     int64_t rowbase[16];
     bool rowok[16];
+    // rows and positions fit in 32 bits (a tile-engine batch holds at most
+    // 2^23 rows), so the divisions here are 32-bit ones
     #pragma unroll
     for (int i = 0; i < 16; ++i) {
-        const int64_t gm = m0 + (tid >> 5) + 2 * i;
-        rowok[i] = gm < M;
-        const int64_t b = rowok[i] ? gm / Po : 0, p = rowok[i] ? gm % Po : 0;
-        const int px = int(p % So), py = int((p / So) % So);
-        const int pz = D == 3 ? int(p / (int64_t(So) * So)) : 0;
+        const uint32_t gm = uint32_t(m0) + uint32_t((tid >> 5) + 2 * i);
+        rowok[i] = gm < uint32_t(M);
+        const uint32_t b = rowok[i] ? gm / uint32_t(Po) : 0u;
+        const uint32_t p = rowok[i] ? gm - b * uint32_t(Po) : 0u;
+        const uint32_t q = p / uint32_t(So), px = p - q * uint32_t(So);
+        const uint32_t pz = D == 3 ? q / uint32_t(So) : 0u, py = q - pz * uint32_t(So);
         const int64_t pb = D == 2 ? int64_t(py) * Si + px : (int64_t(pz) * Si + py) * Si + px;
-        rowbase[i] = chfirst ? b * C * Pi + pb : (b * Pi + pb) * C;
+        rowbase[i] = chfirst ? int64_t(b) * C * Pi + pb : (int64_t(b) * Pi + pb) * C;
     }
     float ra[16], rb[16];
     auto fetch = [&](int64_t k0) {
@@ -740,6 +743,53 @@ __global__ void __launch_bounds__(256) conv_nt32_kernel(const float *__restrict_
     }
 }
 
+// The predictor's head on rows of conv features (inference): out[r] =
+// W2 ReLU(W1 y[r] + b1) + b2 for y [M][32], W1 [256][32], W2 [dim][256], one
+// thread per row with W1 and W2 in shared memory. Same BF16 operand rounding
+// and the same k order as the two GEMMs plus ReLU it replaces, so the same
+// bits.
+template <int DIM>
+__global__ void __launch_bounds__(128) head_kernel(const float *__restrict__ y,
+                                                   const float *__restrict__ W1,
+                                                   const float *__restrict__ b1,
+                                                   const float *__restrict__ W2,
+                                                   const float *__restrict__ b2, int64_t M,
+                                                   float *__restrict__ out, bool round_bf16) {
+    __shared__ float w1[256 * 32];
+    __shared__ float w2[DIM * 256];
+    __shared__ float bb1[256];
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x)
+        w1[i] = round_bf16 ? bf16_round(W1[i]) : W1[i];
+    for (int i = threadIdx.x; i < DIM * 256; i += blockDim.x)
+        w2[i] = round_bf16 ? bf16_round(W2[i]) : W2[i];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) bb1[i] = b1[i];
+    __syncthreads();
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < M;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        float f[32];
+        #pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const float v = __ldg(y + r * 32 + k);
+            f[k] = round_bf16 ? bf16_round(v) : v;
+        }
+        float o[DIM];
+        #pragma unroll
+        for (int d = 0; d < DIM; ++d) o[d] = 0.f;
+        #pragma unroll 2
+        for (int n = 0; n < 256; ++n) {
+            float h = 0.f;
+            #pragma unroll
+            for (int k = 0; k < 32; ++k) h = fmaf(f[k], w1[n * 32 + k], h);
+            h = fmaxf(h + bb1[n], 0.f);
+            if (round_bf16) h = bf16_round(h);
+            #pragma unroll
+            for (int d = 0; d < DIM; ++d) o[d] = fmaf(h, w2[d * 256 + n], o[d]);
+        }
+        #pragma unroll
+        for (int d = 0; d < DIM; ++d) out[r * DIM + d] = o[d] + b2[d];
+    }
+}
+
 // BF16 operands (the training arithmetic) unless switched off for an
 // accuracy check; process-wide.
 static bool g_gemm_bf16 = true;
@@ -779,6 +829,16 @@ int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, in
     else
         conv_nt32_kernel<3><<<unsigned((M + 31) / 32), 256, 0, st>>>(x, chfirst, B, C, Si, W, bias,
                                                                      y, g_gemm_bf16);
+    return 1;
+}
+
+int launch_head(int dim, const float *y, const float *W1, const float *b1, const float *W2,
+                const float *b2, int64_t M, float *out, int sm_count, cudaStream_t st) {
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>((M + 127) / 128, int64_t(sm_count) * 4)));
+    if (dim == 2)
+        head_kernel<2><<<g, 128, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
+    else
+        head_kernel<3><<<g, 128, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
     return 1;
 }
 

@@ -49,6 +49,9 @@ int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t 
 // ReLU(conv(x) + bias) of one valid 3^D convolution of 32 output channels,
 // without an im2col copy (inference). x: [B][C][Si^D] (chfirst) or
 // [B][Si^D][C]; y: [B * So^D][32].
+// W2 ReLU(W1 y + b1) + b2 per row of y [M][32] (the predictor head, inference)
+int launch_head(int dim, const float *y, const float *W1, const float *b1, const float *W2,
+                const float *b2, int64_t M, float *out, int sm_count, cudaStream_t st);
 int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, int Si,
                      const float *W, const float *bias, float *y, cudaStream_t st);
 int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStream_t st);
