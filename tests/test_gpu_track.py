@@ -59,6 +59,8 @@ CASES = [
     ("tg2d", {"n_side": 201, "cfl": 16}),
     ("abc3d", {"n_side": 21, "cfl": 4}),
     ("abc3d", {"n_side": 21, "cfl": 20}),
+    ("hole2d", {"n_side": 61}),      # non-convex: walks blocked by the hole
+    ("hole2d", {"n_side": 121}),
 ]
 
 
@@ -71,6 +73,22 @@ def test_track_parity(ctx, name, kw, mode):
     got = _run(ctx, mesh, c, mode=mode)
     want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode=mode))
     _compare(got, want, "%s %s %s" % (name, kw, mode))
+    mesh.release()
+
+
+def test_non_convex_domain_uses_the_exact_search(ctx):
+    """Walks that meet the hole's boundary with the departure point beyond it
+    end in the exact search (FOUND_VIA_FALLBACK); departure points in the hole
+    or outside the square are OUTSIDE. Same bits as the oracle."""
+    c = make_case("hole2d", n_side=61)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    got = _run(ctx, mesh, c)
+    _compare(got, _oracle_out(om, om.track(c.x, c.u, c.dt)), "hole2d")
+    counts = np.bincount(got["status"], minlength=4)
+    assert counts[2] > 20 and counts[1] > 100, counts
+    r = np.linalg.norm(c.x - c.u * c.dt - 0.5, axis=1)
+    assert (got["host"][r < 0.09] == -1).all()            # inside the hole
     mesh.release()
 
 

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .meshes import mesh_2d, mesh_3d
+from .meshes import mesh_2d, mesh_2d_hole, mesh_3d
 from .fields import (rotation, taylor_green, abc_flow, fourier_modes_2d,
                      fourier_modes_3d, dt_for_cfl)
 
@@ -64,6 +64,13 @@ def make_case(name, cfl=None, n_side=None, seed=None, field_seed=None):
         xyz, conn, h = mesh_2d(n_side, 0.3, 100 if seed is None else seed)
         u = fourier_modes_2d(xyz, 1000 if field_seed is None else field_seed)
         cfl = 8.0 if cfl is None else cfl
+    elif name == "hole2d":
+        # uniform flow past a disc-shaped hole: the walks of the nodes behind
+        # the hole meet its boundary, and some departure points fall in it
+        n_side = n_side or 101
+        xyz, conn, h = mesh_2d_hole(n_side, 0.1, 0.3, 7 if seed is None else seed)
+        u = np.ascontiguousarray(np.broadcast_to(np.array([0.94, 0.34]), xyz.shape))
+        cfl = 16.0 if cfl is None else cfl
     elif name == "modes3d":
         n_side = n_side or 41
         xyz, conn, h = mesh_3d(n_side, 0.1, 200 if seed is None else seed)

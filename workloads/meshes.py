@@ -55,6 +55,38 @@ def mesh_2d(n_side, jitter=0.3, seed=1):
     return _mesh_2d_cached(int(n_side), float(jitter), int(seed))
 
 
+@functools.lru_cache(maxsize=4)
+def _mesh_2d_hole_cached(n_side, radius, jitter, seed):
+    xyz, h = lattice_2d(n_side, jitter, seed)
+    c = np.array([0.5, 0.5])
+    keep = np.linalg.norm(xyz - c, axis=1) > radius + 0.5 * h
+    m = max(8, int(np.ceil(2 * np.pi * radius / h)))
+    t = 2 * np.pi * np.arange(m) / m
+    ring = c + radius * np.stack([np.cos(t), np.sin(t)], axis=1)
+    pts = np.concatenate([xyz[keep], ring])
+    conn = delaunay_2d(pts)
+    cen = pts[conn].mean(axis=1)
+    conn = conn[np.linalg.norm(cen - c, axis=1) > radius]
+    used = np.unique(conn)                       # drop vertices no triangle uses
+    remap = np.full(pts.shape[0], -1, dtype=np.int64)
+    remap[used] = np.arange(used.shape[0])
+    pts = np.ascontiguousarray(pts[used])
+    conn = np.ascontiguousarray(remap[conn].astype(np.int32))
+    pts.setflags(write=False)
+    conn.setflags(write=False)
+    return pts, conn, h
+
+
+def mesh_2d_hole(n_side, radius=0.2, jitter=0.3, seed=7):
+    """(xyz, conn, h): the jittered Delaunay square with a disc of `radius`
+    at its centre taken out (a non-convex domain: walks can meet the hole's
+    boundary while the departure point lies in the domain beyond it). The
+    lattice points within radius + h/2 of the centre are replaced by a ring of
+    points on the circle, spaced about h; triangles whose centroid lies in the
+    disc are dropped (read-only, cached)."""
+    return _mesh_2d_hole_cached(int(n_side), float(radius), float(jitter), int(seed))
+
+
 # Six Kuhn tetrahedra of the cell [0,1]^3: each is the path
 # 000 -> e_a -> e_a+e_b -> 111 for one permutation (a, b, c) of the axes.
 # Corner bit k of a corner index is its offset along axis k.
