@@ -143,10 +143,10 @@ cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
  * neighbour, and stops after step_cap evaluations. Particles whose walk
  * left the mesh or hit the cap, and those whose final element has some
  * lambda < tau (near a face, where a lower id may also contain x_p), go
- * through an exact search of the bucket index; the result is the host
- * defined at the top of this file.
- * Errors: CS_EINVAL (n < 0, null pointer, start == NULL with n != n_v,
- * bad mode), CS_ENOMESH, CS_ENOPRED, CS_ENOMEM, CS_ECUDA.
+ * through an exact search of the bucket index, run by the warp that walked
+ * them; the result is the host defined at the top of this file.
+ * Errors: CS_EINVAL (n outside [0, 2^31 - 2], null pointer, start == NULL
+ * with n != n_v, bad mode), CS_ENOMESH, CS_ENOPRED, CS_ENOMEM, CS_ECUDA.
  */
 cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
                    const double *u, double dt, const int32_t *start, int mode,
@@ -170,12 +170,11 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
  * cudaMalloc / cudaFree may cause. Same arguments, semantics, results and
  * errors as cs_track (DEVICE pointers, enqueued on `stream`, returns without
  * synchronising); the caller still provides every input and output array.
- * The walk's scratch (work cursor, exact-search count and list) lives in one
- * fixed device array of this library, 8 MiB + 256 B, that every GPU loading
- * the library holds until the process exits.
- *   - n must not exceed 2,097,152 (1 << 21); larger n returns CS_EINVAL with a
- *     message naming the limit. Nothing is allocated, ever: no cudaMalloc,
- *     cudaFree or allocating library routine is called.
+ * The walk's only scratch, its work cursor, lives in one fixed 256-byte
+ * device array of this library that every GPU loading the library holds
+ * until the process exits.
+ *   - n has cs_track's range, [0, 2^31 - 2]. Nothing is allocated, ever: no
+ *     cudaMalloc, cudaFree or allocating library routine is called.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.
@@ -391,8 +390,9 @@ typedef struct cs_profile {
     int64_t launches[8];   /* per stage: calls measured                      */
     double  ms[8];         /* per stage: summed event time, milliseconds     */
 } cs_profile;
-#define CS_STAGE_WALK      0   /* departure + start + Algorithm 1 walk       */
-#define CS_STAGE_FALLBACK  1   /* exact search / canonicalisation            */
+#define CS_STAGE_WALK      0   /* departure + start + Algorithm 1 walk, and
+                                  the exact searches, which run inside it    */
+#define CS_STAGE_FALLBACK  1   /* reserved: no longer a separate kernel      */
 #define CS_STAGE_RESAMPLE  2   /* nodal velocity -> predictor grid           */
 #define CS_STAGE_CNN       3   /* CNN forward over the predictor grid        */
 #define CS_STAGE_TRAIN     4   /* one training step (forward+backward+Adam)  */

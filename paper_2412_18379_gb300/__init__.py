@@ -161,7 +161,7 @@ class Context:
                       stream=None):
         """cs_track_noalloc: like track(), but the library allocates nothing;
         pass `out` (preallocated device tensors) to keep the call allocation-
-        free on this side too. n <= 2,097,152."""
+        free on this side too. Same n range as track()."""
         import torch
         n = x.shape[0]
         dev = x.device

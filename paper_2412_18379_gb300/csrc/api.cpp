@@ -53,21 +53,12 @@ cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
     return it == ctx->meshes.end() ? nullptr : it->second;
 }
 
-cs_status ensure_scratch(cs_ctx *ctx, int64_t n) {
+cs_status ensure_scratch(cs_ctx *ctx) {
     cs::Scratch &s = ctx->scratch;
     if (!s.counters) {
         if (cudaMalloc(&s.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
             cudaMalloc(&s.stats, 8 * sizeof(int64_t)) != cudaSuccess)
             return fail(ctx, CS_ENOMEM, "cudaMalloc of scratch counters failed");
-    }
-    if (s.list_cap < n) {
-        if (s.list) cudaFree(s.list);
-        s.list = nullptr;
-        s.list_cap = 0;
-        const int64_t cap = std::max<int64_t>(n, 1024);
-        if (cudaMalloc(&s.list, size_t(cap) * sizeof(int32_t)) != cudaSuccess)
-            return fail(ctx, CS_ENOMEM, "cudaMalloc of the exact-search list failed");
-        s.list_cap = cap;
     }
     return CS_OK;
 }
@@ -104,7 +95,6 @@ void cs_destroy(cs_ctx *ctx) {
     if (ctx->dev_err) cudaFree(ctx->dev_err);
     if (ctx->scratch.counters) cudaFree(ctx->scratch.counters);
     if (ctx->scratch.stats) cudaFree(ctx->scratch.stats);
-    if (ctx->scratch.list) cudaFree(ctx->scratch.list);
     if (ctx->scratch.stage) cudaFree(ctx->scratch.stage);
     for (const auto &r : ctx->prof.pending) {
         cudaEventDestroy(r.a);
@@ -345,14 +335,14 @@ cs_status cs::cs_track_impl(cs_ctx *ctx, cs::Mesh *m, int64_t n, const double *x
                             const float *dhat, int32_t *host_out, int32_t *path_len_out,
                             uint8_t *status_out, int32_t *start_out, cudaStream_t stream) {
     if (n < 0 || n >= (int64_t(1) << 31) - 1)
-        return fail(ctx, CS_EINVAL, "cs_track: n out of range");
+        return fail(ctx, CS_EINVAL, "cs_track: n is outside [0, 2^31 - 2]");
     if (n == 0) return CS_OK;
     if (!x || !u || !host_out || !path_len_out || !status_out)
         return fail(ctx, CS_EINVAL, "cs_track: null pointer");
     if (!start && n != m->d.n_v)
         return fail(ctx, CS_EINVAL, "cs_track: start == NULL needs n == n_vertices");
     CS_CUDA(ctx, cudaSetDevice(ctx->device));
-    cs_status rc = ensure_scratch(ctx, n);
+    cs_status rc = ensure_scratch(ctx);
     if (rc) return rc;
     cs::TrackArgs a{};
     a.n = n;
@@ -430,7 +420,7 @@ cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len, const 
                          int64_t out[6], void *stream) {
     if (!ctx || !out || n < 0 || (n > 0 && (!path_len || !status))) return CS_EINVAL;
     CS_CUDA(ctx, cudaSetDevice(ctx->device));
-    cs_status rc = ensure_scratch(ctx, 0);
+    cs_status rc = ensure_scratch(ctx);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ctx->launches += cs::launch_stats(n, path_len, status, ctx->scratch.stats, ctx->sm_count, st);

@@ -137,12 +137,10 @@ struct Predictor {
     bool packed_dirty = true;
 };
 
-// Device scratch owned by a context: counters and the exact-search list.
+// Device scratch owned by a context.
 struct Scratch {
-    int32_t *counters = nullptr;   // [0] work cursor, [1] fallback count
+    int32_t *counters = nullptr;   // [0] work cursor of the walk (16 reserved)
     int64_t *stats = nullptr;      // [8]
-    int32_t *list = nullptr;       // [cap] particle indices for exact search
-    int64_t list_cap = 0;
     char *stage = nullptr;         // device staging of cs_track_host
     size_t stage_cap = 0;
 };
@@ -217,8 +215,6 @@ struct Profiler {
 // kernel launchers (walk.cu); each returns the number of kernels launched
 int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
                  cudaStream_t st, Profiler *prof = nullptr);
-int launch_fallback(const DevMesh &m, const TrackArgs &a, const int32_t *count,
-                    const int32_t *list, int sm_count, cudaStream_t st, Profiler *prof);
 int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st);
 int launch_stats(int64_t n, const int32_t *path, const uint8_t *status, int64_t *out,
                  int sm_count, cudaStream_t st);

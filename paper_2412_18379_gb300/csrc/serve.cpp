@@ -120,7 +120,6 @@ size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn) {
     add(n * 4);                      // host
     add(n * 4);                      // path
     add(n);                          // status
-    add(std::max<size_t>(n, 1) * 4); // exact-search list
     if (cnn) add(size_t(m.d.n_pasg) * d * 4);  // predicted displacement grid
     return b;
 }
@@ -144,7 +143,6 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     int32_t *host = reinterpret_cast<int32_t *>(take(n * 4));
     int32_t *path = reinterpret_cast<int32_t *>(take(n * 4));
     uint8_t *status = reinterpret_cast<uint8_t *>(take(n));
-    int32_t *list = reinterpret_cast<int32_t *>(take(std::max<size_t>(n, 1) * 4));
     float *dhat = q.used_mode == CS_CNN_SNS ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4))
                                             : nullptr;
     cudaStream_t st = sl.st;
@@ -171,8 +169,6 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     a.start_out = nullptr;
     Scratch sc;
     sc.counters = sl.counters;
-    sc.list = list;
-    sc.list_cap = int64_t(std::max<size_t>(n, 1));
     ctx->launches += launch_track(m.d, a, sc, ctx->sm_count, st, nullptr);
     e = cudaMemcpyAsync(r.host_out, host, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.path_len_out, path, n * 4, cudaMemcpyDeviceToHost, st);

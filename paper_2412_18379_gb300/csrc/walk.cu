@@ -10,6 +10,14 @@
 // step, a ballot finds the lanes whose particle finished; they pop the next
 // prepared particles from the queue, so long walks never leave lanes idle
 // while work remains.
+//
+// Exact search. A walk that leaves the mesh or reaches the step cap, a
+// particle with no start element, and a walk that ends within tau of an
+// interior face (where a lower id may contain x_p too) are resolved where
+// they occur: the whole warp runs the bucketed exact search for that lane's
+// x_p, then goes on walking. These are a few particles in a million, so the
+// pause is short and the other warps keep the SM busy; a separate pass over
+// a list would pay a launch and a tail for them.
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -32,13 +40,12 @@ template <int D> struct Queue {
 // Called by all 32 lanes of the warp.
 template <int D>
 __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, int64_t pp,
-                                        bool valid, Queue<D> &q, int lane, int32_t *fb_count,
-                                        int32_t *fb_list) {
+                                        bool valid, Queue<D> &q, int lane) {
     bool need_search = false;
     int32_t entry = -1, s = -1;
+    double xp[D];
+    float xh[D], xl[D];
     if (valid) {
-        double xp[D];
-        float xh[D], xl[D];
         bool finite = true;
         #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -83,9 +90,8 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
             a.status[pp] = CS_INVALID;
             if (a.start_out) a.start_out[pp] = -1;
         } else if (s < 0) {
-            a.host[pp] = -1;
+            // no start element: the exact search alone decides
             a.path[pp] = 0;
-            a.status[pp] = kPending;
             if (a.start_out) a.start_out[pp] = -1;
             need_search = true;
         } else {
@@ -100,13 +106,19 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
     }
     q.p[lane] = entry;
     q.cur[lane] = s;
-    push_list(need_search, pp, fb_count, fb_list, lane);
+    for (unsigned want = __ballot_sync(kFull, need_search); want; want &= want - 1) {
+        const int j = __ffs(want) - 1;
+        const int32_t h = exact_search_lane<D>(m, xp, xh, xl, j, lane);
+        if (lane == j) {
+            a.host[pp] = h;
+            a.status[pp] = h >= 0 ? CS_FOUND_VIA_FALLBACK : CS_OUTSIDE;
+        }
+    }
 }
 
 template <int D>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh m, const TrackArgs a,
-                                                   int32_t *cursor, int32_t *fb_count,
-                                                   int32_t *fb_list) {
+                                                   int32_t *cursor) {
     using WR = typename Recs<D>::W;
     using XR = typename Recs<D>::X;
     __shared__ Queue<D> queues[kWarps];
@@ -130,8 +142,10 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
         while (idle) {
             if (q_head >= q_n) {
                 if (drained) break;
-                int base = 0;
-                if (lane == 0) base = atomicAdd(cursor, 32);
+                // unsigned: n < 2^31 and the cursor overshoots n by at most
+                // 32 per warp, so it cannot wrap
+                unsigned base = 0;
+                if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned *>(cursor), 32u);
                 base = __shfl_sync(kFull, base, 0);
                 if (int64_t(base) >= n) {
                     drained = true;
@@ -139,7 +153,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
                 }
                 q_n = int(min(int64_t(32), n - base));
                 __syncwarp();
-                prepare<D>(m, a, int64_t(base) + lane, lane < q_n, q, lane, fb_count, fb_list);
+                prepare<D>(m, a, int64_t(base) + lane, lane < q_n, q, lane);
                 __syncwarp();
                 q_head = 0;
             }
@@ -166,7 +180,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
         if (__ballot_sync(kFull, p >= 0) == 0) break;
 
         // ---- one step of Algorithm 1 for every busy lane ----
-        bool done = false, search = false;
+        bool done = false, search = false, found = false;
         if (p >= 0) {
             WalkE<D> e;
             load_walk(rw, cur, e);
@@ -248,22 +262,27 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
                 }
             }
             if (inside) {
-                a.host[p] = e.uid;
+                if (!near) a.host[p] = e.uid;
                 a.path[p] = it;
                 a.status[p] = CS_FOUND;
-                done = true;
+                done = found = true;
                 search = near;      // another element may contain x_p too
             } else if (next < 0 || it >= m.cap) {
-                a.host[p] = -1;
-                a.path[p] = it;
-                a.status[p] = kPending;
+                a.path[p] = it;     // left the mesh or reached the step cap
                 done = true;
                 search = true;
             } else {
                 cur = next;
             }
         }
-        push_list(search, p, fb_count, fb_list, lane);
+        for (unsigned want = __ballot_sync(kFull, search); want; want &= want - 1) {
+            const int j = __ffs(want) - 1;
+            const int32_t h = exact_search_lane<D>(m, xp, xh, xl, j, lane);
+            if (lane == j) {
+                a.host[p] = h;
+                if (!found) a.status[p] = h >= 0 ? CS_FOUND_VIA_FALLBACK : CS_OUTSIDE;
+            }
+        }
         if (done) p = -1;
     }
 }
@@ -273,7 +292,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
 int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
                  cudaStream_t st, Profiler *prof) {
     if (a.n == 0) return 0;
-    cudaMemsetAsync(s.counters, 0, 2 * sizeof(int32_t), st);
+    cudaMemsetAsync(s.counters, 0, sizeof(int32_t), st);
     static int per_sm[4] = {0, 0, 0, 0};
     if (!per_sm[m.dim]) {
         if (m.dim == 2)
@@ -286,11 +305,11 @@ int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_
     const int grid = int(std::min<int64_t>(int64_t(sm_count) * per_sm[m.dim], need));
     const int ev = prof ? prof->begin(CS_STAGE_WALK, st) : -1;
     if (m.dim == 2)
-        walk_kernel<2><<<grid, 256, 0, st>>>(m, a, s.counters, s.counters + 1, s.list);
+        walk_kernel<2><<<grid, 256, 0, st>>>(m, a, s.counters);
     else
-        walk_kernel<3><<<grid, 256, 0, st>>>(m, a, s.counters, s.counters + 1, s.list);
+        walk_kernel<3><<<grid, 256, 0, st>>>(m, a, s.counters);
     if (prof) prof->end(ev, st);
-    return 1 + launch_fallback(m, a, s.counters + 1, s.list, sm_count, st, prof);
+    return 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -299,18 +318,15 @@ int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_
 // Some callers cannot let this library allocate device memory during a call:
 // a host solver that owns all device memory through its own pool, or a time-
 // step loop that must not pay the implicit device synchronisation that
-// cudaMalloc / cudaFree can cause. For them the walk's scratch (the work
-// cursor, the exact-search count and the exact-search list) lives in this
-// fixed, file-scope device array instead of the context's scratch buffers.
-// Every GPU that loads the library holds it until the process exits.
+// cudaMalloc / cudaFree can cause. For them the walk's only scratch, its
+// work cursor, lives in this fixed, file-scope device array instead of the
+// context's scratch buffers. Every GPU that loads the library holds it (256
+// bytes) until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 21;   // 2,097,152 particles
-constexpr int64_t kNoAllocListOffset = 64;                   // list starts 256 B in
-// [0] work cursor, [1] exact-search count, [64 ...] exact-search list
-static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocListOffset +
-                                                           kNoAllocMaxParticles];
+// [0] work cursor; the rest is padding to one 256-byte line
+static __device__ __align__(256) int32_t g_noalloc_scratch[64];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -332,9 +348,9 @@ extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, c
         return CS_ENOMESH;
     }
     const Mesh *mesh = it->second;
-    if (n < 0 || n > kNoAllocMaxParticles) {
+    if (n < 0 || n >= (int64_t(1) << 31) - 1) {
         ctx->err = "cs_track_noalloc: n = " + std::to_string(n) +
-                   " is outside [0, 2097152], the capacity of its fixed scratch array";
+                   " is outside [0, 2^31 - 2]";
         return CS_EINVAL;
     }
     if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS) {
@@ -382,8 +398,6 @@ extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, c
     }
     Scratch s;
     s.counters = base;                      // zeroed by launch_track on the stream
-    s.list = base + kNoAllocListOffset;
-    s.list_cap = kNoAllocMaxParticles;
     TrackArgs a{};
     a.n = n;
     a.x = x;

@@ -1,6 +1,6 @@
 // Device helpers shared by the walk and the exact search: record loads, the
 // FP64 barycentric arithmetic (the arbiter), the certified FP32 filter, ASG
-// grid cells and the exact-search list.
+// grid cells and the warp-cooperative exact search.
 //
 // Exact arithmetic. Every decision of the walk is that of FP64 barycentric
 // coordinates with a pinned rounding order (no fused multiply-add):
@@ -26,7 +26,6 @@
 namespace cs {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint8_t kPending = 0xff;  // status: the exact search decides
 
 // FP32 unit roundoff u = 2^-24 and the filter's constants
 constexpr float kU = 5.9604644775390625e-08f;
@@ -235,16 +234,69 @@ __device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh,
     return grid_cell_cert<D>(x, xh, xl, m, m.sa, m.inv_sa, m.ga);
 }
 
-// Warp-aggregated append of particle p to the exact-search list.
-__device__ __forceinline__ void push_list(bool want, int64_t p, int32_t *count, int32_t *list,
-                                          int lane) {
-    const unsigned msk = __ballot_sync(kFull, want);
-    if (!msk) return;
-    int base = 0;
-    const int leader = __ffs(msk) - 1;
-    if (lane == leader) base = atomicAdd(count, __popc(msk));
-    base = __shfl_sync(kFull, base, leader);
-    if (want) list[base + __popc(msk & ((1u << lane) - 1u))] = int32_t(p);
+// Monotone integer key of a non-NaN double: a < b <=> key(a) < key(b), with
+// +0 and -0 equal (exact comparisons on the integer pipe).
+__device__ __forceinline__ unsigned long long order_key(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    if ((b << 1) == 0) return 0x8000000000000000ull;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// Exact search for the point that lane j holds (xp and its hi/lo split): the
+// host of x_p is the lowest user id among the elements containing it (every
+// FP64 lambda >= -eps, Sec. 2.2), or -1. Candidates are the elements listed in
+// x_p's cell of the bucket index. Called by all 32 lanes of a warp; each lane
+// tests every 32nd candidate, then a warp-wide min. Finite x_p only.
+template <int D>
+__device__ __forceinline__ int32_t exact_search_lane(const DevMesh &m, const double *xp,
+                                                     const float *xh, const float *xl, int j,
+                                                     int lane) {
+    using WR = typename Recs<D>::W;
+    using XR = typename Recs<D>::X;
+    const WR *__restrict__ rw = static_cast<const WR *>(m.recw);
+    const XR *__restrict__ rx = static_cast<const XR *>(m.recx);
+    double q[D];
+    float qh[D], ql[D];
+    bool outside = false;
+    #pragma unroll
+    for (int k = 0; k < D; ++k) {
+        q[k] = __shfl_sync(kFull, xp[k], j);
+        qh[k] = __shfl_sync(kFull, xh[k], j);
+        ql[k] = __shfl_sync(kFull, xl[k], j);
+        const unsigned long long key = order_key(q[k]);
+        outside = outside || key < order_key(m.lo_m[k]) || key > order_key(m.hi_m[k]);
+    }
+    // no element's grown box reaches x_p
+    if (outside) return -1;
+    const int64_t c = grid_cell_cert<D>(q, qh, ql, m, m.sb, m.inv_sb, m.gb);
+    const int32_t t0 = __ldg(m.bstart + c), t1 = __ldg(m.bstart + c + 1);
+    unsigned best = 0xffffffffu;
+    for (int32_t t = t0 + lane; t < t1; t += 32) {
+        const int32_t el = __ldg(m.bitems + t);
+        WalkE<D> e;
+        load_walk(rw, el, e);
+        // containment certified in FP32 when possible, else decided by the
+        // FP64 coordinates
+        float lf[D + 1], T[D + 1];
+        bary32<D>(e, qh, ql, lf, T);
+        bool cin = true, cout = false;
+        #pragma unroll
+        for (int i = 0; i <= D; ++i) {
+            cin = cin && (lf[i] - T[i] >= kNegEpsIn);
+            cout = cout || (lf[i] + T[i] < kNegEpsOut);
+        }
+        bool inside = cin;
+        if (!cin && !cout) {
+            double lam[D + 1];
+            bary64(rx, el, q, lam);
+            inside = true;
+            #pragma unroll
+            for (int i = 0; i <= D; ++i) inside = inside && (lam[i] >= -CS_EPS);
+        }
+        if (inside) best = min(best, unsigned(e.uid));
+    }
+    best = __reduce_min_sync(kFull, best);
+    return best == 0xffffffffu ? -1 : int32_t(best);
 }
 
 }  // namespace cs

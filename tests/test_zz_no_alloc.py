@@ -3,7 +3,9 @@
 It serves callers that cannot let a library allocate during a call (a solver
 that owns all device memory through its own pool, or a time-step loop that
 cannot afford the synchronisation cudaMalloc/cudaFree may bring). Its scratch
-is a fixed device array inside the library, shared by every call. These tests
+is a fixed 256-byte device array inside the library (the walk's work
+cursor; the exact searches run inside the walk and need no list), shared by
+every call. These tests
 call it through the C ABI and compare it with cs_track, which uses the
 context's allocated scratch, on two calls in a row (the second call must not
 see the first call's leftovers). This file is named to be collected last.
@@ -16,7 +18,7 @@ from workloads import make_case
 
 pytestmark = pytest.mark.gpu
 
-MAX_N = 1 << 21
+N_LIMIT = (1 << 31) - 1     # first n that cs_track and cs_track_noalloc reject
 
 
 @pytest.fixture(scope="module")
@@ -71,14 +73,38 @@ def test_noalloc_explicit_starts_and_limit(ctx):
         torch.cuda.synchronize()
         for k in want:
             assert torch.equal(got[k], want[k]), k
-    # beyond the fixed capacity: a clear error, nothing launched or written
+    # outside cs_track's range: a clear error, nothing launched or written
     big = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
     h = torch.full((4,), -7, dtype=torch.int32, device="cuda")
-    rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, MAX_N + 1, big.data_ptr(), big.data_ptr(),
-                                  0.1, start.data_ptr(), cs.CS_SNS, h.data_ptr(), h.data_ptr(),
-                                  h.data_ptr(), None, None)
-    assert rc == -1                                   # CS_EINVAL
-    assert "2097152" in ctx.lib.cs_last_error(ctx.h).decode()
+    for n in (N_LIMIT, -1):
+        rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, n, big.data_ptr(), big.data_ptr(),
+                                      0.1, start.data_ptr(), cs.CS_SNS, h.data_ptr(),
+                                      h.data_ptr(), h.data_ptr(), None, None)
+        assert rc == -1                               # CS_EINVAL
+        assert "2^31 - 2" in ctx.lib.cs_last_error(ctx.h).decode()
     torch.cuda.synchronize()
     assert (h.cpu().numpy() == -7).all()
+    mesh.release()
+
+
+def test_noalloc_three_million_particles(ctx):
+    """More particles than any fixed per-particle scratch of 2^21 entries would
+    hold: 3.1M particles (the 301^2 Taylor-Green particles, repeated 34 times
+    with explicit starts), same bits as cs_track."""
+    import torch
+    c = make_case("tg2d", n_side=301, cfl=12)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    reps = 34
+    x = _dev(np.tile(c.x, (reps, 1)))
+    u = _dev(np.tile(c.u, (reps, 1)))
+    start = _dev(np.tile(mesh.node_start_elements(), reps).astype(np.int32))
+    assert x.shape[0] > 3_000_000
+    want = ctx.track(mesh, x, u, c.dt, start=start, mode="asg", start_out=True)
+    got = ctx.track_noalloc(mesh, x, u, c.dt, start=start, mode="asg", start_out=True)
+    torch.cuda.synchronize()
+    for k in ("host", "path_len", "status", "start"):
+        assert torch.equal(got[k], want[k]), k
+    # the repeats are the same particles: every copy has the first one's result
+    h = got["host"].cpu().numpy().reshape(reps, -1)
+    assert (h == h[0]).all()
     mesh.release()
