@@ -92,6 +92,16 @@ def ncu_traffic(profile, sources):
         return None
 
 
+def nvtx_push(name):
+    """Open an NVTX range if this PyTorch build has NVTX; True if opened."""
+    import torch
+    try:
+        torch.cuda.nvtx.range_push(name)
+        return True
+    except (AttributeError, RuntimeError):
+        return False
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -388,12 +398,17 @@ def main():
         l0 = ctx.launches
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)]
+        # an NVTX range names the timed steps, so that a profiler can select
+        # them (ncu --nvtx --nvtx-include "timed_cnn/")
+        marked = nvtx_push("timed_" + mode)
         for i in range(steps):
             flush.fill_(i & 0xff)
             ev[i][0].record(stream)
             step(mode)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
+        if marked:
+            torch.cuda.nvtx.range_pop()
         total = sum(a.elapsed_time(b) for a, b in ev)
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)

@@ -77,7 +77,7 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
             const int64_t c0 = grid_cell_cert<D>(x0, h0, l0, m, m.psa, m.pinv_sa, m.pga);
             #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const double dh = double(__ldg(a.dhat + c0 * D + k));
+                const double dh = widen_float(__ldg(a.dhat + c0 * D + k));
                 y[k] = __dadd_rn(x0[k], __dmul_rn(dh, m.psa[k]));
                 split_double(y[k], yh[k], yl[k]);
             }

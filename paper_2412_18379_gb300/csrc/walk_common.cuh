@@ -141,46 +141,84 @@ __device__ __forceinline__ void bary32(const WalkE<D> &e, const float *xh, const
     T[0] = sumT + fmaf(k8U, 1.0f + suml, kTiny);
 }
 
+// The two 32-bit halves of a double's bit pattern. Through inline PTX so
+// that the compiler cannot fold the integer tests below back into FP64
+// comparisons: on GB300 every FP64 instruction, compares and conversions
+// included, occupies the FP64 pipe for about 56 cycles per warp, while these
+// integer tests cost a few cycles each.
+__device__ __forceinline__ void dbits(double x, uint32_t &lo, uint32_t &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+}
+
 // x = hi + lo + r with hi = x truncated to 24 significant bits, lo = the
 // remainder truncated to float, |r| <= 2^-44 |hi|, from the bit pattern of x
 // (integer pipe only). Zero gives (0, 0); exponents outside [-74, 127] give
 // hi = NaN, which no filter test certifies (those steps use FP64).
 __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    if ((b << 1) == 0) {
+    uint32_t bl, bh;
+    dbits(x, bl, bh);
+    if (((bh << 1) | bl) == 0) {
         hi = 0.f;
         lo = 0.f;
         return;
     }
-    const int E = int((b >> 52) & 0x7ff) - 1023;
+    const int E = int((bh >> 20) & 0x7ffu) - 1023;
     if (E < -74 || E > 127) {
         hi = __int_as_float(0x7fc00000);
         lo = 0.f;
         return;
     }
-    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
-    hi = __uint_as_float(sign | (unsigned(E + 127) << 23) | unsigned((b >> 29) & 0x7fffffu));
-    const float low = __uint2float_rz(unsigned(b & 0x1fffffffu));
+    const unsigned sign = bh & 0x80000000u;
+    // the 23 fraction bits below the leading one: bh[19:0] and bl[31:29]
+    hi = __uint_as_float(sign | (unsigned(E + 127) << 23) | (((bh << 3) | (bl >> 29)) & 0x7fffffu));
+    const float low = __uint2float_rz(bl & 0x1fffffffu);
     lo = __fmul_rn(sign ? -low : low, __uint_as_float(unsigned(E + 75) << 23));
 }
 
 // x truncated to float from its bit pattern (integer pipe only); magnitudes
 // below 2^-126 become 0, above the float range +-inf, NaN stays NaN.
 __device__ __forceinline__ float trunc_to_float(double x) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned sign = unsigned(b >> 32) & 0x80000000u;
-    const int E = int((b >> 52) & 0x7ff) - 1023;
+    uint32_t bl, bh;
+    dbits(x, bl, bh);
+    const unsigned sign = bh & 0x80000000u;
+    const int E = int((bh >> 20) & 0x7ffu) - 1023;
     if (E < -126) return __uint_as_float(sign);
     if (E > 127) {
-        const bool nan = E == 1024 && (b & 0xfffffffffffffull) != 0;
+        const bool nan = E == 1024 && ((bh & 0xfffffu) | bl) != 0;
         return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
     }
-    return __uint_as_float(sign | (unsigned(E + 127) << 23) | unsigned((b >> 29) & 0x7fffffu));
+    return __uint_as_float(sign | (unsigned(E + 127) << 23) | (((bh << 3) | (bl >> 29)) & 0x7fffffu));
 }
 
 __device__ __forceinline__ bool finite_bits(double x) {
-    return (static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7ff0000000000000ull) !=
-           0x7ff0000000000000ull;
+    uint32_t bl, bh;
+    dbits(x, bl, bh);
+    return (bh & 0x7ff00000u) != 0x7ff00000u;
+}
+
+// The double equal to f (exact), built from f's bit pattern on the integer
+// pipe instead of an FP64-pipe conversion. NaN gives a quiet NaN.
+__device__ __forceinline__ double widen_float(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    uint32_t hi, lo;
+    if (e == 0xffu) {                       // inf, NaN
+        hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u) | (m >> 3);
+        lo = m << 29;
+    } else if (e != 0u) {                   // normal: rebias 127 -> 1023
+        hi = sign | ((e + 896u) << 20) | (m >> 3);
+        lo = m << 29;
+    } else if (m == 0u) {                   // +-0
+        hi = sign;
+        lo = 0u;
+    } else {                                // subnormal: m * 2^-149, leading one at bit t
+        const int t = 31 - __clz(int(m));
+        const unsigned long long frac =
+            (static_cast<unsigned long long>(m) << (52 - t)) & 0xfffffffffffffull;
+        hi = sign | (unsigned(t + 874) << 20) | unsigned(frac >> 32);
+        lo = unsigned(frac);
+    }
+    return __hiloint2double(int(hi), int(lo));
 }
 
 // Cell index of one axis, FP64: floor((x - lo) / s) clamped, NaN -> 0.
@@ -215,10 +253,13 @@ __device__ __forceinline__ int64_t grid_cell_cert(const double *x, const float *
         const float ed = delta_bound(df, xh[k], m.lo_h[k]);
         const float q = df * inv_s[k];
         const float B = fmaf(2.0f * ed, inv_s[k], fmaf(k8U, fabsf(q), kTiny));
-        const float a = floorf(q - B), b = floorf(q + B);
+        // floor of both ends in int32 (the XU pipe; a float -> int64
+        // conversion would take the FP64 pipe); equal ends with |q| < 4e6
+        // are in range, and NaN or out-of-range ends never pass the test
+        const int a = __float2int_rd(q - B), b = __float2int_rd(q + B);
         int64_t i;
         if (a == b && fabsf(q) < 4.0e6f) {
-            i = a < 0.f ? 0 : (a > float(g[k] - 1) ? g[k] - 1 : int64_t(a));
+            i = a < 0 ? 0 : (a > g[k] - 1 ? g[k] - 1 : a);
         } else {
             i = cell_axis64(x[k], m.lo[k], s[k], g[k]);
         }
@@ -237,8 +278,10 @@ __device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh,
 // Monotone integer key of a non-NaN double: a < b <=> key(a) < key(b), with
 // +0 and -0 equal (exact comparisons on the integer pipe).
 __device__ __forceinline__ unsigned long long order_key(double x) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    if ((b << 1) == 0) return 0x8000000000000000ull;
+    uint32_t bl, bh;
+    dbits(x, bl, bh);
+    if (((bh << 1) | bl) == 0) return 0x8000000000000000ull;
+    const unsigned long long b = (static_cast<unsigned long long>(bh) << 32) | bl;
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 

@@ -164,6 +164,37 @@ def test_track_with_given_displacements(ctx, name, kw):
         assert np.array_equal(got[k], ref), k
 
 
+def test_track_with_special_displacements(ctx):
+    """The CNN start with displacements that are not ordinary numbers: signed
+    zeros, float subnormals, values near the float range, infinities and NaN
+    (a diverged predictor). x + dhat * s then lies on x, next to it, far
+    outside the box (clamped to the boundary cells) or is NaN (cell 0); the
+    walk from there must still end in the exact host. Starts, paths, hosts and
+    statuses bit for bit."""
+    import torch
+    c = make_case("tg2d", n_side=61, cfl=8)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    rng = np.random.default_rng(8)
+    dhat = rng.uniform(-4, 4, size=(int(np.prod(g)), c.dim)).astype(np.float32)
+    special = np.array([0.0, -0.0, 1e-40, -1.4e-45, 5.9e-39, -1.17e-38, 3.0e38, -3.3e38,
+                        np.inf, -np.inf, np.nan, 1.0, -0.5], dtype=np.float32)
+    pick = rng.integers(0, special.size, size=dhat.shape)
+    mask = rng.random(dhat.shape) < 0.5
+    dhat[mask] = special[pick[mask]]
+    out = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=_dev(dhat), start_out=True)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    with np.errstate(invalid="ignore", over="ignore"):
+        want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.cells(c.x)])
+    start = np.where(want["path_len"] > 0, want["start"], -1)
+    for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
+                   ("status", want["status"]), ("start", start)):
+        assert np.array_equal(got[k], ref), k
+    mesh.release()
+
+
 def _oracle_cnn_dhat(om, case, flat):
     """Oracle of the predictor stage: FP64 grid velocity, windows at the
     particles' cells, FP64 forward."""
