@@ -214,6 +214,12 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double
  * reference the grid engines are tested against). */
 cs_status cs_predictor_engine(cs_ctx *ctx, int engine);
 
+/* Output rows per tile of the 2-D tensor-core grid kernel: 24, 13 or 8, or
+ * 0 (default) for the height whose tiles best fill the GPU's SMs (fewest
+ * waves of one tile per SM, weighted by each height's pipeline length).
+ * Results do not depend on it. CS_EINVAL for any other value. */
+cs_status cs_predictor_tile_rows(cs_ctx *ctx, int rows);
+
 /* Synchronise the device and report whether a bounded device-side wait gave
  * up since the last call (CS_EDEVICE, message in cs_last_error) or CS_OK. */
 cs_status cs_device_status(cs_ctx *ctx);

@@ -206,6 +206,11 @@ class Context:
         own window through CUDA-core GEMMs."""
         self._check(self.lib.cs_predictor_engine(self.h, 1 if engine in ("tc", "grid") else 0))
 
+    def predictor_tile_rows(self, rows=0):
+        """Tile height of the 2-D tensor-core grid kernel: 24, 13 or 8 rows,
+        or 0 for the automatic choice."""
+        self._check(self.lib.cs_predictor_tile_rows(self.h, int(rows)))
+
     def device_status(self):
         self._check(self.lib.cs_device_status(self.h))
 

@@ -63,8 +63,11 @@ int launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float l
 // tensor-core grid inference of the 2-D predictor (cnn_tc.cu)
 int64_t tc_packed_bytes();
 int launch_pack_tc(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
+// tile_rows: output rows per tile (24, 13 or 8), 0 = tc_pick_tile_rows
 int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, cudaStream_t st);
+                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st);
+// the tile height with the least estimated cost on a grid (24, 13 or 8)
+int tc_pick_tile_rows(const DevMesh &m, int sm_count);
 int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, double dt,
                  int64_t *cells, float *target, int sm_count, cudaStream_t st);
 int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,

@@ -5,9 +5,11 @@
 // cells overlap, so the network is evaluated for all cells at once: with
 // valid convolutions, the window result at cell c equals a fully
 // convolutional pass over the zero-padded grid, read at c. One persistent CTA
-// per SM walks over 24 x 24-cell output tiles:
+// per SM walks over output tiles of 24 columns x TH rows (TH = 24, 13 or 8:
+// the host picks the height whose tiles fill the SMs best, e.g. 13 rows for
+// 144 tiles on a 200 x 200 grid):
 //
-//   input   32 x 32 cells (tile + 4-cell halo), channels u_k dt / s_k, BF16,
+//   input   32 x (TH + 8) cells (tile + 4-cell halo), channels u_k dt / s_k, BF16,
 //           tap-packed: row r holds both channels of taps 0..7 at pixel r
 //   conv1   tcgen05.mma kind::f16, M = 128 pixels, N = 32: one K = 16 step
 //           for taps 0..7, one for tap 8 (a shifted read of the same rows)
@@ -27,8 +29,9 @@
 // its operands from shared memory (about 4 KiB of A per step), not by the
 // tensor cores' arithmetic.
 //
-// Pipeline. A tile is a sequence of 38 items (layer, M-tile): conv1 8, conv2
-// 7, conv3 7, conv4 6, fc1 5 x 2 column halves. Warp 16 issues the conv MMAs
+// Pipeline. A tile is a sequence of items (layer, M-tile); with TH = 24 there
+// are 38: conv1 8, conv2 7, conv3 7, conv4 6, fc1 5 x 2 column halves (TH =
+// 13: 5, 5, 4, 4, 3 x 2). Warp 16 issues the conv MMAs
 // and warp 18 the fc1 MMAs, each committing an item's MMAs to the item's
 // "mma" mbarrier. The 16 epilogue warps form 4 groups (one warp per TMEM lane
 // quarter): groups 0-1 take the conv items, groups 2-3 the fc1 items; a group
@@ -59,9 +62,8 @@
 namespace cs {
 namespace {
 
-constexpr int kTile = 24;            // output cells per tile edge
-constexpr int kW = 32;               // flat row width (= tile + 8)
-constexpr int kRows = 1024;          // pixel rows of the activation buffer
+constexpr int kTileW = 24;           // output cells per tile row
+constexpr int kW = 32;               // flat row width (= tile width + 8)
 constexpr int kEpiWarps = 16;        // 4 groups x 4 TMEM lane quarters
 constexpr int kConvWarp = 16;        // issues the MMAs of conv1..conv4
 constexpr int kLoadWarp = 17;        // loads the tile inputs
@@ -72,18 +74,6 @@ static_assert(kEpiWarps == kConvWarp && kLoadWarp == kConvWarp + 1 && kFcWarp ==
                   kSchedWarp == kConvWarp + 3,
               "warp roles");
 constexpr uint32_t kTmemCols = 512;
-
-// the items of one tile
-constexpr int kItems = 38;
-constexpr int kFcTiles = 5;                  // 576 compacted pixels
-
-// first item of conv1..conv4 (l = 0..3) and fc1 (l = 4)
-__host__ __device__ constexpr int jbase(int l) {
-    return l == 0 ? 0 : l == 1 ? 8 : l == 2 ? 15 : l == 3 ? 22 : 28;
-}
-// M-tiles of conv1..conv4: 32, 28, 26, 24 pixel rows of 32
-__host__ __device__ constexpr int nmt(int l) { return l == 0 ? 8 : l == 3 ? 6 : 7; }
-static_assert(jbase(4) + 2 * kFcTiles == kItems, "item count");
 
 // packed weights (bytes); produced by pack_weights_kernel
 struct TcLayout {
@@ -100,37 +90,84 @@ struct TcLayout {
     static constexpr int total = ((fc2b + 2 * 4) + 127) / 128 * 128;
 };
 
-// shared memory map (bytes)
-constexpr int kRowsX0 = 1096;                               // conv1 rows 0..1023 + tap-8 shift 66
-constexpr int kX0Bytes = 2 * kRowsX0 * 16;                  // bf16 [2][1096][8] tap-packed input
-constexpr int kRowsFc = kTile * kTile;                      // compacted conv4 output rows (576)
-constexpr int kSmX0 = 0;                                    // input buffer
-constexpr int kSmAct = kSmX0 + kX0Bytes;                    // bf16 [4][1024][8] conv1..conv3
-constexpr int kSmFc = kSmAct + 4 * kRows * 16;              // bf16 [4][576][8] conv4 -> fc1
+// Geometry of a tile of kTileW x TH output cells. The input is TH + 8 rows
+// of 32 cells (a 4-cell halo); conv1..conv4 produce TH + 6, + 4, + 2 and TH
+// valid rows, each computed in M-tiles of 128 flat pixels (4 rows of 32).
+// A tall tile (TH = 24) wastes the least on halos; shorter ones give more
+// tiles, so that small grids still occupy every SM (the host picks TH).
+template <int TH>
+struct Geo {
+    static_assert(TH >= 4 && TH <= 26, "tile height");
+    static constexpr int kInRows = TH + 8;
+    // M-tiles of conv layer l = 0..3
+    __host__ __device__ static constexpr int nmt(int l) { return (TH + 6 - 2 * l + 3) / 4; }
+    // first item of conv1..conv4 (l = 0..3) and fc1 (l = 4)
+    __host__ __device__ static constexpr int jbase(int l) { return l == 0 ? 0 : jbase(l - 1) + nmt(l - 1); }
+    static constexpr int kRowsFc = kTileW * TH;           // compacted conv4 output rows
+    static constexpr int kFcTiles = (kRowsFc + 127) / 128;
+    static constexpr int kItems = jbase(4) + 2 * kFcTiles;
+    static constexpr int kRows = 128 * nmt(0);            // rows per chunk of the conv buffer
+    // conv1 reads 128 nmt(0) rows plus the tap-8 shift of 66
+    static constexpr int kRowsX0 = (128 * nmt(0) + 2 * kW + 2 + 7) / 8 * 8;
+    static constexpr int kWinRows = kInRows + 6;          // window rows + zero rows
+    // conv layer whose M-tile mt is the last in a tile to use the TMEM
+    // columns [32 mt, +32): the next tile's conv1 M-tile mt waits for it
+    __host__ __device__ static constexpr int last_user(int mt) {
+        return nmt(3) > mt ? 3 : nmt(2) > mt ? 2 : nmt(1) > mt ? 1 : 0;
+    }
+    // conv4 M-tiles whose compacted rows [96 m, 96 m + 96) feed fc1 M-tile f,
+    // i.e. rows [128 f, 128 f + 128): m in [fc_lo(f), fc_hi(f)]
+    __host__ __device__ static constexpr int fc_lo(int f) { return (128 * f) / 96; }
+    __host__ __device__ static constexpr int fc_hi(int f) {
+        return (128 * f + 127) / 96 < nmt(3) - 1 ? (128 * f + 127) / 96 : nmt(3) - 1;
+    }
 
-constexpr int kSmW = kSmFc + 4 * kRowsFc * 16;              // packed weights
-constexpr int kSmRed = kSmW + TcLayout::total;              // float2 [2][5][128] fc2 partials
-constexpr int kSmBar = kSmRed + 2 * kFcTiles * 128 * 8;
-constexpr int kBarMma = 0;                                  // [2][kItems]
-constexpr int kBarEmpty = 2 * kItems;                       // input buffer consumed by conv1
-constexpr int kBarFinal = kBarEmpty + 1;                    // [2] each issuing warp's last MMAs
-constexpr int kNumBars = kBarFinal + 2;
-constexpr int kWinRows = kW + 6;                            // window rows + zero rows
-constexpr int kSmWin = kSmBar + kNumBars * 8;               // u32 [38][32] input window (BF16 x2)
-constexpr int kSmCnt = kSmWin + kWinRows * kW * 4;          // u32 [kItems + 7] counters
-constexpr int kCntX0 = kItems;                              // counter: tile inputs loaded
-constexpr int kCntT4 = kItems + 1;                          // [6] conv4 M-tile read out of TMEM
-constexpr int kNumCnt = kCntT4 + 6;
-constexpr int kSmSlot = kSmCnt + kNumCnt * 4;               // TMEM address, abort flag
-constexpr int kSmTotal = kSmSlot + 16;
-static_assert(kSmTotal <= 232448, "shared memory of one CTA");
-// fc1 M-tile 4 reads rows 512..639 of each chunk: past row 575 it reads the
-// next chunk (or, for the last chunk, the weights that follow), garbage rows
-// whose outputs are dropped
-static_assert(kSmFc + (3 * kRowsFc + 128 * kFcTiles) * 16 <= kSmTotal, "fc1 reads in bounds");
-static_assert(kRowsX0 >= 128 * 8 + 2 * kW + 2, "conv1 reads in bounds");
-static_assert(kRowsX0 - 1 + 2 * kW + 1 < kWinRows * kW, "window reads in bounds");
-static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+    // shared memory map (bytes)
+    static constexpr int kX0Bytes = 2 * kRowsX0 * 16;     // bf16 [2][kRowsX0][8] tap-packed input
+    static constexpr int kSmX0 = 0;                       // input buffer
+    static constexpr int kSmAct = kSmX0 + kX0Bytes;       // bf16 [4][kRows][8] conv1..conv3
+    static constexpr int kSmFc = kSmAct + 4 * kRows * 16; // bf16 [4][kRowsFc][8] conv4 -> fc1
+    static constexpr int kSmW = kSmFc + 4 * kRowsFc * 16; // packed weights
+    static constexpr int kSmRed = kSmW + TcLayout::total; // float2 [2][kFcTiles][128] fc2 partials
+    static constexpr int kSmBar = kSmRed + 2 * kFcTiles * 128 * 8;
+    static constexpr int kBarMma = 0;                     // [2][kItems]
+    static constexpr int kBarEmpty = 2 * kItems;          // input buffer consumed by conv1
+    static constexpr int kBarFinal = kBarEmpty + 1;       // [2] each issuing warp's last MMAs
+    static constexpr int kNumBars = kBarFinal + 2;
+    static constexpr int kSmWin = kSmBar + kNumBars * 8;  // u32 [kWinRows][32] input window
+    static constexpr int kSmCnt = kSmWin + kWinRows * kW * 4;   // u32 counters
+    static constexpr int kCntX0 = kItems;                 // counter: tile inputs loaded
+    static constexpr int kCntT4 = kItems + 1;             // [nmt(3)] conv4 M-tile read out of TMEM
+    static constexpr int kNumCnt = kCntT4 + nmt(3);
+    static constexpr int kSmSlot = kSmCnt + kNumCnt * 4;  // TMEM address, abort flag
+    static constexpr int kSmTotal = kSmSlot + 16;
+
+    static_assert(kSmTotal <= 232448, "shared memory of one CTA");
+    static_assert(32 * nmt(0) <= 256, "conv layers fit TMEM columns [0, 256)");
+    static_assert(nmt(0) - nmt(1) <= 1 && nmt(1) - nmt(2) <= 1 && nmt(2) - nmt(3) <= 1,
+                  "each conv M-tile depends on M-tiles mt and mt + 1 of the layer before");
+    // fc1 M-tile f reads rows [128 f, +128) of each chunk: past kRowsFc it reads
+    // the next chunk (or, for the last chunk, the weights that follow), garbage
+    // rows whose outputs are dropped
+    static_assert(kSmFc + (3 * kRowsFc + 128 * kFcTiles) * 16 <= kSmTotal, "fc1 reads in bounds");
+    // conv2..conv4 M-tile mt reads rows up to 128 mt + 127 + 66 of each chunk
+    static_assert(kSmAct + (3 * kRows + 128 * nmt(1) + 2 * kW + 2) * 16 <= kSmTotal,
+                  "conv reads in bounds");
+    static_assert(kRowsX0 >= 128 * nmt(0) + 2 * kW + 2, "conv1 reads in bounds");
+    static_assert(kRowsX0 - 1 + 2 * kW + 1 < kWinRows * kW, "window reads in bounds");
+    static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+    static_assert(96 * nmt(3) <= 128 * kFcTiles + 96, "conv4 M-tiles map onto fc1 M-tiles");
+
+    static __device__ __forceinline__ void item_decode(int j, int &l, int &m) {
+        l = j < jbase(1) ? 0 : j < jbase(2) ? 1 : j < jbase(3) ? 2 : j < jbase(4) ? 3 : 4;
+        m = j - jbase(l);
+    }
+};
+static_assert(Geo<24>::kItems == 38 && Geo<24>::jbase(4) == 28 && Geo<24>::kFcTiles == 5,
+              "24-row tile: 38 items");
+static_assert(Geo<24>::last_user(5) == 3 && Geo<24>::last_user(6) == 2 &&
+                  Geo<24>::last_user(7) == 0,
+              "24-row tile: TMEM column reuse");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -328,20 +365,9 @@ __device__ __forceinline__ uint32_t item_col(int l, int m) {
     return l < 4 ? uint32_t(32 * m) : uint32_t(256 + 128 * (m & 1));
 }
 
-// conv4 M-tiles whose compacted rows [96 m, 96 m + 96) feed fc1 M-tile f,
-// i.e. rows [128 f, 128 f + 128): m in [fc_lo(f), fc_hi(f)]
-__host__ __device__ constexpr int fc_lo(int f) { return (128 * f) / 96; }
-__host__ __device__ constexpr int fc_hi(int f) {
-    return (128 * f + 127) / 96 < 5 ? (128 * f + 127) / 96 : 5;
-}
-
-__device__ __forceinline__ void item_decode(int j, int &l, int &m) {
-    l = j < jbase(1) ? 0 : j < jbase(2) ? 1 : j < jbase(3) ? 2 : j < jbase(4) ? 3 : 4;
-    m = j - jbase(l);
-}
-
 // MMAs of M-tile m of conv layer l (l >= 1): 9 taps x 2 K-steps, accumulate
-// into TMEM columns [col, col + 32).
+// into TMEM columns [col, col + 32). kRows: rows per chunk of the conv buffer.
+template <int kRows>
 __device__ __forceinline__ void issue_conv(uint32_t dcol, uint64_t adesc, uint64_t bdesc, int m) {
     constexpr uint32_t id = idesc_bf16(128, 32);
     #pragma unroll
@@ -370,7 +396,8 @@ __device__ __forceinline__ void issue_conv1(uint32_t dcol, uint64_t adesc, uint6
 }
 
 // MMAs of column half h of fc1 M-tile f: 128 compacted pixels x 128 features,
-// K = 32 in two steps.
+// K = 32 in two steps. kRowsFc: rows per chunk of the fc1 input.
+template <int kRowsFc>
 __device__ __forceinline__ void issue_fc1(uint32_t dcol, uint64_t adesc, uint64_t bdesc, int f,
                                           int h) {
     constexpr uint32_t id = idesc_bf16(128, 128);
@@ -380,37 +407,39 @@ __device__ __forceinline__ void issue_fc1(uint32_t dcol, uint64_t adesc, uint64_
                  bdesc + uint64_t(2 * kk * 256 + 128 * h), id, uint32_t(kk));
 }
 
+template <int TH>
 __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const DevMesh m, const float *__restrict__ U, float scale0, float scale1,
     const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err) {
+    using G = Geo<TH>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *x0 = smem + kSmX0;
-    uint8_t *act = smem + kSmAct;
-    uint8_t *fcin = smem + kSmFc;
-    uint8_t *wsm = smem + kSmW;
-    float2 *red = reinterpret_cast<float2 *>(smem + kSmRed);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kSmBar);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmSlot);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kSmSlot + 4);
+    uint8_t *x0 = smem + G::kSmX0;
+    uint8_t *act = smem + G::kSmAct;
+    uint8_t *fcin = smem + G::kSmFc;
+    uint8_t *wsm = smem + G::kSmW;
+    float2 *red = reinterpret_cast<float2 *>(smem + G::kSmRed);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::kSmBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + G::kSmSlot);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + G::kSmSlot + 4);
     // epi_cnt[j] counts the epilogues of item j finished over this CTA's tiles,
     // 4 per tile (one per lane-quarter warp): item j of local tile k is done
     // once epi_cnt[j] >= 4 (k + 1)
-    uint32_t *epi_cnt = reinterpret_cast<uint32_t *>(smem + kSmCnt);
+    uint32_t *epi_cnt = reinterpret_cast<uint32_t *>(smem + G::kSmCnt);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int gx = m.ga[0], gy = m.ga[1];
-    const int tiles_x = (gx + kTile - 1) / kTile, tiles_y = (gy + kTile - 1) / kTile;
+    const int tiles_x = (gx + kTileW - 1) / kTileW, tiles_y = (gy + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y;
 
     // weights into shared memory (once per CTA), zeroed buffers, barriers
     for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(wsm)[i] = reinterpret_cast<const uint4 *>(packed)[i];
-    for (int i = tid; i < kSmW / 16; i += kThreadsTC)
+    for (int i = tid; i < G::kSmW / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < kWinRows * kW; i += kThreadsTC)
-        reinterpret_cast<uint32_t *>(smem + kSmWin)[i] = 0u;
+    for (int i = tid; i < G::kWinRows * kW; i += kThreadsTC)
+        reinterpret_cast<uint32_t *>(smem + G::kSmWin)[i] = 0u;
     if (tid == 0) {
-        for (int i = 0; i < kNumBars; ++i) mbar_init(bars + i, 1u);
-        for (int i = 0; i < kNumCnt; ++i) epi_cnt[i] = 0;
+        for (int i = 0; i < G::kNumBars; ++i) mbar_init(bars + i, 1u);
+        for (int i = 0; i < G::kNumCnt; ++i) epi_cnt[i] = 0;
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -425,23 +454,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
-    uint64_t *bar_mma = bars + kBarMma;
+    uint64_t *bar_mma = bars + G::kBarMma;
 
     if (warp == kLoadWarp) {
-        // ---- inputs: 32 x 32 cells, channels u_k dt / s_k (BF16), zero outside.
+        // ---- inputs: 32 x (TH + 8) cells, channels u_k dt / s_k (BF16), zero outside.
         //      One buffer: tile k + 1 is loaded while conv2..conv4 of tile k run ----
         for (int k = 0;; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
             if (k >= 1 &&
-                !warp_wait(bars + kBarEmpty, uint32_t(k - 1) & 1u, abort_flag, err))
+                !warp_wait(bars + G::kBarEmpty, uint32_t(k - 1) & 1u, abort_flag, err))
                 break;
             const int tx = tile % tiles_x, ty = tile / tiles_x;
-            const int cx0 = tx * kTile - 4, cy0 = ty * kTile - 4;
-            // the 32 x 32 window, scaled, as BF16 pairs; rows 32.. stay zero
-            uint32_t *win = reinterpret_cast<uint32_t *>(smem + kSmWin);
-            #pragma unroll 8
-            for (int y = 0; y < kW; ++y) {
+            const int cx0 = tx * kTileW - 4, cy0 = ty * TH - 4;
+            // the 32 x (TH + 8) window, scaled, as BF16 pairs; the rows past
+            // it stay zero
+            uint32_t *win = reinterpret_cast<uint32_t *>(smem + G::kSmWin);
+            #pragma unroll 4
+            for (int y = 0; y < G::kInRows; ++y) {
                 const int cx = cx0 + lane, cy = cy0 + y;
                 float2 uv = make_float2(0.f, 0.f);
                 if (cx >= 0 && cx < gx && cy >= 0 && cy < gy)
@@ -452,21 +482,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             // tap-packed rows: taps 0..7 of pixel r are pixels r + 32 dy + dx
             uint4 *xv = reinterpret_cast<uint4 *>(x0);
             #pragma unroll 2
-            for (int r = lane; r < kRowsX0; r += kW) {
+            for (int r = lane; r < G::kRowsX0; r += kW) {
                 const uint32_t *p = win + r;
                 xv[r] = make_uint4(p[0], p[1], p[2], p[kW]);
-                xv[kRowsX0 + r] = make_uint4(p[kW + 1], p[kW + 2], p[2 * kW], p[2 * kW + 1]);
+                xv[G::kRowsX0 + r] = make_uint4(p[kW + 1], p[kW + 2], p[2 * kW], p[2 * kW + 1]);
             }
             __syncwarp();
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) red_release_add(epi_cnt + kCntX0, 1u);
+            if (lane == 0) red_release_add(epi_cnt + G::kCntX0, 1u);
         }
     } else if (warp == kConvWarp) {
         // ---- conv MMAs: the whole warp runs the schedule (descriptors and
         //      waits stay warp-uniform), one elected lane issues ----
-        const uint64_t d_act = sdesc(smem_addr(act), kRows * 16, 128);
-        const uint64_t d_x0 = sdesc(smem_addr(x0), kRowsX0 * 16, 128);
+        const uint64_t d_act = sdesc(smem_addr(act), G::kRows * 16, 128);
+        const uint64_t d_x0 = sdesc(smem_addr(x0), G::kRowsX0 * 16, 128);
         const uint64_t d_w1 = sdesc(smem_addr(wsm + TcLayout::w1), 32 * 16, 128);
         const uint64_t d_wc = sdesc(smem_addr(wsm + TcLayout::bconv), 32 * 16, 128);
         const bool leader = elect_one();
@@ -477,97 +507,100 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         for (int k = 0; !stop; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
-            uint64_t *mma_s = bar_mma + (k & 1) * kItems;
-            for (int c = 0; c < jbase(4); ++c) {
+            uint64_t *mma_s = bar_mma + (k & 1) * G::kItems;
+            for (int c = 0; c < G::jbase(4); ++c) {
                 stop = handoff_or(false);
                 if (stop) break;
                 int l, mt;
-                item_decode(c, l, mt);
+                G::item_decode(c, l, mt);
                 fence_after();
                 if (leader) {
                     if (l == 0) {
                         issue_conv1(tmem + uint32_t(32 * mt), d_x0, d_w1, mt);
                     } else {
                         const uint64_t d_w = d_wc + uint64_t((l - 1) * (TcLayout::bconv_bytes / 16));
-                        issue_conv(tmem + uint32_t(32 * mt), d_act, d_w, mt);
+                        issue_conv<G::kRows>(tmem + uint32_t(32 * mt), d_act, d_w, mt);
                     }
                     mma_commit(mma_s + c);
-                    if (c == nmt(0) - 1) mma_commit(bars + kBarEmpty);   // input buffer free again
+                    if (c == G::nmt(0) - 1) mma_commit(bars + G::kBarEmpty);   // input buffer free again
                 }
                 __syncwarp();
             }
         }
         // wait (bounded) for this warp's MMAs in flight before TMEM is released
         if (leader) {
-            mma_commit(bars + kBarFinal);
-            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + kBarFinal, 0); ++i)
+            mma_commit(bars + G::kBarFinal);
+            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + G::kBarFinal, 0); ++i)
                 if (i > 64) __nanosleep(64);
         }
         __syncwarp();
     } else if (warp == kFcWarp) {
         // ---- fc1 MMAs, half h of M-tile f into columns [256 + 128 h, +128): they
         //      run while the next tile's convolutions use columns [0, 256) ----
-        const uint64_t d_fc = sdesc(smem_addr(fcin), kRowsFc * 16, 128);
+        const uint64_t d_fc = sdesc(smem_addr(fcin), G::kRowsFc * 16, 128);
         const uint64_t d_fc1 = sdesc(smem_addr(wsm + TcLayout::bfc1), 256 * 16, 128);
         const bool leader = elect_one();
         bool ok = true;
         for (int k = 0; ok; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
-            uint64_t *mma_s = bar_mma + (k & 1) * kItems;
+            uint64_t *mma_s = bar_mma + (k & 1) * G::kItems;
             const uint32_t done = 4u * uint32_t(k + 1);
             const uint32_t done_p = 4u * uint32_t(k);
-            for (int f = 0; f < kFcTiles && ok; ++f) {
+            for (int f = 0; f < G::kFcTiles && ok; ++f) {
                 for (int h = 0; h < 2 && ok; ++h) {
                     // input: the conv4 M-tiles that wrote compacted rows [128 f, +128)
-                    for (int q = fc_lo(f); q <= fc_hi(f) && ok && h == 0; ++q)
-                        ok = wait_count(epi_cnt + jbase(3) + q, done, abort_flag, err);
+                    for (int q = G::fc_lo(f); q <= G::fc_hi(f) && ok && h == 0; ++q)
+                        ok = wait_count(epi_cnt + G::jbase(3) + q, done, abort_flag, err);
                     // columns: last used by M-tile f - 1 (same half) or the previous tile's M-tile 4
                     if (ok && f > 0)
-                        ok = wait_count(epi_cnt + jbase(4) + 2 * (f - 1) + h, done, abort_flag, err);
+                        ok = wait_count(epi_cnt + G::jbase(4) + 2 * (f - 1) + h, done, abort_flag, err);
                     else if (ok && k > 0)
-                        ok = wait_count(epi_cnt + jbase(4) + 8 + h, done_p, abort_flag, err);
+                        ok = wait_count(epi_cnt + G::jbase(4) + 2 * (G::kFcTiles - 1) + h,
+                                        done_p, abort_flag, err);
                     if (!ok) break;
                     fence_after();
                     if (leader) {
-                        issue_fc1(tmem + item_col(4, h), d_fc, d_fc1, f, h);
-                        mma_commit(mma_s + jbase(4) + 2 * f + h);
+                        issue_fc1<G::kRowsFc>(tmem + item_col(4, h), d_fc, d_fc1, f, h);
+                        mma_commit(mma_s + G::jbase(4) + 2 * f + h);
                     }
                     __syncwarp();
                 }
             }
         }
         if (leader) {
-            mma_commit(bars + kBarFinal + 1);
-            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + kBarFinal + 1, 0); ++i)
+            mma_commit(bars + G::kBarFinal + 1);
+            for (uint32_t i = 0; i < (1u << 24) && !mbar_try_wait(bars + G::kBarFinal + 1, 0); ++i)
                 if (i > 64) __nanosleep(64);
         }
         __syncwarp();
     } else if (warp == kSchedWarp) {
         // ---- releases conv item c of tile k to the conv warp once its inputs
         //      are ready: conv1 M-tile mt needs the tile's input and its TMEM
-        //      columns back from the previous tile (conv4 for mt <= 5, conv3 for
-        //      mt = 6, conv1 for mt = 7); conv2..conv4 M-tile mt needs the
+        //      columns back from the previous tile (from the last layer that
+        //      has an M-tile mt: with 24-row tiles conv4 for mt <= 5, conv3
+        //      for mt = 6, conv1 for mt = 7); conv2..conv4 M-tile mt needs the
         //      previous layer's M-tiles mt and mt + 1 ----
         bool ok = true, stop = false;
         for (int k = 0; !stop; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
-            for (int c = 0; c < jbase(4); ++c) {
+            for (int c = 0; c < G::jbase(4); ++c) {
                 int l, mt;
-                item_decode(c, l, mt);
+                G::item_decode(c, l, mt);
                 if (ok && l == 0) {
                     if (k > 0) {
-                        const int jl = mt <= 5 ? kCntT4 + mt : mt == 6 ? jbase(2) + 6 : jbase(0) + 7;
+                        const int lu = G::last_user(mt);
+                        const int jl = lu == 3 ? G::kCntT4 + mt : G::jbase(lu) + mt;
                         ok = wait_count(epi_cnt + jl, 4u * uint32_t(k), abort_flag, err);
                     }
                     if (ok && mt == 0)
-                        ok = wait_count(epi_cnt + kCntX0, uint32_t(k + 1), abort_flag, err);
+                        ok = wait_count(epi_cnt + G::kCntX0, uint32_t(k + 1), abort_flag, err);
                 } else if (ok) {
                     const uint32_t done = 4u * uint32_t(k + 1);
-                    ok = wait_count(epi_cnt + jbase(l - 1) + mt, done, abort_flag, err);
-                    if (ok && mt + 1 < nmt(l - 1))
-                        ok = wait_count(epi_cnt + jbase(l - 1) + mt + 1, done, abort_flag, err);
+                    ok = wait_count(epi_cnt + G::jbase(l - 1) + mt, done, abort_flag, err);
+                    if (ok && mt + 1 < G::nmt(l - 1))
+                        ok = wait_count(epi_cnt + G::jbase(l - 1) + mt + 1, done, abort_flag, err);
                 }
                 stop = handoff_or(!ok || *abort_flag != 0);
                 if (stop) break;
@@ -578,7 +611,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         //      alternately, groups 2 and 3 the fc1 items, so a conv epilogue never
         //      queues behind the longer fc1 epilogues of the previous tile ----
         const int g = warp >> 2, q = warp & 3;
-        constexpr int kConvItems = jbase(4), kFcItems = kItems - jbase(4);
+        constexpr int kConvItems = G::jbase(4), kFcItems = G::kItems - G::jbase(4);
         const float *b1 = reinterpret_cast<const float *>(wsm + TcLayout::b1);
         const float *cb = reinterpret_cast<const float *>(wsm + TcLayout::cb);
         const float *fc1b = reinterpret_cast<const float *>(wsm + TcLayout::fc1b);
@@ -587,16 +620,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         const uint32_t tq = tmem + (uint32_t(32 * q) << 16);     // this warp's lane quarter
         for (int n = g & 1;; n += 2) {
             const int k = g < 2 ? n / kConvItems : n / kFcItems;
-            const int j = g < 2 ? n - k * kConvItems : jbase(4) + n - k * kFcItems;
+            const int j = g < 2 ? n - k * kConvItems : G::jbase(4) + n - k * kFcItems;
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
             const int s = k & 1;
             const uint32_t par = uint32_t(k >> 1) & 1u;
-            if (!__all_sync(kFull, mbar_wait(bar_mma + s * kItems + j, par, abort_flag, err)))
+            if (!__all_sync(kFull, mbar_wait(bar_mma + s * G::kItems + j, par, abort_flag, err)))
                 break;
             fence_after();
             int l, mt;
-            item_decode(j, l, mt);
+            G::item_decode(j, l, mt);
             if (l < 4) {
                 float v[32];
                 tmem_ld32(tq + item_col(l, mt), v);
@@ -604,24 +637,26 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                     // conv4's columns are free for the next tile's conv1 now
                     fence_before();
                     __syncwarp();
-                    if (lane == 0) red_release_add(epi_cnt + kCntT4 + mt, 1u);
+                    if (lane == 0) red_release_add(epi_cnt + G::kCntT4 + mt, 1u);
                 }
                 uint32_t hv[16];
                 bias_relu_bf16(v, l == 0 ? b1 : cb + 32 * (l - 1), hv);
                 const int row = 128 * mt + 32 * q + lane;
                 if (l < 3) {
-                    store_act<kRows>(act, row, hv);
+                    store_act<G::kRows>(act, row, hv);
                 } else {
-                    // conv4: pixel (y, x) -> compacted row 24 y + x of the fc1 input,
+                    // conv4: pixel (y, x) -> compacted row 24 y + x of the fc1 input
+                    // (rows y >= TH, columns x >= 24 are dropped),
                     // once the previous tile's fc1 M-tiles that read rows [96 mt, +96)
                     // are done (their epilogues end long before, so this is one load)
                     bool ok = true;
-                    for (int f = (96 * mt) / 128; f <= (96 * mt + 95) / 128 && ok && k > 0; ++f)
-                        ok = wait_count(epi_cnt + jbase(4) + 2 * f + 1, 4u * uint32_t(k), abort_flag,
+                    for (int f = (96 * mt) / 128;
+                         f <= (96 * mt + 95) / 128 && f < G::kFcTiles && ok && k > 0; ++f)
+                        ok = wait_count(epi_cnt + G::jbase(4) + 2 * f + 1, 4u * uint32_t(k), abort_flag,
                                         err);
                     if (!ok) break;
-                    if (row % kW < kTile && row / kW < kTile)
-                        store_act<kRowsFc>(fcin, (row / kW) * kTile + row % kW, hv);
+                    if (row % kW < kTileW && row / kW < TH)
+                        store_act<G::kRowsFc>(fcin, (row / kW) * kTileW + row % kW, hv);
                 }
             } else {
                 // fc1 half h of M-tile f: 128 features, their part of fc2. With the
@@ -652,7 +687,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                     }
                 }
                 const float o0 = (a0.x + a0.y) + (b0.x + b0.y), o1 = (a1.x + a1.y) + (b1v.x + b1v.y);
-                float2 *slot = red + (s * kFcTiles + f) * 128 + 32 * q + lane;
+                float2 *slot = red + (s * G::kFcTiles + f) * 128 + 32 * q + lane;
                 if (h == 0) {
                     *slot = make_float2(o0, o1);
                 } else {
@@ -660,10 +695,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                     if (!wait_count(epi_cnt + j - 1, 4u * uint32_t(k + 1), abort_flag, err)) break;
                     const float2 p = *slot;
                     const int row = 128 * f + 32 * q + lane;
-                    const int y = row / kTile, x = row % kTile;
+                    const int y = row / kTileW, x = row % kTileW;
                     const int tx = tile % tiles_x, ty = tile / tiles_x;
-                    const int cx = tx * kTile + x, cy = ty * kTile + y;
-                    if (row < kTile * kTile && cx < gx && cy < gy)
+                    const int cx = tx * kTileW + x, cy = ty * TH + y;
+                    if (row < G::kRowsFc && cx < gx && cy < gy)
                         reinterpret_cast<float2 *>(dhat)[int64_t(cy) * gx + cx] =
                             make_float2(p.x + o0, p.y + o1);
                 }
@@ -746,19 +781,52 @@ int launch_pack_tc(const float *w, const NetShape &S, uint8_t *packed, cudaStrea
     return 1;
 }
 
-int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, cudaStream_t st) {
+namespace {
+
+template <int TH>
+int tiles_of(const DevMesh &m) {
+    return ((m.ga[0] + kTileW - 1) / kTileW) * ((m.ga[1] + TH - 1) / TH);
+}
+
+// Relative cost of a grid pass with TH-row tiles: waves of one tile per SM,
+// each a pipeline of Geo<TH>::kItems items plus a fixed part (weights, TMEM,
+// first input) worth about 8 items.
+template <int TH>
+int64_t tile_cost(const DevMesh &m, int sm_count) {
+    const int64_t waves = (tiles_of<TH>(m) + sm_count - 1) / sm_count;
+    return waves * (Geo<TH>::kItems + 8);
+}
+
+template <int TH>
+int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *packed, float *dhat,
+                int *err, int sm_count, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(cnn2d_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kSmTotal);
+        cudaFuncSetAttribute(cnn2d_tc_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Geo<TH>::kSmTotal);
         attr = true;
     }
-    const int tiles = ((m.ga[0] + kTile - 1) / kTile) * ((m.ga[1] + kTile - 1) / kTile);
-    const int grid = std::min(tiles, sm_count);
-    cnn2d_tc_kernel<<<grid, kThreadsTC, kSmTotal, st>>>(
+    const int grid = std::min(tiles_of<TH>(m), sm_count);
+    cnn2d_tc_kernel<TH><<<grid, kThreadsTC, Geo<TH>::kSmTotal, st>>>(
         m, U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err);
     return 1;
+}
+
+}  // namespace
+
+int tc_pick_tile_rows(const DevMesh &m, int sm_count) {
+    const int64_t c24 = tile_cost<24>(m, sm_count), c13 = tile_cost<13>(m, sm_count),
+                  c8 = tile_cost<8>(m, sm_count);
+    if (c24 <= c13 && c24 <= c8) return 24;
+    return c13 <= c8 ? 13 : 8;
+}
+
+int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st) {
+    const int th = tile_rows ? tile_rows : tc_pick_tile_rows(m, sm_count);
+    if (th == 24) return launch_rows<24>(m, U, dt, packed, dhat, err, sm_count, st);
+    if (th == 13) return launch_rows<13>(m, U, dt, packed, dhat, err, sm_count, st);
+    return launch_rows<8>(m, U, dt, packed, dhat, err, sm_count, st);
 }
 
 }  // namespace cs

@@ -367,7 +367,7 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
             P->packed_dirty = false;
         }
         ctx->launches += launch_cnn2d_tc(pred_view(m->d), m->grid_u, dt, P->packed, dhat, ctx->dev_err,
-                                         ctx->sm_count, st);
+                                         ctx->sm_count, ctx->tc_tile_rows, st);
         return CS_OK;
     }
     if (m->d.dim == 3 && ctx->engine == 1) return predict_tiles(ctx, *P, m, dt, dhat, st);
@@ -416,6 +416,14 @@ extern "C" {
 cs_status cs_predictor_engine(cs_ctx *ctx, int engine) {
     if (!ctx || (engine != 0 && engine != 1)) return CS_EINVAL;
     ctx->engine = engine;
+    return CS_OK;
+}
+
+cs_status cs_predictor_tile_rows(cs_ctx *ctx, int rows) {
+    if (!ctx) return CS_EINVAL;
+    if (rows != 0 && rows != 8 && rows != 13 && rows != 24)
+        return fail(ctx, CS_EINVAL, "cs_predictor_tile_rows: rows must be 0, 8, 13 or 24");
+    ctx->tc_tile_rows = rows;
     return CS_OK;
 }
 

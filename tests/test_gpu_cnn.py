@@ -317,6 +317,56 @@ def test_tensor_core_grid_prediction(ctx, n_side):
     assert np.abs(tc[pick] - ref).max() <= 6e-2 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("n_side", [101, 301])
+def test_tensor_core_tile_heights_agree(ctx, n_side):
+    """The tcgen05 grid kernel with tiles of 24, 13 and 8 rows and with the
+    automatic choice: every cell gets the same bits whatever the height, since
+    a cell's arithmetic does not depend on where the tiles cut the grid. Each
+    height is also checked against the per-window engine on every cell and
+    against the FP64 oracle on the cells next to its own tile edges."""
+    import torch
+    c = make_case("tg2d", n_side=n_side, cfl=8)
+    flat = init_weights(2, 33)
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    g = mesh.info()["asg_grid"]
+    om = oracle.Mesh(c.xyz, c.conn, grid=g)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(g))
+    gx, gy = g
+    outs = {}
+    try:
+        for rows in (0, 24, 13, 8):
+            out = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+            ctx.predictor_tile_rows(rows)
+            ctx.predict(mesh, c.dt, out=out)
+            outs[rows] = out.cpu().numpy()
+        win = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+        ctx.predictor_engine("window")
+        ctx.predict(mesh, c.dt, out=win)
+    finally:
+        ctx.predictor_engine("tc")
+        ctx.predictor_tile_rows(0)
+    ctx.device_status()
+    win = win.cpu().numpy()
+    U = _oracle_grid_u(om, c.u)
+    s = (om.hi - om.lo) / om.grid
+    iy, ix = np.divmod(np.arange(n_cells), gx)
+    for rows in (24, 13, 8):
+        assert np.isfinite(outs[rows]).all(), rows
+        assert np.array_equal(outs[rows].view(np.uint32), outs[24].view(np.uint32)), rows
+        assert np.abs(outs[rows] - win).max() <= 4e-2 * np.abs(win).max(), rows
+        edge = (ix % 24 == 0) | (ix % 24 == 23) | (iy % rows == 0) | (iy % rows == rows - 1)
+        pick = np.nonzero(edge)[0][::7][:600]
+        ref = cnn.forward(2, cnn.unpack(2, flat),
+                          cnn.windows(U.reshape(gy, gx, 2), pick, 2, c.dt / s))
+        assert np.abs(outs[rows][pick] - ref).max() <= 6e-2 * np.abs(ref).max(), rows
+    assert np.array_equal(outs[0].view(np.uint32), outs[24].view(np.uint32))
+    with pytest.raises(Exception):
+        ctx.predictor_tile_rows(12)
+    mesh.release()
+
+
 # ---- the predictor grid: cells of 3^d ASG cells ----------------------------
 
 def _oracle_pred_u(om, u_nodal):
