@@ -59,6 +59,9 @@ cs_status ensure_scratch(cs_ctx *ctx) {
         if (cudaMalloc(&s.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
             cudaMalloc(&s.stats, 8 * sizeof(int64_t)) != cudaSuccess)
             return fail(ctx, CS_ENOMEM, "cudaMalloc of scratch counters failed");
+        // the walk cursors start at zero; each walk then zeroes the other one
+        if (cudaMemset(s.counters, 0, 16 * sizeof(int32_t)) != cudaSuccess)
+            return fail(ctx, CS_ECUDA, "cudaMemset of scratch counters failed");
     }
     return CS_OK;
 }

@@ -297,6 +297,22 @@ __device__ __forceinline__ bool elect_one() {
     return pred != 0;
 }
 
+// Asynchronous global -> shared copies (cp.async): a thread issues all of
+// its copies before waiting once, instead of one load latency per element.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+// 8 bytes, or 8 zero bytes when !valid (src is then not read)
+__device__ __forceinline__ void cp_async8_zfill(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 8u : 0u)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -430,9 +446,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const int tiles_x = (gx + kTileW - 1) / kTileW, tiles_y = (gy + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y;
 
-    // weights into shared memory (once per CTA), zeroed buffers, barriers
+    // weights into shared memory (once per CTA, asynchronous while the
+    // buffers are zeroed), zeroed buffers, barriers
     for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
-        reinterpret_cast<uint4 *>(wsm)[i] = reinterpret_cast<const uint4 *>(packed)[i];
+        cp_async16(wsm + 16 * i, packed + 16 * i);
     for (int i = tid; i < G::kSmW / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < G::kWinRows * kW; i += kThreadsTC)
@@ -449,6 +466,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    cp_async_wait_all();
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -467,15 +485,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                 break;
             const int tx = tile % tiles_x, ty = tile / tiles_x;
             const int cx0 = tx * kTileW - 4, cy0 = ty * TH - 4;
-            // the 32 x (TH + 8) window, scaled, as BF16 pairs; the rows past
-            // it stay zero
-            uint32_t *win = reinterpret_cast<uint32_t *>(smem + G::kSmWin);
-            #pragma unroll 4
+            // the 32 x (TH + 8) window of velocities, zero outside the grid, in
+            // one round of asynchronous copies staged in the input buffer (free
+            // until the tap-packed rows below overwrite it); then scaled, as
+            // BF16 pairs, into the window, whose rows past it stay zero
+            float2 *stage = reinterpret_cast<float2 *>(x0);
+            static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
+            const float2 *U2 = reinterpret_cast<const float2 *>(U);
             for (int y = 0; y < G::kInRows; ++y) {
                 const int cx = cx0 + lane, cy = cy0 + y;
-                float2 uv = make_float2(0.f, 0.f);
-                if (cx >= 0 && cx < gx && cy >= 0 && cy < gy)
-                    uv = __ldg(reinterpret_cast<const float2 *>(U) + int64_t(cy) * gx + cx);
+                const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
+                cp_async8_zfill(stage + y * kW + lane, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+            }
+            cp_async_wait_all();
+            uint32_t *win = reinterpret_cast<uint32_t *>(smem + G::kSmWin);
+            for (int y = 0; y < G::kInRows; ++y) {
+                const float2 uv = stage[y * kW + lane];
                 win[y * kW + lane] = pack_bf16x2(uv.x * scale0, uv.y * scale1);
             }
             __syncwarp();

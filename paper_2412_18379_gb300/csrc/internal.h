@@ -139,7 +139,8 @@ struct Predictor {
 
 // Device scratch owned by a context.
 struct Scratch {
-    int32_t *counters = nullptr;   // [0] work cursor of the walk (16 reserved)
+    int32_t *counters = nullptr;   // [0], [1] work cursors of alternate walks (16 reserved)
+    int parity = 0;                // cursor of the next walk; that walk zeroes the other
     int64_t *stats = nullptr;      // [8]
     char *stage = nullptr;         // device staging of cs_track_host
     size_t stage_cap = 0;
@@ -213,7 +214,7 @@ struct Profiler {
 };
 
 // kernel launchers (walk.cu); each returns the number of kernels launched
-int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
+int launch_track(const DevMesh &m, const TrackArgs &a, Scratch &s, int sm_count,
                  cudaStream_t st, Profiler *prof = nullptr);
 int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st);
 int launch_stats(int64_t n, const int32_t *path, const uint8_t *status, int64_t *out,

@@ -84,7 +84,8 @@ struct Request {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    int32_t *counters = nullptr;
+    int32_t *counters = nullptr;   // walk cursors, see Scratch
+    int parity = 0;
     Request *req = nullptr;
 };
 
@@ -169,7 +170,9 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     a.start_out = nullptr;
     Scratch sc;
     sc.counters = sl.counters;
+    sc.parity = sl.parity;
     ctx->launches += launch_track(m.d, a, sc, ctx->sm_count, st, nullptr);
+    sl.parity = sc.parity;
     e = cudaMemcpyAsync(r.host_out, host, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.path_len_out, path, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.status_out, status, n, cudaMemcpyDeviceToHost, st);
@@ -298,7 +301,8 @@ cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg) {
     for (Slot &sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&sl.counters, 16 * sizeof(int32_t)) != cudaSuccess) {
+            cudaMalloc(&sl.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
+            cudaMemset(sl.counters, 0, 16 * sizeof(int32_t)) != cudaSuccess) {
             ctx->server = S;
             serve_release(ctx);
             return sfail(ctx, CS_ENOMEM, "cs_serve_start: slot resources");

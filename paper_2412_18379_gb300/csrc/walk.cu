@@ -118,7 +118,7 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
 
 template <int D>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh m, const TrackArgs a,
-                                                   int32_t *cursor) {
+                                                   int32_t *cursor, int32_t *next_cursor) {
     using WR = typename Recs<D>::W;
     using XR = typename Recs<D>::X;
     __shared__ Queue<D> queues[kWarps];
@@ -135,6 +135,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
     int32_t cur = -1, it = 0;
     int q_head = 0, q_n = 0;     // warp-uniform
     bool drained = false;        // warp-uniform: global cursor exhausted
+    // the cursor of the next walk on this stream, which no one uses now
+    if (blockIdx.x == 0 && threadIdx.x == 0) *next_cursor = 0;
 
     for (;;) {
         // ---- refill idle lanes from the warp's queue ----
@@ -289,10 +291,14 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
 
 }  // namespace
 
-int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_count,
+int launch_track(const DevMesh &m, const TrackArgs &a, Scratch &s, int sm_count,
                  cudaStream_t st, Profiler *prof) {
     if (a.n == 0) return 0;
-    cudaMemsetAsync(s.counters, 0, sizeof(int32_t), st);
+    // Two cursors used alternately: this walk's was zeroed by the walk before
+    // it on the stream (or at allocation), and it zeroes the other one for
+    // the walk after it. No memset node between the kernels of a step.
+    int32_t *cursor = s.counters + s.parity, *next = s.counters + (s.parity ^ 1);
+    s.parity ^= 1;
     static int per_sm[4] = {0, 0, 0, 0};
     if (!per_sm[m.dim]) {
         if (m.dim == 2)
@@ -305,9 +311,12 @@ int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_
     const int grid = int(std::min<int64_t>(int64_t(sm_count) * per_sm[m.dim], need));
     const int ev = prof ? prof->begin(CS_STAGE_WALK, st) : -1;
     if (m.dim == 2)
-        walk_kernel<2><<<grid, 256, 0, st>>>(m, a, s.counters);
+        walk_kernel<2><<<grid, 256, 0, st>>>(m, a, cursor, next);
     else
-        walk_kernel<3><<<grid, 256, 0, st>>>(m, a, s.counters);
+        walk_kernel<3><<<grid, 256, 0, st>>>(m, a, cursor, next);
+    // a walk that did not launch zeroed nothing: zero both cursors, so the
+    // next call starts from a clean state whichever one it takes
+    if (cudaPeekAtLastError() != cudaSuccess) cudaMemsetAsync(s.counters, 0, 2 * sizeof(int32_t), st);
     if (prof) prof->end(ev, st);
     return 1;
 }
@@ -325,12 +334,14 @@ int launch_track(const DevMesh &m, const TrackArgs &a, const Scratch &s, int sm_
 // ---------------------------------------------------------------------------
 namespace {
 
-// [0] work cursor; the rest is padding to one 256-byte line
+// [0], [1] the walk's alternate work cursors (zero at load); the rest is
+// padding to one 256-byte line
 static __device__ __align__(256) int32_t g_noalloc_scratch[64];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int32_t *g_noalloc_ptr[kMaxDevices] = {};
+int g_noalloc_parity[kMaxDevices] = {};    // cursor of the next call per device
 
 }  // namespace
 
@@ -382,6 +393,7 @@ extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, c
     // once per device, with that device current: the device address of the
     // array (its name in host code is only a host-side stand-in)
     int32_t *base = nullptr;
+    Scratch s;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
         if (!g_noalloc_ptr[ctx->device]) {
@@ -395,9 +407,11 @@ extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, c
             g_noalloc_ptr[ctx->device] = static_cast<int32_t *>(ptr);
         }
         base = g_noalloc_ptr[ctx->device];
+        s.counters = base;
+        s.parity = g_noalloc_parity[ctx->device];
+        // n > 0 here, so launch_track launches the walk and flips the cursor
+        g_noalloc_parity[ctx->device] ^= 1;
     }
-    Scratch s;
-    s.counters = base;                      // zeroed by launch_track on the stream
     TrackArgs a{};
     a.n = n;
     a.x = x;
