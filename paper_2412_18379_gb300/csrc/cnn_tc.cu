@@ -286,6 +286,11 @@ __device__ __forceinline__ bool handoff_or(bool flag) {
     return r != 0;
 }
 
+// Named barrier 2 over the 16 epilogue warps (warps 0..15)
+__device__ __forceinline__ void epi_bar_sync() {
+    asm volatile("bar.sync 2, %0;" ::"n"(kEpiWarps * 32) : "memory");
+}
+
 // true in exactly one lane of the (converged) warp
 __device__ __forceinline__ bool elect_one() {
     uint32_t pred;
@@ -446,13 +451,27 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const int tiles_x = (gx + kTileW - 1) / kTileW, tiles_y = (gy + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y;
 
-    // weights into shared memory (once per CTA, asynchronous while the
-    // buffers are zeroed), zeroed buffers, barriers
+    // The first tile's velocity window (the 16 epilogue warps, idle until the
+    // first MMAs complete, pack it after the barrier below) and the weights
+    // (once per CTA) come in by asynchronous copies while the conv and fc1
+    // buffers and the window's zero rows are cleared. The input buffer needs
+    // no clearing: the tap-packed rows overwrite all of it for every tile.
+    float2 *stage = reinterpret_cast<float2 *>(x0);   // staging, until tap-packed
+    static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
+    const float2 *U2 = reinterpret_cast<const float2 *>(U);
+    if (warp < kEpiWarps) {
+        const int cx0 = (blockIdx.x % tiles_x) * kTileW - 4, cy0 = (blockIdx.x / tiles_x) * TH - 4;
+        for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
+            const int cx = cx0 + i % kW, cy = cy0 + i / kW;
+            const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
+            cp_async8_zfill(stage + i, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+        }
+    }
     for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
         cp_async16(wsm + 16 * i, packed + 16 * i);
-    for (int i = tid; i < G::kSmW / 16; i += kThreadsTC)
+    for (int i = G::kSmAct / 16 + tid; i < G::kSmW / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < G::kWinRows * kW; i += kThreadsTC)
+    for (int i = G::kInRows * kW + tid; i < G::kWinRows * kW; i += kThreadsTC)
         reinterpret_cast<uint32_t *>(smem + G::kSmWin)[i] = 0u;
     if (tid == 0) {
         for (int i = 0; i < G::kNumBars; ++i) mbar_init(bars + i, 1u);
@@ -476,8 +495,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
 
     if (warp == kLoadWarp) {
         // ---- inputs: 32 x (TH + 8) cells, channels u_k dt / s_k (BF16), zero outside.
-        //      One buffer: tile k + 1 is loaded while conv2..conv4 of tile k run ----
-        for (int k = 0;; ++k) {
+        //      One buffer: tile k + 1 is loaded while conv2..conv4 of tile k run
+        //      (the epilogue warps load the first tile) ----
+        for (int k = 1;; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
             if (k >= 1 &&
@@ -489,9 +509,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             // one round of asynchronous copies staged in the input buffer (free
             // until the tap-packed rows below overwrite it); then scaled, as
             // BF16 pairs, into the window, whose rows past it stay zero
-            float2 *stage = reinterpret_cast<float2 *>(x0);
-            static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
-            const float2 *U2 = reinterpret_cast<const float2 *>(U);
             for (int y = 0; y < G::kInRows; ++y) {
                 const int cx = cx0 + lane, cy = cy0 + y;
                 const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
@@ -635,6 +652,25 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         // ---- epilogues: groups 0 and 1 take the conv items of the CTA's sequence
         //      alternately, groups 2 and 3 the fc1 items, so a conv epilogue never
         //      queues behind the longer fc1 epilogues of the previous tile ----
+        // the first tile's input (its window copies completed before the
+        // barrier above): scale and round to BF16 pairs, tap-pack, release
+        {
+            uint32_t *win = reinterpret_cast<uint32_t *>(smem + G::kSmWin);
+            for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
+                const float2 uv = stage[i];
+                win[i] = pack_bf16x2(uv.x * scale0, uv.y * scale1);
+            }
+            epi_bar_sync();
+            uint4 *xv = reinterpret_cast<uint4 *>(x0);
+            for (int r = tid; r < G::kRowsX0; r += kEpiWarps * 32) {
+                const uint32_t *p = win + r;
+                xv[r] = make_uint4(p[0], p[1], p[2], p[kW]);
+                xv[G::kRowsX0 + r] = make_uint4(p[kW + 1], p[kW + 2], p[2 * kW], p[2 * kW + 1]);
+            }
+            fence_async_smem();
+            epi_bar_sync();
+            if (tid == 0) red_release_add(epi_cnt + G::kCntX0, 1u);
+        }
         const int g = warp >> 2, q = warp & 3;
         constexpr int kConvItems = G::jbase(4), kFcItems = G::kItems - G::jbase(4);
         const float *b1 = reinterpret_cast<const float *>(wsm + TcLayout::b1);

@@ -195,6 +195,49 @@ def test_track_with_special_displacements(ctx):
     mesh.release()
 
 
+@pytest.mark.parametrize("name,kw,stride", [("tg2d", {"n_side": 121}, 3),
+                                            ("abc3d", {"n_side": 13}, 1)])
+def test_cnn_start_cells_next_to_cell_faces(ctx, name, kw, stride):
+    """The start point y = x + dhat * s of Algorithm 2 placed on ASG cell
+    faces and within 1 ulp .. 1e-9 of them, on both sides: the start element
+    (the seed of y's ASG cell, whose index the device takes through its FP32
+    cell filter with an FP64 fallback) and the whole walk agree with the FP64
+    oracle bit for bit."""
+    import torch
+    c = make_case(name, **kw)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(stride)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=stride)
+    rng = np.random.default_rng(23)
+    s = (om.hi - om.lo) / om.grid
+    n_cell = int(np.prod(om.pgrid))
+    for dh in (1.37, -2.9, 0.001):
+        dhat = np.full((n_cell, c.dim), dh, dtype=np.float32)
+        disp = np.float32(dh).astype(np.float64) * om.ps
+        # target points on random ASG faces on every axis, then nudged
+        n = 3000
+        face = om.lo + rng.integers(1, om.grid, size=(n, c.dim)) * s
+        nudge = np.array([0.0, 1e-16, -1e-16, 1e-13, -1e-13, 1e-11, -1e-11, 1e-9, -1e-9])
+        y = face + nudge[rng.integers(0, nudge.size, size=(n, c.dim))] * np.maximum(1, np.abs(face))
+        y = np.where(rng.random((n, c.dim)) < 0.2, np.nextafter(face, face + 1), y)
+        x = y - disp
+        keep = np.all((x > om.lo) & (x < om.hi), axis=1)
+        x = np.ascontiguousarray(x[keep])
+        u = np.zeros_like(x)
+        start = rng.integers(0, c.n_elements, size=x.shape[0]).astype(np.int32)
+        out = ctx.track_dhat(mesh, _dev(x), _dev(u), c.dt, dhat=_dev(dhat), start=_dev(start),
+                             start_out=True)
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        want = om.track(x, u, c.dt, start=start, mode="cnn", dhat=dhat[om.pred_cells(x)])
+        st = np.where(want["path_len"] > 0, want["start"], -1)
+        for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
+                       ("status", want["status"]), ("start", st)):
+            assert np.array_equal(got[k], ref), (dh, k, np.nonzero(got[k] != ref)[0][:5])
+        assert x.shape[0] > 500
+    mesh.release()
+
+
 def _oracle_cnn_dhat(om, case, flat):
     """Oracle of the predictor stage: FP64 grid velocity, windows at the
     particles' cells, FP64 forward."""
