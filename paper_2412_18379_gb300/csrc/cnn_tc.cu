@@ -451,24 +451,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const int tiles_x = (gx + kTileW - 1) / kTileW, tiles_y = (gy + TH - 1) / TH;
     const int n_tiles = tiles_x * tiles_y;
 
-    // The first tile's velocity window (the 16 epilogue warps, idle until the
-    // first MMAs complete, pack it after the barrier below) and the weights
-    // (once per CTA) come in by asynchronous copies while the conv and fc1
-    // buffers and the window's zero rows are cleared. The input buffer needs
-    // no clearing: the tap-packed rows overwrite all of it for every tile.
-    float2 *stage = reinterpret_cast<float2 *>(x0);   // staging, until tap-packed
-    static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
-    const float2 *U2 = reinterpret_cast<const float2 *>(U);
-    if (warp < kEpiWarps) {
-        const int cx0 = (blockIdx.x % tiles_x) * kTileW - 4, cy0 = (blockIdx.x / tiles_x) * TH - 4;
-        for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
-            const int cx = cx0 + i % kW, cy = cy0 + i / kW;
-            const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
-            cp_async8_zfill(stage + i, in ? U2 + int64_t(cy) * gx + cx : U2, in);
-        }
-    }
-    for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
-        cp_async16(wsm + 16 * i, packed + 16 * i);
+    // Set-up that touches no global memory runs first: it may overlap the end
+    // of the previous kernel on the stream (programmatic dependent launch)
+    // until pdl_wait() below. The conv and fc1 buffers and the window's zero
+    // rows are cleared; the input buffer needs no clearing, since the
+    // tap-packed rows overwrite all of it for every tile.
     for (int i = G::kSmAct / 16 + tid; i < G::kSmW / 16; i += kThreadsTC)
         reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
     for (int i = G::kInRows * kW + tid; i < G::kWinRows * kW; i += kThreadsTC)
@@ -485,6 +472,24 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    // Then, once the previous kernel's writes are visible, the first tile's
+    // velocity window (the 16 epilogue warps, idle until the first MMAs
+    // complete, pack it after the barrier below) and the weights (once per
+    // CTA), by asynchronous copies.
+    pdl_wait();
+    float2 *stage = reinterpret_cast<float2 *>(x0);   // staging, until tap-packed
+    static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
+    const float2 *U2 = reinterpret_cast<const float2 *>(U);
+    if (warp < kEpiWarps) {
+        const int cx0 = (blockIdx.x % tiles_x) * kTileW - 4, cy0 = (blockIdx.x / tiles_x) * TH - 4;
+        for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
+            const int cx = cx0 + i % kW, cy = cy0 + i / kW;
+            const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
+            cp_async8_zfill(stage + i, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+        }
+    }
+    for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
+        cp_async16(wsm + 16 * i, packed + 16 * i);
     cp_async_wait_all();
     fence_async_smem();
     fence_before();
@@ -868,8 +873,8 @@ int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *pack
         attr = true;
     }
     const int grid = std::min(tiles_of<TH>(m), sm_count);
-    cnn2d_tc_kernel<TH><<<grid, kThreadsTC, Geo<TH>::kSmTotal, st>>>(
-        m, U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err);
+    launch_pdl(cnn2d_tc_kernel<TH>, dim3(grid), dim3(kThreadsTC), size_t(Geo<TH>::kSmTotal), st, m,
+               U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err);
     return 1;
 }
 

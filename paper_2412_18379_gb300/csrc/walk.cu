@@ -135,6 +135,10 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) walk_kernel(const DevMesh
     int32_t cur = -1, it = 0;
     int q_head = 0, q_n = 0;     // warp-uniform
     bool drained = false;        // warp-uniform: global cursor exhausted
+    // nothing before this reads or writes global memory (launched with
+    // programmatic dependent launch, the kernel may start while the kernel
+    // before it, e.g. the predictor writing dhat, is finishing)
+    pdl_wait();
     // the cursor of the next walk on this stream, which no one uses now
     if (blockIdx.x == 0 && threadIdx.x == 0) *next_cursor = 0;
 
@@ -311,9 +315,9 @@ int launch_track(const DevMesh &m, const TrackArgs &a, Scratch &s, int sm_count,
     const int grid = int(std::min<int64_t>(int64_t(sm_count) * per_sm[m.dim], need));
     const int ev = prof ? prof->begin(CS_STAGE_WALK, st) : -1;
     if (m.dim == 2)
-        walk_kernel<2><<<grid, 256, 0, st>>>(m, a, cursor, next);
+        launch_pdl(walk_kernel<2>, dim3(grid), dim3(256), 0, st, m, a, cursor, next);
     else
-        walk_kernel<3><<<grid, 256, 0, st>>>(m, a, cursor, next);
+        launch_pdl(walk_kernel<3>, dim3(grid), dim3(256), 0, st, m, a, cursor, next);
     // a walk that did not launch zeroed nothing: zero both cursors, so the
     // next call starts from a clean state whichever one it takes
     if (cudaPeekAtLastError() != cudaSuccess) cudaMemsetAsync(s.counters, 0, 2 * sizeof(int32_t), st);

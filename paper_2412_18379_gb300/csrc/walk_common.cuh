@@ -27,6 +27,30 @@ namespace cs {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch. launch_pdl lets the kernel be scheduled
+// while the previous kernel on the stream is still finishing, which hides
+// the launch gap between the kernels of a step; the kernel must call
+// pdl_wait() before it touches global memory that an earlier kernel on the
+// stream writes or reads (it returns once those kernels have completed and
+// their writes are visible; without the launch attribute it returns at once).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // FP32 unit roundoff u = 2^-24 and the filter's constants
 constexpr float kU = 5.9604644775390625e-08f;
 constexpr float k4U = 4.0f * kU;
