@@ -665,21 +665,27 @@ __global__ void __launch_bounds__(256) conv_nt32_kernel(const float *__restrict_
         rowbase[i] = chfirst ? int64_t(b) * C * Pi + pb : (int64_t(b) * Pi + pb) * C;
     }
     float ra[16], rb[16];
+    // K order: (channel, tap) for a channels-first input, as W is stored;
+    // (tap, channel) for a channels-last one, so that the 32 lanes of a warp,
+    // which take 32 consecutive k, read 32 consecutive channels of one input
+    // position (one 128-byte line) instead of 32 scattered taps
     auto fetch = [&](int64_t k0) {
         const int64_t gk = k0 + kk;
-        int64_t koff = 0;
+        int64_t koff = 0, wk = 0;
         const bool kok = gk < K;
         if (kok) {
-            const int ch = int(gk / taps), t = int(gk % taps);
+            const int ch = chfirst ? int(gk / taps) : int(gk % C);
+            const int t = chfirst ? int(gk % taps) : int(gk / C);
             const int dx = t % 3, dy = (t / 3) % 3, dz = D == 3 ? t / 9 : 0;
             const int64_t toff = D == 2 ? int64_t(dy) * Si + dx : (int64_t(dz) * Si + dy) * Si + dx;
             koff = chfirst ? int64_t(ch) * Pi + toff : toff * C + ch;
+            wk = int64_t(ch) * taps + t;
         }
         #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const float av = (rowok[i] && kok) ? __ldg(x + rowbase[i] + koff) : 0.f;
             const int r = (tid >> 5) + 2 * i;   // weight row (output channel)
-            const float bv = kok ? __ldg(Wt + int64_t(r) * K + gk) : 0.f;
+            const float bv = kok ? __ldg(Wt + int64_t(r) * K + wk) : 0.f;
             ra[i] = round_bf16 ? bf16_round(av) : av;
             rb[i] = round_bf16 ? bf16_round(bv) : bv;
         }
@@ -744,49 +750,64 @@ __global__ void __launch_bounds__(256) conv_nt32_kernel(const float *__restrict_
 }
 
 // The predictor's head on rows of conv features (inference): out[r] =
-// W2 ReLU(W1 y[r] + b1) + b2 for y [M][32], W1 [256][32], W2 [dim][256], one
-// thread per row with W1 and W2 in shared memory. Same BF16 operand rounding
-// and the same k order as the two GEMMs plus ReLU it replaces, so the same
-// bits.
+// W2 ReLU(W1 y[r] + b1) + b2 for y [M][32], W1 [256][32], W2 [dim][256]. One
+// warp per row: lane l computes features n = l, l + 32, ..., l + 224 (each a
+// sum over k in order), the row's 256 features meet in shared memory, and
+// lanes d < dim sum W2 over n in order. Same BF16 operand rounding and the
+// same summation orders as the two GEMMs plus ReLU it replaces, so the same
+// bits. W1 is stored transposed in shared memory ([k][n]) so that the lanes
+// read consecutive words.
 template <int DIM>
-__global__ void __launch_bounds__(128) head_kernel(const float *__restrict__ y,
+__global__ void __launch_bounds__(256) head_kernel(const float *__restrict__ y,
                                                    const float *__restrict__ W1,
                                                    const float *__restrict__ b1,
                                                    const float *__restrict__ W2,
                                                    const float *__restrict__ b2, int64_t M,
                                                    float *__restrict__ out, bool round_bf16) {
-    __shared__ float w1[256 * 32];
+    __shared__ float w1t[32 * 256];
     __shared__ float w2[DIM * 256];
     __shared__ float bb1[256];
-    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x)
-        w1[i] = round_bf16 ? bf16_round(W1[i]) : W1[i];
+    __shared__ float hs[8][256];
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) {
+        const float v = W1[i];                        // W1[n][k], i = 32 n + k
+        w1t[(i & 31) * 256 + (i >> 5)] = round_bf16 ? bf16_round(v) : v;
+    }
     for (int i = threadIdx.x; i < DIM * 256; i += blockDim.x)
         w2[i] = round_bf16 ? bf16_round(W2[i]) : W2[i];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) bb1[i] = b1[i];
     __syncthreads();
-    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < M;
-         r += int64_t(gridDim.x) * blockDim.x) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *h = hs[wib];
+    for (int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; r < M;
+         r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        // the row's 32 inputs, in every lane (one broadcast load each)
         float f[32];
         #pragma unroll
         for (int k = 0; k < 32; ++k) {
             const float v = __ldg(y + r * 32 + k);
             f[k] = round_bf16 ? bf16_round(v) : v;
         }
-        float o[DIM];
+        float hv[8];
         #pragma unroll
-        for (int d = 0; d < DIM; ++d) o[d] = 0.f;
-        #pragma unroll 2
-        for (int n = 0; n < 256; ++n) {
-            float h = 0.f;
+        for (int j = 0; j < 8; ++j) hv[j] = 0.f;
+        #pragma unroll
+        for (int k = 0; k < 32; ++k)
             #pragma unroll
-            for (int k = 0; k < 32; ++k) h = fmaf(f[k], w1[n * 32 + k], h);
-            h = fmaxf(h + bb1[n], 0.f);
-            if (round_bf16) h = bf16_round(h);
-            #pragma unroll
-            for (int d = 0; d < DIM; ++d) o[d] = fmaf(h, w2[d * 256 + n], o[d]);
+            for (int j = 0; j < 8; ++j) hv[j] = fmaf(f[k], w1t[k * 256 + lane + 32 * j], hv[j]);
+        #pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int n = lane + 32 * j;
+            float v = fmaxf(hv[j] + bb1[n], 0.f);
+            h[n] = round_bf16 ? bf16_round(v) : v;
         }
-        #pragma unroll
-        for (int d = 0; d < DIM; ++d) out[r * DIM + d] = o[d] + b2[d];
+        __syncwarp();
+        if (lane < DIM) {
+            float o = 0.f;
+            #pragma unroll 8
+            for (int n = 0; n < 256; ++n) o = fmaf(h[n], w2[lane * 256 + n], o);
+            out[r * DIM + lane] = o + b2[lane];
+        }
+        __syncwarp();
     }
 }
 
@@ -834,11 +855,13 @@ int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, in
 
 int launch_head(int dim, const float *y, const float *W1, const float *b1, const float *W2,
                 const float *b2, int64_t M, float *out, int sm_count, cudaStream_t st) {
-    const int g = int(std::max<int64_t>(1, std::min<int64_t>((M + 127) / 128, int64_t(sm_count) * 4)));
+    // 8 rows in flight per block (one per warp); at most two blocks per SM,
+    // since each block first stages the 35 KB of head weights
+    const int g = int(std::max<int64_t>(1, std::min<int64_t>((M + 7) / 8, int64_t(sm_count) * 2)));
     if (dim == 2)
-        head_kernel<2><<<g, 128, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
+        head_kernel<2><<<g, 256, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
     else
-        head_kernel<3><<<g, 128, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
+        head_kernel<3><<<g, 256, 0, st>>>(y, W1, b1, W2, b2, M, out, g_gemm_bf16);
     return 1;
 }
 
