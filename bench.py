@@ -458,7 +458,8 @@ def main():
     walk_roof = {"bound": "hbm", "achieved": alg_bytes / (walk_ms / walk_l * 1e-3) / 1e9,
                  "peak": hbm_peak, "unit": "GB/s", "kernel": "walk_kernel<%d>" % dim,
                  "kernel_ms": walk_ms / walk_l, "algorithmic_bytes_per_launch": alg_bytes,
-                 "traffic": ncu_traffic("walk_kernel_%s_ncu.md" % args.workload, WALK_SOURCES),
+                 "traffic": ncu_traffic("walk_kernel_%s_%s_ncu.md" % (args.workload, args.mode),
+                                        WALK_SOURCES),
                  "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
     walk_roof["frac"] = walk_roof["achieved"] / hbm_peak
     rooflines = {"walk": walk_roof}
