@@ -152,18 +152,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_rate(case, sample_n, seed=0):
+def particle_set(case, kind):
+    """(x, u, start) of the particles: one per mesh node (start None: the
+    node's element), or one per (element, node) pair starting from the element."""
+    from workloads import element_node_particles
+    if kind == "element-nodes":
+        return element_node_particles(case)
+    return case.x, case.u, None
+
+
+def cpu_oracle_rate(case, sample_n, seed=0, particles="nodes"):
     """The oracle as it stands (single-threaded C through ctypes) on a bounded
     sample of the workload's particles: departure point, Algorithm 1 walk from
-    the node's element, exact host. Returns particles/s and seconds."""
+    the plain start, exact host. Returns particles/s and seconds."""
     import oracle
     om = oracle.Mesh(case.xyz, case.conn)
+    px, pu, pstart = particle_set(case, particles)
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(case.n_particles, size=min(sample_n, case.n_particles),
-                             replace=False))
-    start = om.node_elem[idx]
+    idx = np.sort(rng.choice(px.shape[0], size=min(sample_n, px.shape[0]), replace=False))
+    start = om.node_elem[idx] if pstart is None else pstart[idx]
     t0 = time.perf_counter()
-    om.track(case.x[idx], case.u[idx], case.dt, start=start, mode="sns")
+    om.track(px[idx], pu[idx], case.dt, start=start, mode="sns")
     dt = time.perf_counter() - t0
     return idx.size / dt, dt
 
@@ -178,7 +187,7 @@ def run_reference(args):
     sample = args.ref_sample
     times = []
     for i in range(args.warmup + args.steps):
-        _, dt = cpu_oracle_rate(case, sample, seed=i)
+        _, dt = cpu_oracle_rate(case, sample, seed=i, particles=args.particles)
         if i >= args.warmup:
             times.append(dt)
     per_step = float(np.mean(times))
@@ -321,6 +330,9 @@ def main():
     ap.add_argument("--workload", default="tg2d", choices=sorted(WORKLOADS))
     ap.add_argument("--cfl", type=float, default=8.0)
     ap.add_argument("--mode", default="cnn", choices=["sns", "asg", "cnn"])
+    ap.add_argument("--particles", default="nodes", choices=["nodes", "element-nodes"],
+                    help="one particle per mesh node, or per (element, node) pair "
+                         "((d + 1) n_e particles, each starting from its element)")
     ap.add_argument("--pred-stride", type=int, default=5,
                     help="ASG cells per predictor cell and axis (odd)")
     ap.add_argument("--train-fields", type=int, default=4)
@@ -374,9 +386,15 @@ def main():
         training = train_predictor(ctx, mesh, case, args.train_fields, args.train_steps,
                                    args.train_batch, seed=rank)
 
-    x = torch.from_numpy(case.x).to(dev)
-    u = torch.from_numpy(case.u).to(dev)
-    n = case.n_particles
+    px, pu, pstart = particle_set(case, args.particles)
+    x = torch.from_numpy(px).to(dev)
+    u = torch.from_numpy(pu).to(dev)
+    start = None if pstart is None else torch.from_numpy(pstart).to(dev)
+    n = px.shape[0]
+    if start is not None and "cnn" in modes:
+        # particles that are not the mesh nodes take the predictor's input
+        # from the stored grid velocity of the nodal field
+        ctx.grid_velocity(mesh, torch.from_numpy(case.u).to(dev))
     out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
                path_len=torch.empty(n, dtype=torch.int32, device=dev),
                status=torch.empty(n, dtype=torch.uint8, device=dev))
@@ -384,7 +402,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(mode):
-        ctx.track(mesh, x, u, case.dt, mode=mode, out=out, stream=stream)
+        ctx.track(mesh, x, u, case.dt, start=start, mode=mode, out=out, stream=stream)
 
     def run_steps(mode, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -478,23 +496,25 @@ def main():
     roofline = dict(rooflines[dominant])
 
     # end to end through the host-pointer entry point (pinned buffers)
-    xh = torch.from_numpy(case.x).pin_memory()
-    uh = torch.from_numpy(case.u).pin_memory()
+    xh = torch.from_numpy(px).pin_memory()
+    uh = torch.from_numpy(pu).pin_memory()
+    sh = None if pstart is None else torch.from_numpy(pstart).pin_memory()
     hout = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
                 path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
                 status=torch.empty(n, dtype=torch.uint8).pin_memory())
     for _ in range(0 if args.quick else 3):
-        ctx.track_host(mesh, xh, uh, case.dt, mode=args.mode, out=hout)
+        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout)
     torch.cuda.synchronize()
     e2e_steps = max(3, args.steps // 10) if not args.quick else 1
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.track_host(mesh, xh, uh, case.dt, mode=args.mode, out=hout)
+        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
         e2e_s = max_over_ranks(e2e_s, device=dev)
     e2e = {"value": world * n / e2e_s, "unit": "particles/s",
-           "h2d_bytes_per_step": n * dim * 16, "d2h_bytes_per_step": n * 9,
+           "h2d_bytes_per_step": n * dim * 16 + (0 if sh is None else n * 4),
+           "d2h_bytes_per_step": n * 9,
            "entry_point": "cs_track_host"}
 
     serving = None
@@ -504,7 +524,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt_cpu = cpu_oracle_rate(case, args.cpu_sample)
+        rate, dt_cpu = cpu_oracle_rate(case, args.cpu_sample, particles=args.particles)
         cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
                "sample": "%d of the %d particles (seeded draw), the oracle's plain SNS: "
                          "departure point + Algorithm 1 walk + exact host, %.2f s"
@@ -520,6 +540,9 @@ def main():
             "config": {"workload": wl["desc"] + ", CFL %g" % args.cfl,
                        "mode": {"cnn": "CNN-SNS (Algorithm 2)", "sns": "plain SNS",
                                 "asg": "ASG-direct"}[args.mode],
+                       "particles": ("one per mesh node, from the node's element"
+                                     if pstart is None else
+                                     "one per (element, node) pair, from the element"),
                        "n_particles": n, "n_elements": case.n_elements,
                        "asg_grid": info["asg_grid"],
                        "predictor_grid": {"stride": info["pred_stride"],

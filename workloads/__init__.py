@@ -15,10 +15,10 @@ jittered unit cube split into six Kuhn tetrahedra per lattice cell (3-D).
 from .meshes import lattice_2d, delaunay_2d, kuhn_3d, mesh_2d, mesh_3d
 from .fields import (rotation, taylor_green, abc_flow, fourier_modes_2d,
                      fourier_modes_3d, dt_for_cfl, cfl_of)
-from .cases import make_case, Case
+from .cases import make_case, Case, element_node_particles
 
 __all__ = [
     "lattice_2d", "delaunay_2d", "kuhn_3d", "mesh_2d", "mesh_3d",
     "rotation", "taylor_green", "abc_flow", "fourier_modes_2d",
-    "fourier_modes_3d", "dt_for_cfl", "cfl_of", "make_case", "Case",
+    "fourier_modes_3d", "dt_for_cfl", "cfl_of", "make_case", "Case", "element_node_particles",
 ]

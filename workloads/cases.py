@@ -83,3 +83,16 @@ def make_case(name, cfl=None, n_side=None, seed=None, field_seed=None):
     x = np.array(xyz, dtype=np.float64, copy=True)
     return Case(name=name, dim=dim, xyz=xyz, conn=conn, h=h, x=x,
                 u=np.ascontiguousarray(u), dt=dt, cfl=cfl)
+
+
+def element_node_particles(case):
+    """One particle per (element, local node) pair, the characteristic-tracing
+    layout of an L-G step (Sec. 2.1, Eq. 4: every element's nodes are traced
+    back from that element): n = (d + 1) * n_elements particles, ordered
+    element-major. Returns (x, u, start): the node's position and velocity,
+    and the owning element's user id as the plain-SNS start."""
+    nodes = case.conn.reshape(-1)
+    x = np.ascontiguousarray(case.xyz[nodes])
+    u = np.ascontiguousarray(case.u[nodes])
+    start = np.repeat(np.arange(case.n_elements, dtype=np.int32), case.dim + 1)
+    return x, u, start
