@@ -1,0 +1,70 @@
+"""Host-side helpers of bench.py (no GPU): the particle layouts it times, the
+ncu-summary lookup behind the roofline's `traffic`, and the CPU baseline."""
+
+import os
+
+import numpy as np
+import pytest
+
+import bench
+from workloads import make_case
+
+
+def test_particle_sets():
+    c = make_case("rotation2d")
+    x, u, start = bench.particle_set(c, "nodes")
+    assert x is c.x and u is c.u and start is None
+    x, u, start = bench.particle_set(c, "element-nodes")
+    assert x.shape == (3 * c.n_elements, 2) and start.shape == (3 * c.n_elements,)
+    assert np.array_equal(start[::3], np.arange(c.n_elements))
+
+
+def _fake_root(tmp_path, source_text, profile_lines):
+    root = tmp_path / "root"
+    (root / "paper_2412_18379_gb300" / "csrc").mkdir(parents=True)
+    (root / "profiles").mkdir()
+    (root / "paper_2412_18379_gb300" / "csrc" / "k.cu").write_text(source_text)
+    (root / "profiles" / "k_ncu.md").write_text("\n".join(profile_lines) + "\n")
+    return root
+
+
+def test_traffic_only_from_a_summary_of_the_current_source(tmp_path, monkeypatch):
+    src = "__global__ void k() {}\n"
+    root = _fake_root(tmp_path, src, ["# k"])
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    sha = bench.source_sha(("k.cu",))
+    assert len(sha) == 16
+    (root / "profiles" / "k_ncu.md").write_text(
+        "# k\n\n- source_sha256_16: %s\n- sources: k.cu\n- dram_bytes_per_full_launch: 1234\n" % sha)
+    assert bench.ncu_traffic("k_ncu.md", ("k.cu",)) == 1234.0
+    # the kernel changed since the capture: no traffic
+    (root / "paper_2412_18379_gb300" / "csrc" / "k.cu").write_text(src + "// edited\n")
+    assert bench.ncu_traffic("k_ncu.md", ("k.cu",)) is None
+    # no summary, or one without the figure: no traffic
+    assert bench.ncu_traffic("missing_ncu.md", ("k.cu",)) is None
+    (root / "profiles" / "k_ncu.md").write_text("- source_sha256_16: %s\n"
+                                                % bench.source_sha(("k.cu",)))
+    assert bench.ncu_traffic("k_ncu.md", ("k.cu",)) is None
+
+
+def test_committed_summaries_name_their_sources():
+    prof = os.path.join(bench.ROOT, "profiles")
+    names = [f for f in os.listdir(prof) if f.endswith("_ncu.md")]
+    assert names
+    for f in names:
+        vals = {}
+        for line in open(os.path.join(prof, f)):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                vals[k.strip()] = v.strip()
+        assert len(vals["source_sha256_16"]) == 16, f
+        for s in vals["sources"].split(","):
+            assert os.path.exists(os.path.join(bench.ROOT, "paper_2412_18379_gb300", "csrc", s)), f
+        assert float(vals["dram_bytes_per_full_launch"]) > 0, f
+
+
+@pytest.mark.parametrize("particles", ["nodes", "element-nodes"])
+def test_cpu_baseline_on_a_sample(particles):
+    c = make_case("rotation2d")
+    rate, seconds = bench.cpu_oracle_rate(c, 500, seed=1, particles=particles)
+    assert rate > 0 and seconds > 0
