@@ -597,3 +597,35 @@ def test_cnn_sns_3d_on_tiles_keeps_hosts(ctx):
     assert np.array_equal(got["host"], plain["host"])
     for k in ("host", "path_len", "status"):
         assert np.array_equal(got[k], want[k]), k
+
+
+def test_full_size_cnn_sns_parity(ctx):
+    """The 1001 x 1001 Taylor-Green workload at CFL 8 with the predictor on
+    the stride-5 grid (the benchmark's configuration): the oracle, given the
+    device's predicted displacements, takes the same starts, paths, statuses
+    and hosts on every particle, and the hosts are plain SNS's."""
+    import torch
+    c = make_case("tg2d", cfl=8)
+    flat = init_weights(2, 12)
+    o = cnn.spec(2)
+    fc2 = sum(int(np.prod(w)) + int(np.prod(b)) for _, w, b in o[:-1])
+    flat[fc2:] *= 0.25
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(5)
+    out = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn", start_out=True)
+    dhat = torch.empty((int(np.prod(mesh.info()["pred_grid"])), 2), dtype=torch.float32,
+                       device="cuda")
+    ctx.predict(mesh, c.dt, out=dhat)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=5)
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    start = np.where(want["path_len"] > 0, want["start"], -1)
+    for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
+                   ("status", want["status"]), ("start", start)):
+        bad = np.nonzero(got[k] != ref)[0]
+        assert bad.size == 0, (k, bad.size, bad[:5])
+    plain = om.track(c.x, c.u, c.dt, mode="sns")
+    assert np.array_equal(got["host"], plain["host"])
+    mesh.release()
