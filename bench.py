@@ -285,9 +285,8 @@ def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed, pred_s
             if c.dim == 2:
                 m.set_predictor_grid(pred_stride)
             u = (fourier_modes_2d if c.dim == 2 else fourier_modes_3d)(c.xyz, 77 + i)
-        if c.dim == 2:
-            ctx.grid_velocity(m, torch.from_numpy(u).cuda())
-        entries.append(dict(case=c, mesh=m, x=torch.from_numpy(c.x).pin_memory(),
+        field = ctx.upload_field(m, u) if c.dim == 2 else None
+        entries.append(dict(case=c, mesh=m, field=field, x=torch.from_numpy(c.x).pin_memory(),
                             u=torch.from_numpy(np.ascontiguousarray(u)).pin_memory(),
                             start=torch.from_numpy(m.node_start_elements()).pin_memory(),
                             umax=float(np.sqrt((u * u).sum(axis=1)).max())))
@@ -308,7 +307,7 @@ def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed, pred_s
                 pass
             sl = slice(off, off + n)
             t, _ = ctx.submit(e["mesh"], e["x"][sl], e["u"][sl], dt, start=e["start"][sl],
-                              mode="cnn")
+                              mode="cnn", field=e["field"])
             tickets.append(t)
         for t in tickets:
             ctx.wait(t, timeout_ms=120000)
@@ -391,10 +390,11 @@ def main():
     u = torch.from_numpy(pu).to(dev)
     start = None if pstart is None else torch.from_numpy(pstart).to(dev)
     n = px.shape[0]
+    field = None
     if start is not None and "cnn" in modes:
-        # particles that are not the mesh nodes take the predictor's input
-        # from the stored grid velocity of the nodal field
-        ctx.grid_velocity(mesh, torch.from_numpy(case.u).to(dev))
+        # particles that are not the mesh nodes: the predictor reads the
+        # resident field of the nodal velocity
+        field = ctx.upload_field(mesh, case.u)
     out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
                path_len=torch.empty(n, dtype=torch.int32, device=dev),
                status=torch.empty(n, dtype=torch.uint8, device=dev))
@@ -402,7 +402,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(mode):
-        ctx.track(mesh, x, u, case.dt, start=start, mode=mode, out=out, stream=stream)
+        ctx.track(mesh, x, u, case.dt, start=start, mode=mode, out=out, stream=stream,
+                  field=field)
 
     def run_steps(mode, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -503,12 +504,12 @@ def main():
                 path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
                 status=torch.empty(n, dtype=torch.uint8).pin_memory())
     for _ in range(0 if args.quick else 3):
-        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout)
+        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout, field=field)
     torch.cuda.synchronize()
     e2e_steps = max(3, args.steps // 10) if not args.quick else 1
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout)
+        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout, field=field)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
         e2e_s = max_over_ranks(e2e_s, device=dev)

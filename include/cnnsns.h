@@ -20,7 +20,11 @@
  *  - Arrays are row-major and densely packed: xyz[n_v][dim], conn[n_e][dim+1],
  *    x[n][dim], u[n][dim].
  *  - The caller owns every array it passes; the library owns its device
- *    copies of meshes (until cs_mesh_release / cs_destroy).
+ *    copies of meshes and fields (until cs_mesh_release / cs_field_release /
+ *    cs_destroy).
+ *  - Every device allocation of the library counts against the context's
+ *    HBM budget (cs_create); an allocation that would pass it fails with
+ *    CS_ENOMEM and nothing is allocated.
  *  - One context serves one thread at a time; calls on a context must not
  *    overlap (it owns one scratch arena).
  *
@@ -69,6 +73,9 @@ typedef int32_t cs_status;
 
 #define CS_EPS 1e-12
 
+/* field id of calls that name no velocity field (see cs_track) */
+#define CS_NO_FIELD (-1)
+
 typedef struct cs_mesh_info {
     int32_t dim;
     int64_t n_vertices;
@@ -85,14 +92,21 @@ typedef struct cs_mesh_info {
     int32_t pred_grid[3];       /* predictor cells per axis (see below)      */
 } cs_mesh_info;
 
-/* Create a context on CUDA device `cuda_device`. */
-cs_status cs_create(cs_ctx **out, int cuda_device);
+/* Create a context on CUDA device `cuda_device`. hbm_budget_bytes caps the
+ * device memory the context may hold at once (meshes, fields, predictor
+ * weights and workspaces, scratch, the serving arena); 0 = no cap beyond the
+ * device's own. Errors: CS_EINVAL (device out of range), CS_ENOMEM, CS_ECUDA. */
+cs_status cs_create(cs_ctx **out, int cuda_device, size_t hbm_budget_bytes);
 
 /* Release every mesh, predictor and scratch buffer of the context. */
 void cs_destroy(cs_ctx *ctx);
 
 /* Message of the last failed call on this context (owned by the context). */
 const char *cs_last_error(const cs_ctx *ctx);
+
+/* Device bytes the context holds now and its budget (0 = none); either
+ * pointer may be NULL. */
+cs_status cs_memory_usage(cs_ctx *ctx, size_t *used_bytes, size_t *budget_bytes);
 
 /*
  * Upload a mesh {K_l} (Sec. 2.2). Host pointers. Builds on the host: the
@@ -122,18 +136,40 @@ cs_status cs_node_start_elements(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
 cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
 
 /*
+ * Upload a velocity field of a mesh: the nodal velocity u_nodal[n_v][dim]
+ * (HOST or DEVICE pointer, FP64) that Algorithm 2's start predictor reads
+ * (Sec. 2.3: the CNN input is the velocity field around the particle). The
+ * library keeps a device copy and its P1 resampling to the mesh's predictor
+ * grid (cs_grid_velocity's arithmetic), redone at the next use after
+ * cs_predictor_grid changes that grid. Synchronous.
+ * Errors: CS_ENOMESH, CS_EINVAL (null pointer), CS_EBUSY (while serving),
+ * CS_ENOMEM (device memory or HBM budget), CS_ECUDA.
+ */
+cs_status cs_field_upload(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal,
+                          int32_t *field_id_out);
+
+/* Release a field (CS_EINVAL if unknown, CS_EBUSY while serving). Releasing
+ * a mesh releases its fields. */
+cs_status cs_field_release(cs_ctx *ctx, int32_t field_id);
+
+/*
  * Locate n particles (Algorithm 1 / Algorithm 2). DEVICE pointers; the work
  * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and
  * the call returns without synchronising.
+ *   field_id: the velocity field (cs_field_upload) whose grid velocity the
+ *             CNN-SNS start predictor reads, or CS_NO_FIELD. Read by
+ *             CS_CNN_SNS only.
  *   x[n][dim], u[n][dim]: particle position and velocity; x_p = x - (u*dt).
  *   start[n]: user ids of the plain-SNS start, or NULL when the particles are
  *             the mesh vertices in order (n == n_vertices): then start =
  *             cs_node_start_elements(). A start of -1 skips the walk.
  *   mode: CS_SNS, CS_ASG_DIRECT or CS_CNN_SNS. CS_CNN_SNS needs a loaded
- *         predictor (cs_predictor_load). When start == NULL and the particles
- *         are the mesh nodes, u is the nodal field: the call resamples it to
- *         the predictor grid, runs the predictor and walks (Algorithm 2). Otherwise
- *         it uses the grid velocity stored by cs_grid_velocity.
+ *         predictor (cs_predictor_load); the call runs the predictor over the
+ *         predictor grid and then walks (Algorithm 2). The predictor reads
+ *         the grid velocity of field_id. With CS_NO_FIELD the particles must
+ *         be the mesh nodes (start == NULL, n == n_vertices): u is then the
+ *         nodal field, resampled to the predictor grid by this call and kept
+ *         as the mesh's stored grid velocity (cs_predict, cs_windows).
  *   host_out[n]  user id of the host of x_p, or -1.
  *   path_len_out[n]  I_t of Algorithm 1 (elements evaluated, start included).
  *   status_out[n]    CS_FOUND / CS_OUTSIDE / CS_FOUND_VIA_FALLBACK / CS_INVALID.
@@ -146,19 +182,21 @@ cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out);
  * through an exact search of the bucket index, run by the warp that walked
  * them; the result is the host defined at the top of this file.
  * Errors: CS_EINVAL (n outside [0, 2^31 - 2], null pointer, start == NULL
- * with n != n_v, bad mode), CS_ENOMESH, CS_ENOPRED, CS_ENOMEM, CS_ECUDA.
+ * with n != n_v, bad mode, field_id not a field of this mesh, CS_CNN_SNS with
+ * CS_NO_FIELD on particles that are not the mesh nodes), CS_ENOMESH,
+ * CS_ENOPRED, CS_ENOMEM, CS_ECUDA.
  */
-cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n, const double *x,
                    const double *u, double dt, const int32_t *start, int mode,
                    int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                    int32_t *start_out, void *stream);
 
 /* cs_track with HOST pointers: copies inputs to the device, runs, copies the
  * results back and synchronises. Same arguments and errors. */
-cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
-                        const double *u, double dt, const int32_t *start, int mode,
-                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
-                        int32_t *start_out);
+cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
+                        const double *x, const double *u, double dt, const int32_t *start,
+                        int mode, int32_t *host_out, int32_t *path_len_out,
+                        uint8_t *status_out, int32_t *start_out);
 
 /*
  * cs_track without any device allocation. (This entry point is a property of
@@ -168,11 +206,16 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
  * call -- a solver that owns every byte of device memory through its own pool,
  * or a time-step loop that cannot afford the device-wide synchronisation that
  * cudaMalloc / cudaFree may cause. Same arguments, semantics, results and
- * errors as cs_track (DEVICE pointers, enqueued on `stream`, returns without
- * synchronising); the caller still provides every input and output array.
- * The walk's only scratch, its work cursor, lives in one fixed 256-byte
- * device array of this library that every GPU loading the library holds
- * until the process exits.
+ * errors as cs_track for CS_SNS and CS_ASG_DIRECT (DEVICE pointers, enqueued
+ * on `stream`, returns without synchronising); the caller still provides
+ * every input and output array.
+ *   - CS_CNN_SNS is refused with CS_EINVAL: its start predictor writes a
+ *     displacement grid this call would have to allocate. A caller that
+ *     holds a displacement grid of its own uses cs_track_dhat. field_id is
+ *     therefore never read.
+ *   - The walk's only scratch, its work cursor, lives in one fixed 256-byte
+ *     device array of this library that every GPU loading the library holds
+ *     until the process exits.
  *   - n has cs_track's range, [0, 2^31 - 2]. Nothing is allocated, ever: no
  *     cudaMalloc, cudaFree or allocating library routine is called.
  *   - The first call on a device looks up the array's device address
@@ -183,10 +226,10 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
  *     overlaps on the GPU (other streams, other contexts, other threads on the
  *     same device) race on the array: serialise them.
  */
-cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
-                           const double *u, double dt, const int32_t *start, int mode,
-                           int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
-                           int32_t *start_out, void *stream);
+cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
+                           const double *x, const double *u, double dt, const int32_t *start,
+                           int mode, int32_t *host_out, int32_t *path_len_out,
+                           uint8_t *status_out, int32_t *start_out, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Learned start predictor (Sec. 2.3 and Algorithm 2).                       */
@@ -327,12 +370,16 @@ cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
 /* arena_bytes. Requests wait in arrival order; the head request is admitted */
 /* as soon as a slot is free and the arena has room for its buffers (its     */
 /* HBM footprint: 2*dim*8 + 17 (+4 with starts) bytes per particle, plus the */
-/* prediction grid for CNN-SNS). Admitted requests run concurrently on their */
-/* streams; results are identical to cs_track_host on the same inputs.      */
-/* Meshes, grid velocities (cs_grid_velocity) and predictor weights must be  */
-/* resident before cs_serve_start and unchanged while serving. CNN-SNS      */
-/* requests run on the 2-D tensor-core predictor; where it is unavailable   */
-/* (3-D, no predictor, no grid velocity) they fall back to plain SNS.       */
+/* prediction grid for CNN-SNS, plus a grid velocity when the request names  */
+/* no field). Admitted requests run concurrently on their streams; results   */
+/* are identical to cs_track_host on the same inputs. Meshes, fields and     */
+/* predictor weights must be resident before cs_serve_start and unchanged    */
+/* while serving (mesh, field and predictor-grid changes return CS_EBUSY).   */
+/* A CNN-SNS request runs the grid predictor of its dimension (tensor cores  */
+/* in 2-D, the tile engine in 3-D, whose shared workspace serialises the 3-D */
+/* predictions while the walks still overlap) on its field's grid velocity,  */
+/* or on its own u when its particles are the mesh nodes; without a loaded  */
+/* predictor, or with neither, it falls back to plain SNS.                   */
 /* ------------------------------------------------------------------------ */
 typedef struct cs_serve_cfg {
     int32_t slots;          /* concurrent requests on the GPU (1..64)        */
@@ -341,6 +388,7 @@ typedef struct cs_serve_cfg {
 
 typedef struct cs_request {
     int32_t mesh_id;
+    int32_t field_id;       /* velocity field of CNN-SNS, or CS_NO_FIELD     */
     int64_t n;
     const double *x;        /* HOST [n][dim] (pinned memory overlaps best)   */
     const double *u;        /* HOST [n][dim]                                 */
@@ -361,7 +409,8 @@ typedef struct cs_serve_stats {
     int32_t max_concurrent;                    /* requests in flight at once */
 } cs_serve_stats;
 
-/* Start the worker (one server per context). CS_EBUSY if already serving. */
+/* Start the worker (one server per context). CS_EBUSY if already serving;
+ * CS_ENOMEM if the arena does not fit the device or the HBM budget. */
 cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg);
 
 /* Queue a request; returns at once with a ticket. The caller keeps the
@@ -386,6 +435,28 @@ cs_status cs_serve_stop(cs_ctx *ctx);
  * status 0..3. */
 cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len,
                          const uint8_t *status, int64_t out[6], void *stream);
+
+/* Error statistics of a finished tracking call (Sec. 3.1), DEVICE inputs,
+ * synchronous:
+ *   err of a particle = distance between the centroids (mean of the
+ *       vertices) of its tracking origin start[p] (the walk's start element,
+ *       cs_track's start_out) and of its host host[p]; particles where either
+ *       is -1 are skipped. start may be NULL (no err).
+ *   displacement error = |dhat[pcell(x)] * s - (x_p - x)|, the predicted
+ *       displacement at the predictor cell of x (cell units times the
+ *       predictor cell size s) against the true one, x_p = x - (u*dt);
+ *       computed only when dhat ([prod pred_grid][dim] floats, e.g. from
+ *       cs_predict) is given, and only for finite x_p.
+ * Sums are in FP64 (their order is not fixed); maxima are exact. */
+typedef struct cs_error_stats {
+    int64_t n_err;
+    double  err_sum, err_max;
+    int64_t n_disp;
+    double  disp_sum, disp_max;
+} cs_error_stats;
+cs_status cs_track_error(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                         const double *u, double dt, const int32_t *start, const int32_t *host,
+                         const float *dhat, cs_error_stats *out, void *stream);
 
 /* Launch counter: kernels this context has launched since creation. */
 int64_t cs_kernel_launches(const cs_ctx *ctx);

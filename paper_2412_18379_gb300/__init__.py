@@ -11,13 +11,14 @@ import numpy as np
 
 from . import _capi
 from ._capi import (CS_SNS, CS_CNN_SNS, CS_ASG_DIRECT, CS_FOUND, CS_OUTSIDE,
-                    CS_FOUND_VIA_FALLBACK, CS_INVALID, CS_EPS, CsError)
+                    CS_FOUND_VIA_FALLBACK, CS_INVALID, CS_EPS, CS_NO_FIELD, CsError)
 
 MODES = {"sns": CS_SNS, "cnn": CS_CNN_SNS, "cnn_sns": CS_CNN_SNS, "asg": CS_ASG_DIRECT,
          "asg_direct": CS_ASG_DIRECT}
 
-__all__ = ["Context", "Mesh", "CsError", "CS_SNS", "CS_CNN_SNS", "CS_ASG_DIRECT",
-           "CS_FOUND", "CS_OUTSIDE", "CS_FOUND_VIA_FALLBACK", "CS_INVALID", "CS_EPS"]
+__all__ = ["Context", "Mesh", "Field", "CsError", "CS_SNS", "CS_CNN_SNS", "CS_ASG_DIRECT",
+           "CS_FOUND", "CS_OUTSIDE", "CS_FOUND_VIA_FALLBACK", "CS_INVALID", "CS_EPS",
+           "CS_NO_FIELD", "check_track_args"]
 
 
 def _ptr(a):
@@ -32,6 +33,55 @@ def _stream_ptr(stream):
     if stream is None:
         return None
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_name(a):
+    return str(a.dtype).replace("torch.", "")
+
+
+def _contiguous(a):
+    if isinstance(a, np.ndarray):
+        return a.flags["C_CONTIGUOUS"]
+    return a.is_contiguous()
+
+
+def check_track_args(dim, x, u, start=None, out=None, on_device=True):
+    """Check the arrays of a tracking call before any pointer reaches the C
+    ABI, which trusts the sizes it is given: a wrong dtype, shape or stride
+    would make the kernels read or write past the arrays. x, u: contiguous
+    float64 [n, dim]; start: contiguous int32 [n]; out: contiguous host,
+    path_len (int32), status (uint8) and start (int32) with at least n
+    elements. on_device: every array must be a CUDA tensor on x's device
+    (else CPU memory). Raises ValueError; returns n."""
+    if getattr(x, "ndim", None) != 2 or x.shape[1] != dim:
+        raise ValueError("x must have shape [n, %d]" % dim)
+    n = int(x.shape[0])
+    arrays = [("x", x, "float64", (n, dim)), ("u", u, "float64", (n, dim))]
+    if start is not None:
+        arrays.append(("start", start, "int32", (n,)))
+    for key, dt in (("host", "int32"), ("path_len", "int32"), ("status", "uint8"),
+                    ("start", "int32")):
+        if out is not None and out.get(key) is not None:
+            arrays.append(("out['%s']" % key, out[key], dt, None))
+    dev = getattr(x, "device", None)
+    for name, a, dt, shape in arrays:
+        if a is None:
+            raise ValueError("%s is missing" % name)
+        if _dtype_name(a) != dt:
+            raise ValueError("%s must be %s, not %s" % (name, dt, _dtype_name(a)))
+        if not _contiguous(a):
+            raise ValueError("%s must be contiguous" % name)
+        if shape is not None and tuple(a.shape) != shape:
+            raise ValueError("%s must have shape %s, not %s" % (name, shape, tuple(a.shape)))
+        if shape is None and int(np.prod(a.shape)) < n:
+            raise ValueError("%s holds %d elements, fewer than n = %d"
+                             % (name, int(np.prod(a.shape)), n))
+        cuda = bool(getattr(a, "is_cuda", False))
+        if on_device and (not cuda or a.device != dev):
+            raise ValueError("%s must be a CUDA tensor on %s" % (name, dev))
+        if not on_device and cuda:
+            raise ValueError("%s must be in host memory" % name)
+    return n
 
 
 class Mesh:
@@ -75,13 +125,34 @@ class Mesh:
             self.id = None
 
 
-class Context:
-    """One library context on one CUDA device."""
+class Field:
+    """A velocity field of a mesh, resident on the device (cs_field_upload)."""
 
-    def __init__(self, device=0, lib_path=None):
+    def __init__(self, ctx, field_id, mesh):
+        self.ctx = ctx
+        self.id = field_id
+        self.mesh = mesh
+
+    def release(self):
+        if self.id is not None:
+            self.ctx._check(self.ctx.lib.cs_field_release(self.ctx.h, self.id))
+            self.id = None
+
+
+def _field_id(field):
+    if field is None:
+        return CS_NO_FIELD
+    return field.id if isinstance(field, Field) else int(field)
+
+
+class Context:
+    """One library context on one CUDA device; hbm_budget caps the device
+    bytes it may hold (0 = no cap)."""
+
+    def __init__(self, device=0, hbm_budget=0, lib_path=None):
         self.lib = _capi.load(lib_path)
         h = ctypes.c_void_p()
-        rc = self.lib.cs_create(ctypes.byref(h), int(device))
+        rc = self.lib.cs_create(ctypes.byref(h), int(device), int(hbm_budget))
         if rc != 0:
             raise CsError(rc, "cs_create(device=%d) failed" % device)
         self.h = h
@@ -106,6 +177,25 @@ class Context:
     @property
     def launches(self):
         return int(self.lib.cs_kernel_launches(self.h))
+
+    def memory_usage(self):
+        """(device bytes held, budget) of the context."""
+        used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+        self._check(self.lib.cs_memory_usage(self.h, ctypes.byref(used), ctypes.byref(budget)))
+        return int(used.value), int(budget.value)
+
+    def upload_field(self, mesh, u_nodal):
+        """Resident velocity field of a mesh from its nodal velocity [n_v, dim]
+        (float64 numpy array or torch tensor, host or CUDA)."""
+        if isinstance(u_nodal, np.ndarray):
+            u_nodal = np.ascontiguousarray(u_nodal, dtype=np.float64)
+        if (_dtype_name(u_nodal) != "float64" or not _contiguous(u_nodal)
+                or tuple(u_nodal.shape) != (mesh.n_vertices, mesh.dim)):
+            raise ValueError("u_nodal must be contiguous float64 [%d, %d]"
+                             % (mesh.n_vertices, mesh.dim))
+        fid = ctypes.c_int32()
+        self._check(self.lib.cs_field_upload(self.h, mesh.id, _ptr(u_nodal), ctypes.byref(fid)))
+        return Field(self, fid.value, mesh)
 
     def profile(self, on=True):
         self._check(self.lib.cs_profile_enable(self.h, 1 if on else 0))
@@ -133,71 +223,97 @@ class Context:
                                             ctypes.byref(mid)))
         return Mesh(self, mid.value, dim, xyz.shape[0], conn.shape[0])
 
-    def track(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
-              stream=None):
-        """Device path: x, u are float64 CUDA tensors [n, dim]; returns (or
-        fills `out` with) device tensors host, path_len, status[, start]."""
+    def _device_out(self, n, dev, out, start_out):
         import torch
-        n = x.shape[0]
-        dev = x.device
-        for t in (x, u):
-            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-                raise ValueError("x and u must be contiguous float64 CUDA tensors")
         if out is None:
             out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
                        path_len=torch.empty(n, dtype=torch.int32, device=dev),
                        status=torch.empty(n, dtype=torch.uint8, device=dev))
             if start_out:
                 out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
-        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        return out
+
+    def track(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
+              stream=None, field=None):
+        """Device path: x, u are float64 CUDA tensors [n, dim]; returns (or
+        fills `out` with) device tensors host, path_len, status[, start].
+        field: the Field (or id) whose grid velocity CNN-SNS predicts from."""
+        import torch
+        n = check_track_args(mesh.dim, x, u, start, out)
+        out = self._device_out(n, x.device, out, start_out)
+        check_track_args(mesh.dim, x, u, start, out)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track(
-            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
             MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
             _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start")),
             _stream_ptr(st)))
         return out
 
     def track_noalloc(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
-                      stream=None):
+                      stream=None, field=None):
         """cs_track_noalloc: like track(), but the library allocates nothing;
         pass `out` (preallocated device tensors) to keep the call allocation-
-        free on this side too. Same n range as track()."""
+        free on this side too. Same n range as track(); CNN-SNS is refused."""
         import torch
-        n = x.shape[0]
-        dev = x.device
-        if out is None:
-            out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
-                       path_len=torch.empty(n, dtype=torch.int32, device=dev),
-                       status=torch.empty(n, dtype=torch.uint8, device=dev))
-            if start_out:
-                out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
-        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        n = check_track_args(mesh.dim, x, u, start, out)
+        out = self._device_out(n, x.device, out, start_out)
+        check_track_args(mesh.dim, x, u, start, out)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track_noalloc(
-            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
             MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
             _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start")),
             _stream_ptr(st)))
         return out
 
-    def track_host(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False):
+    def track_host(self, mesh, x, u, dt, start=None, mode="sns", out=None, start_out=False,
+                   field=None):
         """Host path: numpy (or pinned torch CPU) inputs; copies in, runs,
         copies out and synchronises inside the library."""
-        n = x.shape[0]
-        if out is None:
-            out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
-                       status=np.empty(n, dtype=np.uint8))
-            if start_out:
-                out["start"] = np.empty(n, dtype=np.int32)
         if isinstance(x, np.ndarray):
             x = np.ascontiguousarray(x, dtype=np.float64)
             u = np.ascontiguousarray(u, dtype=np.float64)
             if start is not None:
                 start = np.ascontiguousarray(start, dtype=np.int32)
+        n = check_track_args(mesh.dim, x, u, start, out, on_device=False)
+        if out is None:
+            out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
+                       status=np.empty(n, dtype=np.uint8))
+            if start_out:
+                out["start"] = np.empty(n, dtype=np.int32)
+        check_track_args(mesh.dim, x, u, start, out, on_device=False)
         self._check(self.lib.cs_track_host(
-            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+            self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
             MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
             _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start"))))
         return out
+
+    def track_error(self, mesh, x, u, dt, host, start=None, dhat=None, stream=None):
+        """Error statistics (Sec. 3.1) of a finished call: mean/max origin error
+        err (centroid of the start element to centroid of the host) and, with
+        a displacement grid dhat, mean/max |dhat * s - (x_p - x)|."""
+        import torch
+        check_track_args(mesh.dim, x, u, start)
+        n = int(x.shape[0])
+        if _dtype_name(host) != "int32" or not host.is_cuda or host.numel() < n:
+            raise ValueError("host must be an int32 CUDA tensor of n elements")
+        if dhat is not None:
+            cells = int(np.prod(mesh.info()["pred_grid"]))
+            if (_dtype_name(dhat) != "float32" or not dhat.is_cuda or not dhat.is_contiguous()
+                    or dhat.numel() < cells * mesh.dim):
+                raise ValueError("dhat must be a contiguous float32 CUDA tensor [%d, %d]"
+                                 % (cells, mesh.dim))
+        res = _capi.ErrorStats()
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        self._check(self.lib.cs_track_error(self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt),
+                                            _ptr(start), _ptr(host), _ptr(dhat),
+                                            ctypes.byref(res), _stream_ptr(st)))
+        return dict(n_err=res.n_err,
+                    err_mean=res.err_sum / res.n_err if res.n_err else float("nan"),
+                    err_max=res.err_max, n_disp=res.n_disp,
+                    disp_mean=res.disp_sum / res.n_disp if res.n_disp else float("nan"),
+                    disp_max=res.disp_max)
 
     # ---------------- start predictor ----------------
     def predictor_engine(self, engine):
@@ -292,16 +408,20 @@ class Context:
 
     def track_dhat(self, mesh, x, u, dt, dhat=None, start=None, out=None, start_out=False,
                    stream=None):
+        """CNN-SNS start rule with a given displacement grid dhat (float32 CUDA
+        [prod pred_grid, dim], predictor cell units; None = the mesh's stored
+        prediction)."""
         import torch
-        n = x.shape[0]
-        dev = x.device
-        if out is None:
-            out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
-                       path_len=torch.empty(n, dtype=torch.int32, device=dev),
-                       status=torch.empty(n, dtype=torch.uint8, device=dev))
-            if start_out:
-                out["start"] = torch.empty(n, dtype=torch.int32, device=dev)
-        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        n = check_track_args(mesh.dim, x, u, start, out)
+        if dhat is not None:
+            cells = int(np.prod(mesh.info()["pred_grid"]))
+            if (_dtype_name(dhat) != "float32" or not dhat.is_cuda or not dhat.is_contiguous()
+                    or dhat.numel() < cells * mesh.dim):
+                raise ValueError("dhat must be a contiguous float32 CUDA tensor [%d, %d]"
+                                 % (cells, mesh.dim))
+        out = self._device_out(n, x.device, out, start_out)
+        check_track_args(mesh.dim, x, u, start, out)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track_dhat(
             self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(dhat),
             _ptr(out["host"]), _ptr(out["path_len"]), _ptr(out["status"]),
@@ -314,15 +434,16 @@ class Context:
         self._check(self.lib.cs_serve_start(self.h, ctypes.byref(cfg)))
         self._requests = {}
 
-    def submit(self, mesh, x, u, dt, start=None, mode="sns"):
+    def submit(self, mesh, x, u, dt, start=None, mode="sns", field=None):
         """Queue a request (host arrays, pinned torch tensors overlap best).
         Returns (ticket, outputs); outputs are valid after wait(ticket)."""
         import torch
-        n = x.shape[0]
+        n = check_track_args(mesh.dim, x, u, start, on_device=False)
         out = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
                    path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
                    status=torch.empty(n, dtype=torch.uint8).pin_memory())
-        req = _capi.Request(mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start),
+        req = _capi.Request(mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt),
+                            _ptr(start),
                             MODES[mode] if isinstance(mode, str) else int(mode),
                             _ptr(out["host"]), _ptr(out["path_len"]), _ptr(out["status"]))
         t = ctypes.c_int64()

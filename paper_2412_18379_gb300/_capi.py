@@ -15,6 +15,7 @@ CS_OK = 0
 CS_SNS, CS_CNN_SNS, CS_ASG_DIRECT = 0, 1, 2
 CS_FOUND, CS_OUTSIDE, CS_FOUND_VIA_FALLBACK, CS_INVALID = 0, 1, 2, 3
 CS_EPS = 1e-12
+CS_NO_FIELD = -1
 
 ERRORS = {
     -1: "CS_EINVAL", -2: "CS_ENOMEM", -3: "CS_ENOMESH", -4: "CS_EBUSY",
@@ -48,7 +49,11 @@ class MeshInfo(ctypes.Structure):
 
 # name -> (restype, argtypes); every symbol include/cnnsns.h declares
 SIGNATURES = {
-    "cs_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_int]),
+    "cs_create": (_i32, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t]),
+    "cs_memory_usage": (_i32, [_vp, ctypes.POINTER(ctypes.c_size_t),
+                               ctypes.POINTER(ctypes.c_size_t)]),
+    "cs_field_upload": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_i32)]),
+    "cs_field_release": (_i32, [_vp, _i32]),
     "cs_destroy": (None, [_vp]),
     "cs_last_error": (ctypes.c_char_p, [_vp]),
     "cs_mesh_upload": (_i32, [_vp, ctypes.c_int, _i64, _vp, _i64, _vp, _vp,
@@ -57,12 +62,12 @@ SIGNATURES = {
     "cs_mesh_query": (_i32, [_vp, _i32, ctypes.POINTER(MeshInfo)]),
     "cs_node_start_elements": (_i32, [_vp, _i32, _vp]),
     "cs_seed_grid": (_i32, [_vp, _i32, _vp]),
-    "cs_track": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp, _vp,
-                        _vp, _vp]),
-    "cs_track_host": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp,
-                             _vp, _vp]),
-    "cs_track_noalloc": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp,
-                                _vp, _vp, _vp]),
+    "cs_track": (_i32, [_vp, _i32, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp, _vp,
+                        _vp, _vp, _vp]),
+    "cs_track_host": (_i32, [_vp, _i32, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp,
+                             _vp, _vp, _vp]),
+    "cs_track_noalloc": (_i32, [_vp, _i32, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp,
+                                _vp, _vp, _vp, _vp]),
     "cs_track_stats": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp]),
     "cs_kernel_launches": (_i64, [_vp]),
     "cs_predictor_precision": (_i32, [_vp, ctypes.c_int]),
@@ -95,7 +100,8 @@ class ServeCfg(ctypes.Structure):
 
 
 class Request(ctypes.Structure):
-    _fields_ = [("mesh_id", _i32), ("n", _i64), ("x", _vp), ("u", _vp), ("dt", _dbl),
+    _fields_ = [("mesh_id", _i32), ("field_id", _i32), ("n", _i64), ("x", _vp), ("u", _vp),
+                ("dt", _dbl),
                 ("start", _vp), ("mode", _i32), ("host_out", _vp), ("path_len_out", _vp),
                 ("status_out", _vp)]
 
@@ -114,6 +120,15 @@ SIGNATURES.update({
     "cs_serve_report": (_i32, [_vp, ctypes.POINTER(ServeStats)]),
     "cs_serve_stop": (_i32, [_vp]),
 })
+
+
+class ErrorStats(ctypes.Structure):
+    _fields_ = [("n_err", _i64), ("err_sum", _dbl), ("err_max", _dbl), ("n_disp", _i64),
+                ("disp_sum", _dbl), ("disp_max", _dbl)]
+
+
+SIGNATURES["cs_track_error"] = (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp,
+                                       ctypes.POINTER(ErrorStats), _vp])
 
 
 class Profile(ctypes.Structure):

@@ -28,8 +28,9 @@ template <class T>
 cs_status dev_copy(cs_ctx *ctx, cs::Mesh *m, const T *src, size_t count, T **dst) {
     void *p = nullptr;
     const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) return fail(ctx, CS_ENOMEM, "cudaMalloc of mesh data failed");
+    cs_status rc = cs::dmalloc(ctx, &p, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
     m->allocs.push_back(p);
     m->info.device_bytes += bytes;
     if (count && src) {
@@ -43,9 +44,27 @@ cs_status dev_copy(cs_ctx *ctx, cs::Mesh *m, const T *src, size_t count, T **dst
     return CS_OK;
 }
 
-void free_mesh(cs::Mesh *m) {
-    for (void *p : m->allocs) cudaFree(p);
+void free_mesh(cs_ctx *ctx, cs::Mesh *m) {
+    for (void *p : m->allocs) cs::dfree(ctx, p);
     delete m;
+}
+
+void free_field(cs_ctx *ctx, cs::Field *f) {
+    cs::dfree(ctx, f->u_nodal);
+    cs::dfree(ctx, f->grid_u);
+    delete f;
+}
+
+// release the fields of one mesh (mesh_id) or of every mesh (0)
+void release_fields(cs_ctx *ctx, int32_t mesh_id) {
+    for (auto it = ctx->fields.begin(); it != ctx->fields.end();) {
+        if (mesh_id == 0 || it->second->mesh_id == mesh_id) {
+            free_field(ctx, it->second);
+            it = ctx->fields.erase(it);
+        } else {
+            ++it;
+        }
+    }
 }
 
 cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
@@ -56,9 +75,9 @@ cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
 cs_status ensure_scratch(cs_ctx *ctx) {
     cs::Scratch &s = ctx->scratch;
     if (!s.counters) {
-        if (cudaMalloc(&s.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
-            cudaMalloc(&s.stats, 8 * sizeof(int64_t)) != cudaSuccess)
-            return fail(ctx, CS_ENOMEM, "cudaMalloc of scratch counters failed");
+        cs_status rc = cs::dmalloc_n(ctx, &s.counters, 16);
+        if (rc == CS_OK) rc = cs::dmalloc_n(ctx, &s.stats, 16);
+        if (rc) return rc;
         // the walk cursors start at zero; each walk then zeroes the other one
         if (cudaMemset(s.counters, 0, 16 * sizeof(int32_t)) != cudaSuccess)
             return fail(ctx, CS_ECUDA, "cudaMemset of scratch counters failed");
@@ -68,9 +87,46 @@ cs_status ensure_scratch(cs_ctx *ctx) {
 
 }  // namespace
 
+cs_status cs::dmalloc(cs_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(ctx->hbm_mu);
+        if (ctx->hbm_budget && ctx->hbm_used + bytes > ctx->hbm_budget)
+            return fail(ctx, CS_ENOMEM, "device allocation of " + std::to_string(bytes) +
+                                            " bytes would pass the context's HBM budget (" +
+                                            std::to_string(ctx->hbm_used) + " of " +
+                                            std::to_string(ctx->hbm_budget) + " bytes in use)");
+        ctx->hbm_used += bytes;   // reserved while cudaMalloc runs
+    }
+    void *q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lock(ctx->hbm_mu);
+        ctx->hbm_used -= bytes;
+        return fail(ctx, CS_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    std::lock_guard<std::mutex> lock(ctx->hbm_mu);
+    ctx->hbm_blocks[q] = bytes;
+    *p = q;
+    return CS_OK;
+}
+
+void cs::dfree(cs_ctx *ctx, void *p) {
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(ctx->hbm_mu);
+        auto it = ctx->hbm_blocks.find(p);
+        if (it != ctx->hbm_blocks.end()) {
+            ctx->hbm_used -= it->second;
+            ctx->hbm_blocks.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
 extern "C" {
 
-cs_status cs_create(cs_ctx **out, int cuda_device) {
+cs_status cs_create(cs_ctx **out, int cuda_device, size_t hbm_budget_bytes) {
     if (!out) return CS_EINVAL;
     *out = nullptr;
     int count = 0;
@@ -79,6 +135,7 @@ cs_status cs_create(cs_ctx **out, int cuda_device) {
     cs_ctx *ctx = new (std::nothrow) cs_ctx();
     if (!ctx) return CS_ENOMEM;
     ctx->device = cuda_device;
+    ctx->hbm_budget = hbm_budget_bytes;
     if (cudaSetDevice(cuda_device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cuda_device) !=
             cudaSuccess) {
@@ -93,12 +150,13 @@ void cs_destroy(cs_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cs::serve_release(ctx);
-    for (auto &kv : ctx->meshes) free_mesh(kv.second);
-    for (auto &p : ctx->pred) cs::predictor_release(p);
-    if (ctx->dev_err) cudaFree(ctx->dev_err);
-    if (ctx->scratch.counters) cudaFree(ctx->scratch.counters);
-    if (ctx->scratch.stats) cudaFree(ctx->scratch.stats);
-    if (ctx->scratch.stage) cudaFree(ctx->scratch.stage);
+    release_fields(ctx, 0);
+    for (auto &kv : ctx->meshes) free_mesh(ctx, kv.second);
+    for (auto &p : ctx->pred) cs::predictor_release(ctx, p);
+    cs::dfree(ctx, ctx->dev_err);
+    cs::dfree(ctx, ctx->scratch.counters);
+    cs::dfree(ctx, ctx->scratch.stats);
+    cs::dfree(ctx, ctx->scratch.stage);
     for (const auto &r : ctx->prof.pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -110,6 +168,14 @@ void cs_destroy(cs_ctx *ctx) {
 const char *cs_last_error(const cs_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 int64_t cs_kernel_launches(const cs_ctx *ctx) { return ctx ? ctx->launches.load() : 0; }
+
+cs_status cs_memory_usage(cs_ctx *ctx, size_t *used_bytes, size_t *budget_bytes) {
+    if (!ctx) return CS_EINVAL;
+    std::lock_guard<std::mutex> lock(ctx->hbm_mu);
+    if (used_bytes) *used_bytes = ctx->hbm_used;
+    if (budget_bytes) *budget_bytes = ctx->hbm_budget;
+    return CS_OK;
+}
 
 cs_status cs_profile_enable(cs_ctx *ctx, int on) {
     if (!ctx) return CS_EINVAL;
@@ -156,6 +222,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     }
     if (rc != CS_OK) return fail(ctx, rc, "cs_mesh_upload: " + msg);
 
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_mesh_upload: stop serving first");
     cs::Mesh *m = new (std::nothrow) cs::Mesh();
     if (!m) return fail(ctx, CS_ENOMEM, "host allocation failed");
     cs::DevMesh &d = m->d;
@@ -178,7 +245,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         (rc = dev_copy(ctx, m, H.bitems.data(), H.bitems.size(), &bitems)) ||
         (rc = dev_copy(ctx, m, H.conn.data(), H.conn.size(), &cn)) ||
         (rc = dev_copy(ctx, m, H.centroid.data(), H.centroid.size(), &cent))) {
-        free_mesh(m);
+        free_mesh(ctx, m);
         return rc;
     }
     int64_t n_asg = 1, n_b = 1;
@@ -187,7 +254,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         n_b *= H.gb[k];
     }
     if ((rc = dev_copy<int32_t>(ctx, m, nullptr, size_t(n_asg), &seed))) {
-        free_mesh(m);
+        free_mesh(ctx, m);
         return rc;
     }
     d.recw = recw;
@@ -234,7 +301,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
-        free_mesh(m);
+        free_mesh(ctx, m);
         return cuda_fail(ctx, e, "seed grid kernel");
     }
 
@@ -266,10 +333,63 @@ cs_status cs_mesh_release(cs_ctx *ctx, int32_t mesh_id) {
     if (!ctx) return CS_EINVAL;
     cs::Mesh *m = find_mesh(ctx, mesh_id);
     if (!m) return fail(ctx, CS_ENOMESH, "cs_mesh_release: unknown mesh id");
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_mesh_release: stop serving first");
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    release_fields(ctx, mesh_id);
     ctx->meshes.erase(mesh_id);
-    free_mesh(m);
+    free_mesh(ctx, m);
+    return CS_OK;
+}
+
+cs_status cs_field_upload(cs_ctx *ctx, int32_t mesh_id, const double *u_nodal,
+                          int32_t *field_id_out) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_field_upload: unknown mesh id");
+    if (!u_nodal || !field_id_out) return fail(ctx, CS_EINVAL, "cs_field_upload: null pointer");
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_field_upload: stop serving first");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs::Field *f = new (std::nothrow) cs::Field();
+    if (!f) return fail(ctx, CS_ENOMEM, "host allocation failed");
+    f->mesh_id = mesh_id;
+    const size_t bytes = size_t(m->d.n_v) * m->d.dim * sizeof(double);
+    cs_status rc = cs::dmalloc_n(ctx, &f->u_nodal, size_t(m->d.n_v) * m->d.dim);
+    if (rc) {
+        free_field(ctx, f);
+        return rc;
+    }
+    // host or device source (cudaMemcpyDefault: unified addressing tells which)
+    cudaError_t e = cudaMemcpy(f->u_nodal, u_nodal, bytes, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        free_field(ctx, f);
+        return cuda_fail(ctx, e, "cs_field_upload: copy of the nodal velocity");
+    }
+    const float *grid = nullptr;
+    rc = cs::field_grid(ctx, m, f, nullptr, &grid);
+    if (rc == CS_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cs_field_upload: resample");
+    }
+    if (rc) {
+        free_field(ctx, f);
+        return rc;
+    }
+    const int32_t id = ctx->next_field++;
+    ctx->fields[id] = f;
+    *field_id_out = id;
+    return CS_OK;
+}
+
+cs_status cs_field_release(cs_ctx *ctx, int32_t field_id) {
+    if (!ctx) return CS_EINVAL;
+    auto it = ctx->fields.find(field_id);
+    if (it == ctx->fields.end()) return fail(ctx, CS_EINVAL, "cs_field_release: unknown field id");
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_field_release: stop serving first");
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    free_field(ctx, it->second);
+    ctx->fields.erase(it);
     return CS_OK;
 }
 
@@ -303,8 +423,8 @@ cs_status cs_seed_grid(cs_ctx *ctx, int32_t mesh_id, int32_t *out) {
     return CS_OK;
 }
 
-cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, const double *u,
-                   double dt, const int32_t *start, int mode, int32_t *host_out,
+cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n, const double *x,
+                   const double *u, double dt, const int32_t *start, int mode, int32_t *host_out,
                    int32_t *path_len_out, uint8_t *status_out, int32_t *start_out,
                    void *stream) {
     if (!ctx) return CS_EINVAL;
@@ -312,19 +432,36 @@ cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x, con
     if (!m) return fail(ctx, CS_ENOMESH, "cs_track: unknown mesh id");
     if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS)
         return fail(ctx, CS_EINVAL, "cs_track: unknown mode");
+    if (n < 0 || n >= (int64_t(1) << 31) - 1)
+        return fail(ctx, CS_EINVAL, "cs_track: n is outside [0, 2^31 - 2]");
     const float *dhat = nullptr;
     if (mode == CS_CNN_SNS) {
         if (!ctx->pred[m->d.dim - 2].loaded)
             return fail(ctx, CS_ENOPRED, "cs_track: no predictor loaded");
+        cs::Field *f = nullptr;
+        if (field_id != CS_NO_FIELD) {
+            auto it = ctx->fields.find(field_id);
+            if (it == ctx->fields.end() || it->second->mesh_id != mesh_id)
+                return fail(ctx, CS_EINVAL, "cs_track: field id is not a field of this mesh");
+            f = it->second;
+        }
         if (n == 0) return CS_OK;
         if (!x || !u) return fail(ctx, CS_EINVAL, "cs_track: null pointer");
-        CS_CUDA(ctx, cudaSetDevice(ctx->device));
-        // particles at the mesh nodes: their velocities are the nodal field
+        // without a field, the particles must be the mesh nodes: their
+        // velocities are then the nodal field
         const bool nodes = !start && n == m->d.n_v;
-        if (!nodes && !m->grid_u_valid)
-            return fail(ctx, CS_EINVAL, "cs_track: CNN-SNS needs cs_grid_velocity first");
-        cs_status rc = cs::cnn_prepare(ctx, m, nodes ? u : nullptr, dt,
-                                       static_cast<cudaStream_t>(stream), &dhat);
+        if (!f && !nodes)
+            return fail(ctx, CS_EINVAL,
+                        "cs_track: CNN-SNS needs a field id (cs_field_upload) unless the "
+                        "particles are the mesh nodes");
+        CS_CUDA(ctx, cudaSetDevice(ctx->device));
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const float *grid = nullptr;
+        if (f) {
+            cs_status rc = cs::field_grid(ctx, m, f, st, &grid);
+            if (rc) return rc;
+        }
+        cs_status rc = cs::cnn_prepare(ctx, m, grid, f ? nullptr : u, dt, st, &dhat);
         if (rc) return rc;
     }
     return cs::cs_track_impl(ctx, m, n, x, u, dt, start, mode, dhat, host_out, path_len_out,
@@ -366,9 +503,9 @@ cs_status cs::cs_track_impl(cs_ctx *ctx, cs::Mesh *m, int64_t n, const double *x
 
 extern "C" {
 
-cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
-                        const double *u, double dt, const int32_t *start, int mode,
-                        int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
+                        const double *x, const double *u, double dt, const int32_t *start,
+                        int mode, int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                         int32_t *start_out) {
     if (!ctx) return CS_EINVAL;
     cs::Mesh *m = find_mesh(ctx, mesh_id);
@@ -383,11 +520,11 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
     const size_t total = 2 * in_b + size_t(n) * (4 + 4 + 4 + 4 + 1) + 256;
     cs::Scratch &S = ctx->scratch;
     if (S.stage_cap < total) {
-        if (S.stage) cudaFree(S.stage);
+        cs::dfree(ctx, S.stage);
         S.stage = nullptr;
         S.stage_cap = 0;
-        if (cudaMalloc(&S.stage, total) != cudaSuccess)
-            return fail(ctx, CS_ENOMEM, "cs_track_host: device staging allocation failed");
+        cs_status rc = cs::dmalloc_n(ctx, &S.stage, total);
+        if (rc) return rc;
         S.stage_cap = total;
     }
     char *buf = S.stage;
@@ -403,7 +540,7 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
     if (e == cudaSuccess && start)
         e = cudaMemcpyAsync(ds, start, size_t(n) * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host: copy in");
-    rc = cs_track(ctx, mesh_id, n, dx, du, dt, start ? ds : nullptr, mode, dh, dp, dst,
+    rc = cs_track(ctx, mesh_id, field_id, n, dx, du, dt, start ? ds : nullptr, mode, dh, dp, dst,
                   start_out ? dso : nullptr, st);
     if (rc == CS_OK) {
         e = cudaMemcpyAsync(host_out, dh, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
@@ -430,6 +567,36 @@ cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len, const 
     CS_CUDA(ctx, cudaMemcpyAsync(out, ctx->scratch.stats, 6 * sizeof(int64_t),
                                  cudaMemcpyDeviceToHost, st));
     CS_CUDA(ctx, cudaStreamSynchronize(st));
+    return CS_OK;
+}
+
+cs_status cs_track_error(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                         const double *u, double dt, const int32_t *start, const int32_t *host,
+                         const float *dhat, cs_error_stats *out, void *stream) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_error: unknown mesh id");
+    if (!out || n < 0 || (n > 0 && (!host || (dhat && (!x || !u)))))
+        return fail(ctx, CS_EINVAL, "cs_track_error: bad arguments");
+    CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs_status rc = ensure_scratch(ctx);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *sums = reinterpret_cast<double *>(ctx->scratch.stats + 8);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(ctx->scratch.stats + 12);
+    ctx->launches += cs::launch_error_stats(m->d, n, start, host, x, u, dt, dhat, sums, cnt,
+                                            ctx->sm_count, st);
+    double h[4];
+    unsigned long long c[2];
+    CS_CUDA(ctx, cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CS_CUDA(ctx, cudaMemcpyAsync(c, cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CS_CUDA(ctx, cudaStreamSynchronize(st));
+    out->n_err = int64_t(c[0]);
+    out->err_sum = h[0];
+    out->err_max = h[1];
+    out->n_disp = int64_t(c[1]);
+    out->disp_sum = h[2];
+    out->disp_max = h[3];
     return CS_OK;
 }
 

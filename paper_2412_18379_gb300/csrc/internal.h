@@ -6,7 +6,9 @@
 #include <atomic>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "cnnsns.h"
@@ -106,11 +108,21 @@ struct Mesh {
     cs_mesh_info info{};
     std::vector<void *> allocs;
     std::vector<int32_t> node_elem_user;  // host copy, user ids
-    float *grid_u = nullptr;              // [n_asg][dim] grid velocity (CNN input)
-    float *grid_dhat = nullptr;           // [n_asg][dim] predicted displacement
-    int32_t *interp_node = nullptr;       // [n_asg][dim+1] P1 interpolation at cell centres:
+    float *grid_u = nullptr;              // [n_pasg][dim] stored grid velocity (CNN input)
+    float *grid_dhat = nullptr;           // [n_pasg][dim] predicted displacement
+    int32_t *interp_node = nullptr;       // [n_pasg][dim+1] P1 interpolation at cell centres:
     float *interp_w = nullptr;            //   host vertices and weights (static per mesh)
     bool grid_u_valid = false;
+    int32_t pgrid_version = 0;            // bumped by every cs_predictor_grid
+};
+
+// A velocity field of a mesh (cs_field_upload): the nodal velocity, kept for
+// re-resampling, and its grid velocity on the mesh's current predictor grid.
+struct Field {
+    int32_t mesh_id = 0;
+    double *u_nodal = nullptr;            // [n_v][dim]
+    float *grid_u = nullptr;              // [n_pasg][dim]
+    int32_t grid_version = -1;            // Mesh::pgrid_version grid_u was built for
 };
 
 // The start predictor of one dimension: FP32 master weights, gradients, Adam
@@ -132,7 +144,7 @@ struct Predictor {
           *tgt = nullptr;
     int64_t *idx = nullptr;
     std::vector<float *> tiles;  // workspace of the tile engine (fully convolutional)
-    int64_t tiles_key = -1;      // (tile side, tiles per pass) it was sized for
+    std::vector<int64_t> tiles_cap;   // floats held by each buffer of `tiles`
     uint8_t *packed = nullptr;   // weights in the tensor-core kernel's layout
     bool packed_dirty = true;
 };
@@ -219,6 +231,9 @@ int launch_track(const DevMesh &m, const TrackArgs &a, Scratch &s, int sm_count,
 int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st);
 int launch_stats(int64_t n, const int32_t *path, const uint8_t *status, int64_t *out,
                  int sm_count, cudaStream_t st);
+int launch_error_stats(const DevMesh &m, int64_t n, const int32_t *start, const int32_t *host,
+                       const double *x, const double *u, double dt, const float *dhat,
+                       double *out, unsigned long long *cnt, int sm_count, cudaStream_t st);
 
 }  // namespace cs
 
@@ -228,6 +243,14 @@ struct cs_ctx {
     std::string err;
     std::map<int32_t, cs::Mesh *> meshes;
     int32_t next_mesh = 1;
+    std::map<int32_t, cs::Field *> fields;
+    int32_t next_field = 1;
+    // device memory held by the context: every allocation goes through
+    // cs::dmalloc, which refuses one that would pass the budget (0 = none)
+    size_t hbm_budget = 0;
+    size_t hbm_used = 0;
+    std::unordered_map<void *, size_t> hbm_blocks;
+    std::mutex hbm_mu;
     cs::Scratch scratch;
     cs::Profiler prof;
     cs::Predictor pred[2];   // dim 2, dim 3
@@ -239,16 +262,43 @@ struct cs_ctx {
 };
 
 namespace cs {
+// Device memory of a context (api.cpp). dmalloc fails with CS_ENOMEM when
+// cudaMalloc fails or the block would take the context past its HBM budget;
+// dfree releases a block dmalloc returned (null is ignored).
+cs_status dmalloc(cs_ctx *ctx, void **p, size_t bytes);
+void dfree(cs_ctx *ctx, void *p);
+template <class T>
+cs_status dmalloc_n(cs_ctx *ctx, T **p, size_t count) {
+    void *q = nullptr;
+    const cs_status rc = dmalloc(ctx, &q, (count ? count : 1) * sizeof(T));
+    *p = static_cast<T *>(q);
+    return rc;
+}
+// The grid velocity of a field on its mesh's current predictor grid,
+// resampled (allocating) if the predictor grid changed since (predictor.cpp).
+cs_status field_grid(cs_ctx *ctx, Mesh *m, Field *f, cudaStream_t st, const float **grid_out);
 // shared body of cs_track / cs_track_dhat (api.cpp)
 cs_status cs_track_impl(cs_ctx *ctx, Mesh *m, int64_t n, const double *x, const double *u,
                         double dt, const int32_t *start, int mode, const float *dhat,
                         int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                         int32_t *start_out, cudaStream_t stream);
 // predictor.cpp
-void predictor_release(Predictor &P);
-cs_status predict_grid(cs_ctx *ctx, Mesh *m, double dt, float *dhat, cudaStream_t st);
+void predictor_release(cs_ctx *ctx, Predictor &P);
+// prediction at every predictor cell of m from the grid velocity `grid`
+cs_status predict_grid(cs_ctx *ctx, Mesh *m, const float *grid, double dt, float *dhat,
+                       cudaStream_t st);
+// grow the 3-D tile engine's workspace for mesh m (no-op in 2-D)
+cs_status reserve_tiles(cs_ctx *ctx, Mesh *m);
+// make resident what serving's start predictors read (packed 2-D weights,
+// 3-D tile workspace for every mesh, interpolation tables, field grids)
+cs_status prepare_serving(cs_ctx *ctx);
+// true when a CNN-SNS request on mesh m can run its predictor while serving
+bool serving_predictor_ready(cs_ctx *ctx, const Mesh *m);
 // serve.cpp
 void serve_release(cs_ctx *ctx);
-cs_status cnn_prepare(cs_ctx *ctx, Mesh *m, const double *u_nodal, double dt, cudaStream_t st,
-                      const float **dhat_out);
+// CNN-SNS start predictions of mesh m into m->grid_dhat: from the grid velocity
+// `grid` if given, else from the nodal velocity u_nodal, resampled into the
+// mesh's stored grid velocity
+cs_status cnn_prepare(cs_ctx *ctx, Mesh *m, const float *grid, const double *u_nodal, double dt,
+                      cudaStream_t st, const float **dhat_out);
 }  // namespace cs

@@ -60,37 +60,32 @@ cs_status fail(cs_ctx *ctx, cs_status code, const std::string &msg) {
 
 template <class T>
 cs_status dalloc(cs_ctx *ctx, T **p, size_t count) {
-    if (cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T)) !=
-        cudaSuccess) {
-        *p = nullptr;
-        return fail(ctx, CS_ENOMEM, "cudaMalloc failed in the predictor");
-    }
-    return CS_OK;
+    return dmalloc_n(ctx, p, count);
 }
 
-void free_workspace(Predictor &P) {
-    for (float *p : P.col) cudaFree(p);
-    for (float *p : P.z) cudaFree(p);
-    for (float *p : P.y) cudaFree(p);
+void free_workspace(cs_ctx *ctx, Predictor &P) {
+    for (float *p : P.col) dfree(ctx, p);
+    for (float *p : P.z) dfree(ctx, p);
+    for (float *p : P.y) dfree(ctx, p);
     P.col.clear();
     P.z.clear();
     P.y.clear();
     float **fs[] = {&P.z5, &P.a5, &P.out, &P.gout, &P.dcol, &P.dy0, &P.dy1, &P.da5, &P.win, &P.tgt};
     for (float **f : fs) {
-        if (*f) cudaFree(*f);
+        dfree(ctx, *f);
         *f = nullptr;
     }
-    if (P.idx) cudaFree(P.idx);
+    dfree(ctx, P.idx);
     P.idx = nullptr;
     P.cap = 0;
-    for (float *p : P.tiles) cudaFree(p);
+    for (float *p : P.tiles) dfree(ctx, p);
     P.tiles.clear();
-    P.tiles_key = -1;
+    P.tiles_cap.clear();
 }
 
 cs_status ensure_workspace(cs_ctx *ctx, Predictor &P, int64_t B) {
     if (P.cap >= B) return CS_OK;
-    free_workspace(P);
+    free_workspace(ctx, P);
     NetShape S(P.dim);
     int Si = S.S0, C = S.cin;
     int64_t max_col = 0, max_dy = 0;
@@ -249,14 +244,14 @@ cs_status ensure_mesh_grid(cs_ctx *ctx, cs::Mesh *m) {
 
 namespace cs {
 
-void predictor_release(Predictor &P) {
-    free_workspace(P);
+void predictor_release(cs_ctx *ctx, Predictor &P) {
+    free_workspace(ctx, P);
     float **fs[] = {&P.w, &P.g, &P.m, &P.v, &P.loss};
     for (float **f : fs) {
-        if (*f) cudaFree(*f);
+        dfree(ctx, *f);
         *f = nullptr;
     }
-    if (P.packed) cudaFree(P.packed);
+    dfree(ctx, P.packed);
     P.packed = nullptr;
     P.packed_dirty = true;
     P.loaded = false;
@@ -267,59 +262,91 @@ void predictor_release(Predictor &P) {
 // side T + 2 R through the window engine's layers (convolutions as implicit
 // GEMMs fused with bias and ReLU), so the convolutions are shared between
 // neighbouring cells instead of being recomputed for each cell's own window.
-cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float *dhat,
-                        cudaStream_t st) {
-    const DevMesh pv = pred_view(m->d);
+struct TilePlan {
+    int T = 1, nt[3] = {1, 1, 1};
+    int64_t n_tiles = 1, Bt = 1;
+    std::vector<int64_t> per;   // floats per tile of each workspace buffer
+};
+
+TilePlan plan_tiles(const DevMesh &pv) {
     const int D = pv.dim;
     NetShape S(D);
     const int R = S.n_conv;
-    int T = 1, nt[3] = {1, 1, 1};
+    TilePlan t;
     for (int k = 0; k < D; ++k) {
         const int n = (pv.ga[k] + 23) / 24;            // tiles of at most 24 cells per axis
-        T = std::max(T, (pv.ga[k] + n - 1) / n);
+        t.T = std::max(t.T, (pv.ga[k] + n - 1) / n);
     }
-    for (int k = 0; k < D; ++k) nt[k] = (pv.ga[k] + T - 1) / T;
-    const int64_t n_tiles = int64_t(nt[0]) * nt[1] * nt[2];
+    for (int k = 0; k < D; ++k) t.nt[k] = (pv.ga[k] + t.T - 1) / t.T;
+    t.n_tiles = int64_t(t.nt[0]) * t.nt[1] * t.nt[2];
     // buffer sizes per tile: input, then (col, z, y) per conv layer, z5, a5, out
-    std::vector<int64_t> per;
-    int Si = T + 2 * R, C = S.cin;
-    per.push_back(int64_t(C) * S.positions(Si));
+    int Si = t.T + 2 * R, C = S.cin;
+    t.per.push_back(int64_t(C) * S.positions(Si));
     for (int l = 0; l < S.n_conv; ++l) {
         // (col, z, y): the fused convolution needs neither an im2col copy nor
         // the pre-activation, so only y has a size
         const int64_t Po = S.positions(Si - 2);
-        per.push_back(1);
-        per.push_back(1);
-        per.push_back(Po * S.ch);
+        t.per.push_back(1);
+        t.per.push_back(1);
+        t.per.push_back(Po * S.ch);
         Si -= 2;
         C = S.ch;
     }
-    const int64_t P_out = S.positions(T);
-    per.push_back(1);                 // z5, a5: the fused head keeps them in registers
-    per.push_back(1);
-    per.push_back(P_out * D);
+    t.per.push_back(1);                 // z5, a5: the fused head keeps them in registers
+    t.per.push_back(1);
+    t.per.push_back(S.positions(t.T) * D);
     int64_t tile_floats = 0;
-    for (int64_t v : per) tile_floats += v;
-    const int64_t Bt = std::max<int64_t>(1, std::min<int64_t>(n_tiles, (int64_t(1) << 28) / tile_floats));
-    const int64_t key = int64_t(T) * 1000000 + Bt * 10 + D;
-    if (P.tiles_key != key) {
-        for (float *p : P.tiles) cudaFree(p);
-        P.tiles.clear();
-        P.tiles_key = -1;
-        for (int64_t v : per) {
-            float *b = nullptr;
-            cs_status rc = dalloc(ctx, &b, size_t(v * Bt));
-            if (rc) return rc;
-            P.tiles.push_back(b);
+    for (int64_t v : t.per) tile_floats += v;
+    t.Bt = std::max<int64_t>(1, std::min<int64_t>(t.n_tiles, (int64_t(1) << 28) / tile_floats));
+    return t;
+}
+
+// Grow the tile workspace to hold plan t (buffers only grow, so a workspace
+// sized for every mesh of a serving run is never reallocated while in use).
+cs_status grow_tiles(cs_ctx *ctx, Predictor &P, const TilePlan &t) {
+    std::vector<int64_t> need(t.per.size());
+    for (size_t i = 0; i < t.per.size(); ++i) need[i] = t.per[i] * t.Bt;
+    bool fits = P.tiles.size() == need.size() && int64_t(P.tiles_cap.size()) == int64_t(need.size());
+    for (size_t i = 0; fits && i < need.size(); ++i) fits = P.tiles_cap[i] >= need[i];
+    if (fits) return CS_OK;
+    std::vector<int64_t> cap(need.size());
+    for (size_t i = 0; i < need.size(); ++i)
+        cap[i] = std::max(need[i], i < P.tiles_cap.size() ? P.tiles_cap[i] : int64_t(0));
+    for (float *p : P.tiles) dfree(ctx, p);
+    P.tiles.clear();
+    P.tiles_cap.clear();
+    for (int64_t v : cap) {
+        float *b = nullptr;
+        cs_status rc = dalloc(ctx, &b, size_t(v));
+        if (rc) {
+            for (float *p : P.tiles) dfree(ctx, p);
+            P.tiles.clear();
+            return rc;
         }
-        P.tiles_key = key;
+        P.tiles.push_back(b);
     }
+    P.tiles_cap = cap;
+    return CS_OK;
+}
+
+cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, const float *grid, double dt,
+                        float *dhat, cudaStream_t st) {
+    const DevMesh pv = pred_view(m->d);
+    const int D = pv.dim;
+    NetShape S(D);
+    const int R = S.n_conv;
+    const TilePlan tp = plan_tiles(pv);
+    cs_status rc = grow_tiles(ctx, P, tp);
+    if (rc) return rc;
+    const int T = tp.T;
+    const int64_t n_tiles = tp.n_tiles, Bt = tp.Bt;
+    const int64_t P_out = S.positions(T);
     float scale[3] = {0, 0, 0};
     for (int k = 0; k < D; ++k) scale[k] = float(dt / pv.sa[k]);
     const int sm = ctx->sm_count;
     for (int64_t t0 = 0; t0 < n_tiles; t0 += Bt) {
         const int64_t B = std::min(Bt, n_tiles - t0);
-        ctx->launches += launch_tile_input(pv, m->grid_u, T, R, nt[0], nt[1], t0, B, scale,
+        ctx->launches += launch_tile_input(pv, grid, T, R, tp.nt[0], tp.nt[1], t0, B, scale,
                                            P.tiles[0], sm, st);
         const float *x = P.tiles[0];
         bool chfirst = true;
@@ -334,23 +361,21 @@ cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, double dt, float
             Sl -= 2;
         }
         const int f1 = S.n_conv, f2 = S.n_conv + 1;
-        float *z5 = P.tiles[1 + 3 * S.n_conv], *a5 = P.tiles[2 + 3 * S.n_conv],
-              *out = P.tiles[3 + 3 * S.n_conv];
+        float *out = P.tiles[3 + 3 * S.n_conv];
         const int64_t M = B * P_out;
-        (void)z5;
-        (void)a5;
         ctx->launches += launch_head(D, x, P.w + S.w_off[f1], P.w + S.b_off[f1], P.w + S.w_off[f2],
                                      P.w + S.b_off[f2], M, out, sm, st);
-        ctx->launches += launch_tile_scatter(pv, T, nt[0], nt[1], t0, B, out, dhat, sm, st);
+        ctx->launches += launch_tile_scatter(pv, T, tp.nt[0], tp.nt[1], t0, B, out, dhat, sm, st);
     }
     return CS_OK;
 }
 
-// prediction of every ASG cell of mesh m from its stored grid velocity
-cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStream_t st) {
+// prediction at every predictor cell of mesh m from the grid velocity `grid`
+cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, float *dhat,
+                       cudaStream_t st) {
     Predictor *P = get_pred(ctx, m->d.dim);
     if (!P || !P->loaded) return fail(ctx, CS_ENOPRED, "no predictor loaded for this dimension");
-    if (!m->grid_u_valid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
+    if (!grid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
     if (m->d.dim == 2 && ctx->engine == 1) {
         // tensor-core grid kernel: weights repacked after every load / training
         if (!P->packed) {
@@ -366,11 +391,11 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
             ctx->launches += launch_pack_tc(P->w, NetShape(2), P->packed, st);
             P->packed_dirty = false;
         }
-        ctx->launches += launch_cnn2d_tc(pred_view(m->d), m->grid_u, dt, P->packed, dhat, ctx->dev_err,
+        ctx->launches += launch_cnn2d_tc(pred_view(m->d), grid, dt, P->packed, dhat, ctx->dev_err,
                                          ctx->sm_count, ctx->tc_tile_rows, st);
         return CS_OK;
     }
-    if (m->d.dim == 3 && ctx->engine == 1) return predict_tiles(ctx, *P, m, dt, dhat, st);
+    if (m->d.dim == 3 && ctx->engine == 1) return predict_tiles(ctx, *P, m, grid, dt, dhat, st);
     const int64_t chunk = 8192;
     cs_status rc = ensure_workspace(ctx, *P, chunk);
     if (rc) return rc;
@@ -379,7 +404,7 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
     for (int k = 0; k < D; ++k) scale[k] = float(dt / pred_view(m->d).sa[k]);
     for (int64_t c0 = 0; c0 < pred_view(m->d).n_asg; c0 += chunk) {
         const int64_t B = std::min(chunk, pred_view(m->d).n_asg - c0);
-        ctx->launches += launch_windows(pred_view(m->d), m->grid_u, nullptr, c0, B, scale, P->win,
+        ctx->launches += launch_windows(pred_view(m->d), grid, nullptr, c0, B, scale, P->win,
                                         ctx->sm_count, st);
         ctx->launches += forward(ctx, *P, B, P->win, st);
         PCHK(cudaMemcpyAsync(dhat + c0 * D, P->out, size_t(B) * D * sizeof(float),
@@ -388,11 +413,82 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, double dt, float *dhat, cudaStr
     return CS_OK;
 }
 
-cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt,
-                      cudaStream_t st, const float **dhat_out) {
+cs_status reserve_tiles(cs_ctx *ctx, cs::Mesh *m) {
+    if (m->d.dim != 3 || ctx->engine != 1) return CS_OK;
+    Predictor *P = get_pred(ctx, 3);
+    if (!P || !P->loaded) return CS_OK;
+    return grow_tiles(ctx, *P, plan_tiles(pred_view(m->d)));
+}
+
+bool serving_predictor_ready(cs_ctx *ctx, const cs::Mesh *m) {
+    const Predictor &P = ctx->pred[m->d.dim - 2];
+    if (!P.loaded || ctx->engine != 1 || !m->interp_node) return false;
+    if (m->d.dim == 2) return P.packed && !P.packed_dirty && ctx->dev_err;
+    return !P.tiles.empty();
+}
+
+cs_status prepare_serving(cs_ctx *ctx) {
+    for (int dim = 2; dim <= 3; ++dim) {
+        Predictor &P = ctx->pred[dim - 2];
+        if (!P.loaded || ctx->engine != 1) continue;
+        if (dim == 2) {
+            if (!P.packed) {
+                cs_status rc = dalloc(ctx, &P.packed, size_t(tc_packed_bytes()));
+                if (rc) return rc;
+            }
+            if (!ctx->dev_err) {
+                cs_status rc = dalloc(ctx, &ctx->dev_err, 1);
+                if (rc) return rc;
+                PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+            }
+            if (P.packed_dirty) {
+                ctx->launches += launch_pack_tc(P.w, NetShape(2), P.packed, nullptr);
+                P.packed_dirty = false;
+            }
+        }
+        for (auto &kv : ctx->meshes) {
+            cs::Mesh *m = kv.second;
+            if (m->d.dim != dim) continue;
+            cs_status rc = ensure_interp(ctx, m, nullptr);
+            if (rc == CS_OK) rc = reserve_tiles(ctx, m);
+            if (rc) return rc;
+        }
+    }
+    for (auto &kv : ctx->fields) {
+        auto it = ctx->meshes.find(kv.second->mesh_id);
+        if (it == ctx->meshes.end()) continue;
+        const float *g = nullptr;
+        cs_status rc = field_grid(ctx, it->second, kv.second, nullptr, &g);
+        if (rc) return rc;
+    }
+    PCHK(cudaDeviceSynchronize());
+    return CS_OK;
+}
+
+cs_status field_grid(cs_ctx *ctx, cs::Mesh *m, cs::Field *f, cudaStream_t st,
+                     const float **grid_out) {
+    if (f->grid_version != m->pgrid_version || !f->grid_u) {
+        dfree(ctx, f->grid_u);
+        f->grid_u = nullptr;
+        f->grid_version = -1;
+        cs_status rc = dalloc(ctx, &f->grid_u, size_t(m->d.n_pasg) * m->d.dim);
+        if (rc) return rc;
+        rc = ensure_interp(ctx, m, st);
+        if (rc) return rc;
+        ctx->launches += launch_resample(pred_view(m->d), m->interp_node, m->interp_w, f->u_nodal,
+                                         f->grid_u, ctx->sm_count, st);
+        f->grid_version = m->pgrid_version;
+    }
+    *grid_out = f->grid_u;
+    return CS_OK;
+}
+
+cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const float *grid, const double *u_nodal,
+                      double dt, cudaStream_t st, const float **dhat_out) {
     cs_status rc = ensure_mesh_grid(ctx, m);
     if (rc) return rc;
-    if (u_nodal) {
+    if (!grid) {
+        if (!u_nodal) return fail(ctx, CS_EINVAL, "no velocity for the start predictor");
         rc = ensure_interp(ctx, m, st);
         if (rc) return rc;
         const int ev = ctx->prof.begin(CS_STAGE_RESAMPLE, st);
@@ -400,9 +496,10 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const double *u_nodal, double dt
                                          ctx->sm_count, st);
         ctx->prof.end(ev, st);
         m->grid_u_valid = true;
+        grid = m->grid_u;
     }
     const int ev = ctx->prof.begin(CS_STAGE_CNN, st);
-    rc = predict_grid(ctx, m, dt, m->grid_dhat, st);
+    rc = predict_grid(ctx, m, grid, dt, m->grid_dhat, st);
     ctx->prof.end(ev, st);
     if (rc) return rc;
     *dhat_out = m->grid_dhat;
@@ -459,14 +556,14 @@ cs_status cs_predictor_load(cs_ctx *ctx, int dim, const float *weights, int64_t 
         return fail(ctx, CS_EINVAL, "cs_predictor_load: bad dim or size (expected " +
                                         std::to_string(cs_predictor_size(dim)) + " floats)");
     PCHK(cudaSetDevice(ctx->device));
-    predictor_release(*P);
+    predictor_release(ctx, *P);
     P->dim = dim;
     P->n = n;
     cs_status rc;
     if ((rc = dalloc(ctx, &P->w, size_t(n))) || (rc = dalloc(ctx, &P->g, size_t(n))) ||
         (rc = dalloc(ctx, &P->m, size_t(n))) || (rc = dalloc(ctx, &P->v, size_t(n))) ||
         (rc = dalloc(ctx, &P->loss, 1))) {
-        predictor_release(*P);
+        predictor_release(ctx, *P);
         return rc;
     }
     PCHK(cudaMemcpy(P->w, weights, size_t(n) * sizeof(float), cudaMemcpyHostToDevice));
@@ -510,8 +607,9 @@ cs_status cs_predictor_grid(cs_ctx *ctx, int32_t mesh_id, int32_t stride) {
         if (!q) continue;
         auto it = std::find(m->allocs.begin(), m->allocs.end(), q);
         if (it != m->allocs.end()) m->allocs.erase(it);
-        cudaFree(q);
+        dfree(ctx, q);
     }
+    m->pgrid_version += 1;   // the fields' grid velocities are resampled at next use
     m->grid_u = m->grid_dhat = nullptr;
     m->interp_node = nullptr;
     m->interp_w = nullptr;
@@ -610,8 +708,8 @@ cs_status cs_predict(cs_ctx *ctx, int32_t mesh_id, double dt, float *dhat_out, v
     PCHK(cudaSetDevice(ctx->device));
     cs_status rc = ensure_mesh_grid(ctx, m);
     if (rc) return rc;
-    rc = predict_grid(ctx, m, dt, dhat_out ? dhat_out : m->grid_dhat,
-                      static_cast<cudaStream_t>(stream));
+    rc = predict_grid(ctx, m, m->grid_u_valid ? m->grid_u : nullptr, dt,
+                      dhat_out ? dhat_out : m->grid_dhat, static_cast<cudaStream_t>(stream));
     if (rc) return rc;
     PCHK(cudaGetLastError());
     return CS_OK;
@@ -668,7 +766,7 @@ cs_status cs_predictor_train(cs_ctx *ctx, int dim, const float *windows, const f
         if (e != cudaSuccess) out = fail(ctx, CS_ECUDA, std::string("cs_predictor_train: ") +
                                                             cudaGetErrorString(e));
     }
-    cudaFree(losses);
+    dfree(ctx, losses);
     return out;
 }
 

@@ -67,7 +67,98 @@ __global__ void __launch_bounds__(256) stats_kernel(int64_t n, const int32_t *pa
     }
 }
 
+// Error statistics of a finished track call (Sec. 3.1): the origin error err
+// of a particle is the distance between the centroids of its tracking origin
+// (the walk's start element) and of its host; the displacement error is
+// |dhat * s - (x_p - x)|, the predicted displacement at the predictor cell of
+// x (in length units) against the true one. Sums and maxima go to out[0..3]
+// (FP64, maxima as the bit patterns of non-negative doubles), counts to
+// cnt[0..1].
+template <int D>
+__global__ void __launch_bounds__(256) error_stats_kernel(
+    const DevMesh m, int64_t n, const int32_t *__restrict__ start, const int32_t *__restrict__ host,
+    const double *__restrict__ x, const double *__restrict__ u, double dt,
+    const float *__restrict__ dhat, double *out, unsigned long long *cnt) {
+    double es = 0.0, em = 0.0, ds = 0.0, dm = 0.0;
+    unsigned long long ne = 0, nd = 0;
+    for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+         p += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t s = start ? start[p] : -1, h = host[p];
+        if (start && s >= 0 && s < m.n_e && h >= 0 && h < m.n_e) {
+            const int32_t a = __ldg(m.iperm + s), b = __ldg(m.iperm + h);
+            double q = 0.0;
+            #pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double d = __dsub_rn(m.centroid[int64_t(a) * D + k], m.centroid[int64_t(b) * D + k]);
+                q = __dadd_rn(q, __dmul_rn(d, d));
+            }
+            const double e = __dsqrt_rn(q);
+            es += e;
+            em = fmax(em, e);
+            ne += 1;
+        }
+        if (dhat) {
+            double xv[D], dtrue[D];
+            bool finite = true;
+            #pragma unroll
+            for (int k = 0; k < D; ++k) {
+                xv[k] = x[p * D + k];
+                const double xp = __dsub_rn(xv[k], __dmul_rn(u[p * D + k], dt));
+                dtrue[k] = __dsub_rn(xp, xv[k]);
+                finite = finite && isfinite(xp);
+            }
+            if (finite) {
+                const int64_t c = grid_cell<D>(xv, m.lo, m.psa, m.pga);
+                double q = 0.0;
+                #pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const double d =
+                        __dsub_rn(__dmul_rn(double(dhat[c * D + k]), m.psa[k]), dtrue[k]);
+                    q = __dadd_rn(q, __dmul_rn(d, d));
+                }
+                const double e = __dsqrt_rn(q);
+                ds += e;
+                dm = fmax(dm, e);
+                nd += 1;
+            }
+        }
+    }
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        es += __shfl_xor_sync(kFull, es, o);
+        ds += __shfl_xor_sync(kFull, ds, o);
+        em = fmax(em, __shfl_xor_sync(kFull, em, o));
+        dm = fmax(dm, __shfl_xor_sync(kFull, dm, o));
+        ne += __shfl_xor_sync(kFull, ne, o);
+        nd += __shfl_xor_sync(kFull, nd, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, es);
+        atomicMax(reinterpret_cast<unsigned long long *>(out + 1),
+                  static_cast<unsigned long long>(__double_as_longlong(em)));
+        atomicAdd(out + 2, ds);
+        atomicMax(reinterpret_cast<unsigned long long *>(out + 3),
+                  static_cast<unsigned long long>(__double_as_longlong(dm)));
+        atomicAdd(cnt + 0, ne);
+        atomicAdd(cnt + 1, nd);
+    }
+}
+
 }  // namespace
+
+int launch_error_stats(const DevMesh &m, int64_t n, const int32_t *start, const int32_t *host,
+                       const double *x, const double *u, double dt, const float *dhat,
+                       double *out, unsigned long long *cnt, int sm_count, cudaStream_t st) {
+    cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
+    cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st);
+    if (n == 0) return 0;
+    const int grid = int(std::min<int64_t>(int64_t(sm_count) * 4, (n + 255) / 256));
+    if (m.dim == 2)
+        error_stats_kernel<2><<<grid, 256, 0, st>>>(m, n, start, host, x, u, dt, dhat, out, cnt);
+    else
+        error_stats_kernel<3><<<grid, 256, 0, st>>>(m, n, start, host, x, u, dt, dhat, out, cnt);
+    return 1;
+}
 
 int launch_seed_grid(const DevMesh &m, int32_t *seed, int sm_count, cudaStream_t st) {
     const int grid = sm_count * 8;

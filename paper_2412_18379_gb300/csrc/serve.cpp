@@ -74,6 +74,7 @@ struct Request {
     int64_t ticket = 0;
     cs_request r{};
     Mesh *mesh = nullptr;
+    const float *grid = nullptr;   // CNN-SNS: the field's grid velocity, or null (resample u)
     Clock::time_point t_submit, t_admit, t_done;
     size_t off = 0, bytes = 0;
     cs_status result = CS_OK;
@@ -100,6 +101,10 @@ struct Server {
     std::map<int64_t, Request *> all;
     int64_t next_ticket = 1;
     bool stop = false;
+    // the 3-D predictor's workspace is shared: each 3-D prediction waits for
+    // the one enqueued before it (worker thread only)
+    cudaEvent_t pred3_ev = nullptr;
+    bool pred3_any = false;
     // statistics
     std::vector<double> lat_ms;
     int64_t completed = 0, rejected = 0, particles = 0;
@@ -110,7 +115,7 @@ struct Server {
 
 namespace {
 
-size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn) {
+size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn, bool own_grid) {
     const int d = m.d.dim;
     const size_t n = size_t(r.n);
     size_t b = 0;
@@ -121,7 +126,8 @@ size_t request_bytes(const cs_request &r, const Mesh &m, bool cnn) {
     add(n * 4);                      // host
     add(n * 4);                      // path
     add(n);                          // status
-    if (cnn) add(size_t(m.d.n_pasg) * d * 4);  // predicted displacement grid
+    if (cnn) add(size_t(m.d.n_pasg) * d * 4);        // predicted displacement grid
+    if (own_grid) add(size_t(m.d.n_pasg) * d * 4);   // grid velocity of the request's u
     return b;
 }
 
@@ -144,17 +150,35 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     int32_t *host = reinterpret_cast<int32_t *>(take(n * 4));
     int32_t *path = reinterpret_cast<int32_t *>(take(n * 4));
     uint8_t *status = reinterpret_cast<uint8_t *>(take(n));
-    float *dhat = q.used_mode == CS_CNN_SNS ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4))
-                                            : nullptr;
+    const bool cnn = q.used_mode == CS_CNN_SNS;
+    float *dhat = cnn ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4)) : nullptr;
+    float *own_grid = cnn && !q.grid ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4))
+                                     : nullptr;
     cudaStream_t st = sl.st;
     cudaError_t e = cudaMemcpyAsync(x, r.x, n * d * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, r.u, n * d * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && start)
         e = cudaMemcpyAsync(start, r.start, n * 4, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return CS_ECUDA;
-    if (dhat) {
-        const cs_status rc = predict_grid(ctx, &m, r.dt, dhat, st);
+    if (cnn) {
+        // the start predictor on the request's own field: the field's resident
+        // grid velocity, or (particles = the mesh nodes) the request's u
+        // resampled to the predictor grid
+        const float *grid = q.grid;
+        if (!grid) {
+            ctx->launches += launch_resample(pred_view(m.d), m.interp_node, m.interp_w, u, own_grid,
+                                             ctx->sm_count, st);
+            grid = own_grid;
+        }
+        if (d == 3) {
+            if (S.pred3_any) cudaStreamWaitEvent(st, S.pred3_ev, 0);
+        }
+        const cs_status rc = predict_grid(ctx, &m, grid, r.dt, dhat, st);
         if (rc) return rc;
+        if (d == 3) {
+            cudaEventRecord(S.pred3_ev, st);
+            S.pred3_any = true;
+        }
     }
     TrackArgs a{};
     a.n = r.n;
@@ -269,9 +293,10 @@ void serve_release(cs_ctx *ctx) {
     for (Slot &sl : S->slots) {
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.ev) cudaEventDestroy(sl.ev);
-        if (sl.counters) cudaFree(sl.counters);
+        dfree(ctx, sl.counters);
     }
-    if (S->arena.base) cudaFree(S->arena.base);
+    if (S->pred3_ev) cudaEventDestroy(S->pred3_ev);
+    dfree(ctx, S->arena.base);
     for (auto &kv : S->all) delete kv.second;
     delete S;
     ctx->server = nullptr;
@@ -291,9 +316,16 @@ cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg) {
     Server *S = new (std::nothrow) Server();
     if (!S) return CS_ENOMEM;
     S->ctx = ctx;
-    if (cudaMalloc(&S->arena.base, cfg->arena_bytes) != cudaSuccess) {
-        delete S;
-        return sfail(ctx, CS_ENOMEM, "cs_serve_start: arena allocation failed");
+    // the arena counts against the context's HBM budget like every other block
+    {
+        void *arena = nullptr;
+        if (dmalloc(ctx, &arena, cfg->arena_bytes) != CS_OK) {
+            delete S;
+            return sfail(ctx, CS_ENOMEM, "cs_serve_start: arena of " +
+                                             std::to_string(cfg->arena_bytes) +
+                                             " bytes: " + ctx->err);
+        }
+        S->arena.base = static_cast<char *>(arena);
     }
     S->arena.size = cfg->arena_bytes;
     S->arena.free_[0] = cfg->arena_bytes;
@@ -301,33 +333,27 @@ cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg) {
     for (Slot &sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&sl.counters, 16 * sizeof(int32_t)) != cudaSuccess ||
+            dmalloc_n(ctx, &sl.counters, 16) != CS_OK ||
             cudaMemset(sl.counters, 0, 16 * sizeof(int32_t)) != cudaSuccess) {
             ctx->server = S;
             serve_release(ctx);
             return sfail(ctx, CS_ENOMEM, "cs_serve_start: slot resources");
         }
     }
-    // resident predictor weights in the tensor-core layout before any request
-    Predictor &P = ctx->pred[0];
-    if (P.loaded && ctx->engine == 1) {
-        if (!P.packed && cudaMalloc(&P.packed, size_t(tc_packed_bytes())) != cudaSuccess) {
-            ctx->server = S;
-            serve_release(ctx);
-            return sfail(ctx, CS_ENOMEM, "cs_serve_start: predictor buffer");
-        }
-        if (!ctx->dev_err) {
-            if (cudaMalloc(&ctx->dev_err, sizeof(int)) != cudaSuccess) {
-                ctx->server = S;
-                serve_release(ctx);
-                return sfail(ctx, CS_ENOMEM, "cs_serve_start: error flag");
-            }
-            cudaMemset(ctx->dev_err, 0, sizeof(int));
-        }
-        if (P.packed_dirty) {
-            ctx->launches += launch_pack_tc(P.w, NetShape(2), P.packed, nullptr);
-            P.packed_dirty = false;
-        }
+    if (cudaEventCreateWithFlags(&S->pred3_ev, cudaEventDisableTiming) != cudaSuccess) {
+        ctx->server = S;
+        serve_release(ctx);
+        return sfail(ctx, CS_ECUDA, "cs_serve_start: event");
+    }
+    // everything the requests' start predictors read, resident before any
+    // request: packed 2-D weights, the 3-D tile workspace sized for every
+    // mesh, the meshes' interpolation tables and the fields' grid velocities
+    const cs_status prc = prepare_serving(ctx);
+    if (prc != CS_OK) {
+        const std::string msg = ctx->err;
+        ctx->server = S;
+        serve_release(ctx);
+        return sfail(ctx, prc, "cs_serve_start: " + msg);
     }
     cudaDeviceSynchronize();
     ctx->server = S;
@@ -349,19 +375,27 @@ cs_status cs_serve_submit(cs_ctx *ctx, const cs_request *req, int64_t *ticket) {
         return sfail(ctx, CS_EINVAL, "cs_serve_submit: unknown mode");
     if (!req->start && req->n != m->d.n_v)
         return sfail(ctx, CS_EINVAL, "cs_serve_submit: start == NULL needs n == n_vertices");
-    // CNN-SNS where the tensor-core predictor and the mesh's grid velocity are
-    // resident; otherwise the request falls back to plain SNS
+    const Field *f = nullptr;
+    if (req->field_id != CS_NO_FIELD) {
+        auto fi = ctx->fields.find(req->field_id);
+        if (fi == ctx->fields.end() || fi->second->mesh_id != req->mesh_id)
+            return sfail(ctx, CS_EINVAL, "cs_serve_submit: field id is not a field of this mesh");
+        f = fi->second;
+    }
+    // CNN-SNS where the grid predictor is resident and the request names its
+    // field (or its particles are the mesh nodes, whose u is the field);
+    // otherwise the request falls back to plain SNS
     int mode = req->mode;
-    if (mode == CS_CNN_SNS &&
-        !(m->d.dim == 2 && ctx->pred[0].loaded && ctx->engine == 1 && m->grid_u_valid &&
-          ctx->pred[0].packed && !ctx->pred[0].packed_dirty))
+    const bool nodes = !req->start && req->n == m->d.n_v;
+    if (mode == CS_CNN_SNS && !(serving_predictor_ready(ctx, m) && (f || nodes)))
         mode = CS_SNS;
     Request *q = new (std::nothrow) Request();
     if (!q) return CS_ENOMEM;
     q->r = *req;
     q->mesh = m;
     q->used_mode = mode;
-    q->bytes = request_bytes(*req, *m, mode == CS_CNN_SNS);
+    q->grid = mode == CS_CNN_SNS && f ? f->grid_u : nullptr;
+    q->bytes = request_bytes(*req, *m, mode == CS_CNN_SNS, mode == CS_CNN_SNS && !f);
     std::lock_guard<std::mutex> lock(S->mu);
     if (q->bytes > S->arena.size) {
         const size_t need = q->bytes;

@@ -419,11 +419,13 @@ int g_noalloc_parity[kMaxDevices] = {};    // cursor of the next call per device
 
 }  // namespace cs
 
-extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
-                                      const double *u, double dt, const int32_t *start,
-                                      int mode, int32_t *host_out, int32_t *path_len_out,
-                                      uint8_t *status_out, int32_t *start_out, void *stream) {
+extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
+                                      const double *x, const double *u, double dt,
+                                      const int32_t *start, int mode, int32_t *host_out,
+                                      int32_t *path_len_out, uint8_t *status_out,
+                                      int32_t *start_out, void *stream) {
     using namespace cs;
+    (void)field_id;   // only CS_CNN_SNS reads a field, and it is refused below
     if (!ctx) return CS_EINVAL;
     auto it = ctx->meshes.find(mesh_id);
     if (it == ctx->meshes.end()) {
@@ -431,18 +433,21 @@ extern "C" cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int64_t n, c
         return CS_ENOMESH;
     }
     const Mesh *mesh = it->second;
+    if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS) {
+        ctx->err = "cs_track_noalloc: unknown mode";
+        return CS_EINVAL;
+    }
     if (n < 0 || n >= (int64_t(1) << 31) - 1) {
         ctx->err = "cs_track_noalloc: n = " + std::to_string(n) +
                    " is outside [0, 2^31 - 2]";
         return CS_EINVAL;
     }
-    if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS) {
-        ctx->err = "cs_track_noalloc: unknown mode";
-        return CS_EINVAL;
-    }
+    // the start predictor writes a displacement grid the library would have
+    // to allocate: use cs_track_dhat with a caller-owned grid instead
     if (mode == CS_CNN_SNS) {
-        ctx->err = "cs_track_noalloc: no predictor loaded";
-        return CS_ENOPRED;
+        ctx->err = "cs_track_noalloc: CS_CNN_SNS is not supported (its predicted displacement "
+                   "grid needs device memory); use cs_track_dhat with a caller-owned grid";
+        return CS_EINVAL;
     }
     if (n == 0) return CS_OK;
     if (!x || !u || !host_out || !path_len_out || !status_out) {

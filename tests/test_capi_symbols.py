@@ -52,5 +52,5 @@ def test_create_without_gpu_fails_cleanly(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     lib.cs_create.restype = ctypes.c_int32
-    rc = lib.cs_create(ctypes.byref(h), 0)
+    rc = lib.cs_create(ctypes.byref(h), 0, ctypes.c_size_t(0))
     assert rc != 0 and not h.value

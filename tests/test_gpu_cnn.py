@@ -629,3 +629,113 @@ def test_full_size_cnn_sns_parity(ctx):
     plain = om.track(c.x, c.u, c.dt, mode="sns")
     assert np.array_equal(got["host"], plain["host"])
     mesh.release()
+
+
+# ---- direct oracle parity of every grid engine ------------------------------
+
+@pytest.mark.parametrize("n_side,stride", [(13, 1), (31, 3)])
+def test_tile_engine_3d_matches_oracle_on_every_cell(ctx, n_side, stride):
+    """The 3-D fully convolutional tile engine against the FP64 forward pass
+    (oracle.cnn.forward on oracle windows of the oracle's grid velocity) on
+    every predictor cell. Tolerance: the engine rounds the input window and
+    every layer's operands to BF16 (relative 2^-9 each): five layers x two
+    operands plus the input, 11 x 2^-9 ~ 2.1e-2 of the output scale; the
+    bound allows the worst cell 5e-2, the 2-D bound's margin (4e-2 for 7
+    roundings there) scaled alike."""
+    import torch
+    c = make_case("abc3d", n_side=n_side, cfl=6)
+    flat = init_weights(3, 41)
+    ctx.load_predictor(3, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(stride)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=stride)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(om.pgrid))
+    tile = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predictor_engine("tc")
+    ctx.predict(mesh, c.dt, out=tile)
+    torch.cuda.synchronize()
+    tile = tile.cpu().numpy()
+    U = _oracle_pred_u(om, c.u)
+    cells = np.arange(n_cells)
+    w = cnn.windows(U.reshape(tuple(int(v) for v in om.pgrid[::-1]) + (3,)), cells, 3,
+                    c.dt / om.ps)
+    ref = cnn.forward(3, cnn.unpack(3, flat), w)
+    assert np.isfinite(tile).all()
+    err = np.abs(tile - ref).max()
+    assert err <= 5e-2 * np.abs(ref).max(), (err, np.abs(ref).max())
+    mesh.release()
+
+
+def test_tensor_core_at_the_benchmark_configuration(ctx):
+    """The tcgen05 grid kernel exactly as the benchmark runs it: the 1001^2
+    Taylor-Green mesh, predictor grid stride 5 (200 x 200 cells), automatic
+    tile height (13 rows: 144 tiles), against the FP64 forward pass on every
+    cell next to a tile edge or the grid edge and on 3000 random cells. The
+    bound is the 2-D one (6e-2 of the output scale: the BF16 input window and
+    six layers' BF16 operands)."""
+    import torch
+    c = make_case("tg2d", cfl=8)
+    flat = init_weights(2, 31)
+    ctx.load_predictor(2, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(5)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=5)
+    gx, gy = (int(v) for v in om.pgrid)
+    assert (gx, gy) == (200, 200)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = gx * gy
+    tc = torch.full((n_cells, 2), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predictor_engine("tc")
+    ctx.predictor_tile_rows(0)
+    ctx.predict(mesh, c.dt, out=tc)
+    ctx.device_status()
+    tc = tc.cpu().numpy()
+    assert np.isfinite(tc).all()
+    th = 13
+    iy, ix = np.divmod(np.arange(n_cells), gx)
+    edge = ((ix % 24 == 0) | (ix % 24 == 23) | (iy % th == 0) | (iy % th == th - 1) |
+            (ix == gx - 1) | (iy == gy - 1))
+    rng = np.random.default_rng(8)
+    pick = np.unique(np.concatenate([np.nonzero(edge)[0], rng.integers(0, n_cells, 3000)]))
+    U = _oracle_pred_u(om, c.u)
+    w = cnn.windows(U.reshape(gy, gx, 2), pick, 2, c.dt / om.ps)
+    ref = cnn.forward(2, cnn.unpack(2, flat), w)
+    err = np.abs(tc[pick] - ref).max()
+    assert err <= 6e-2 * np.abs(ref).max(), (err, np.abs(ref).max())
+    mesh.release()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adam_steps_against_the_oracle(ctx, dim):
+    """Five training steps on the device against oracle.cnn.Adam. Each step
+    trains on the whole batch, so its gradient is the one cs_predictor_grad
+    returns at the step's weights (up to the FP32 summation order of the
+    shuffled batch); the oracle's Adam takes those gradients from the same
+    start, keeping its own FP64 moments and bias corrections. The weights
+    after every step agree to 2e-6 (lr = 1e-3 steps, FP32 updates) wherever
+    the gradient is not tiny; elsewhere Adam's normalised step is sensitive to
+    the summation order; there every step of the device stays within Adam's
+    bound lr (1 - beta1) / sqrt(1 - beta2) ~ 3.2 lr."""
+    rng = np.random.default_rng(60 + dim)
+    flat = init_weights(dim, 9)
+    ctx.load_predictor(dim, flat)
+    S = cnn.patch_size(dim)
+    B = 64
+    win = _dev(rng.standard_normal((B, dim) + (S,) * dim).astype(np.float32))
+    tgt = _dev(rng.standard_normal((B, dim)).astype(np.float32))
+    opt = cnn.Adam(flat.size, lr=1e-3)
+    w_ref = flat.astype(np.float64)
+    for step in range(5):
+        g, _ = ctx.predictor_grad(dim, win, tgt)
+        g = g.cpu().numpy().astype(np.float64)
+        w_prev = w_ref
+        w_ref = opt.step(w_ref, g)
+        ctx.train(dim, win, tgt, batch=B, steps=1, lr=1e-3, seed=step)
+        w_dev = ctx.save_predictor(dim).astype(np.float64)
+        big = np.abs(g) > 1e-5 * np.abs(g).max()
+        assert np.allclose(w_dev[big], w_ref[big], rtol=0, atol=2e-6), step
+        assert np.all(np.abs(w_dev - w_prev) <= 3.2e-3), step
+        # continue from the device's weights so that the comparison stays per step
+        w_ref = w_dev.copy()
+    assert opt.t == 5

@@ -24,16 +24,20 @@ def setup():
     build.build()
     ctx = cs.Context(0)
     ctx.load_predictor(2, init_weights(2, 5))
+    ctx.load_predictor(3, init_weights(3, 5))
     meshes = []
     for name, kw in [("tg2d", {"n_side": 201}), ("modes2d", {"n_side": 301}),
                      ("abc3d", {"n_side": 21})]:
         c = make_case(name, **kw)
         m = ctx.upload_mesh(c.xyz, c.conn)
-        if c.dim == 2:
-            ctx.grid_velocity(m, torch.from_numpy(c.u).cuda())   # resident field
-        meshes.append((c, m, m.node_start_elements()))
+        m.set_predictor_grid(3)
+        f = ctx.upload_field(m, c.u)                       # resident field
+        meshes.append((c, m, m.node_start_elements(), f))
+    # uploaded before serving starts (meshes are fixed while serving)
+    big = make_case("tg2d", n_side=401)
+    mb = ctx.upload_mesh(big.xyz, big.conn)
     torch.cuda.synchronize()
-    yield ctx, meshes
+    yield ctx, meshes, (big, mb)
     ctx.close()
 
 
@@ -42,7 +46,7 @@ def _requests(meshes, count, seed):
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(count):
-        c, m, node_elem = meshes[rng.integers(len(meshes))]
+        c, m, node_elem, f = meshes[rng.integers(len(meshes))]
         n = int(np.exp(rng.uniform(np.log(500), np.log(c.n_particles))))
         idx = np.sort(rng.choice(c.n_particles, size=n, replace=False))
         x = torch.from_numpy(np.ascontiguousarray(c.x[idx])).pin_memory()
@@ -50,27 +54,28 @@ def _requests(meshes, count, seed):
         st = torch.from_numpy(np.ascontiguousarray(node_elem[idx])).pin_memory()
         dt = dt_for_cfl(c.u, c.h, rng.uniform(1.0, 16.0))
         mode = ["sns", "asg", "cnn"][i % 3]
-        reqs.append((m, x, u, st, dt, mode))
+        reqs.append((m, x, u, st, dt, mode, f))
     return reqs
 
 
 def _run(ctx, reqs, burst):
     outs = [None] * len(reqs)
     if burst:
-        tickets = [ctx.submit(m, x, u, dt, start=st, mode=mode) for m, x, u, st, dt, mode in reqs]
+        tickets = [ctx.submit(m, x, u, dt, start=st, mode=mode, field=f)
+                   for m, x, u, st, dt, mode, f in reqs]
         modes = [ctx.wait(t) for t, _ in tickets]
         outs = [{k: v.numpy().copy() for k, v in o.items()} for _, o in tickets]
     else:
         modes = []
-        for i, (m, x, u, st, dt, mode) in enumerate(reqs):
-            t, o = ctx.submit(m, x, u, dt, start=st, mode=mode)
+        for i, (m, x, u, st, dt, mode, f) in enumerate(reqs):
+            t, o = ctx.submit(m, x, u, dt, start=st, mode=mode, field=f)
             modes.append(ctx.wait(t))
             outs[i] = {k: v.numpy().copy() for k, v in o.items()}
     return outs, modes
 
 
 def test_results_same_alone_and_in_the_mix(setup):
-    ctx, meshes = setup
+    ctx, meshes, _ = setup
     reqs = _requests(meshes, 36, seed=1)
     ctx.serve_start(slots=6, arena_bytes=1 << 30)
     try:
@@ -83,40 +88,41 @@ def test_results_same_alone_and_in_the_mix(setup):
     for i, (a, b) in enumerate(zip(alone, mixed)):
         for k in ("host", "path_len", "status"):
             assert np.array_equal(a[k], b[k]), (i, k)
-    # CNN-SNS requests on the 3-D mesh fell back to plain SNS, 2-D ran CNN-SNS
-    for (m, _, _, _, _, mode), used in zip(reqs, modes_b):
+    # CNN-SNS requests ran CNN-SNS on their own field, in 2-D (tensor cores)
+    # and in 3-D (tile engine)
+    for (m, _, _, _, _, mode, _), used in zip(reqs, modes_b):
         if mode == "cnn":
-            assert used == (1 if m.dim == 2 else 0)
+            assert used == 1
+    assert {m.dim for (m, _, _, _, _, mode, _) in reqs if mode == "cnn"} == {2, 3}
     # the mix overlapped on the device and the latencies are reported
     assert rep["completed"] == 72 and rep["rejected"] == 0
     assert rep["max_concurrent"] > 1
     assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
     # the serving results equal the direct host-pointer entry point
-    m, x, u, st, dt, mode = reqs[0]
-    ref = ctx.track_host(m, x.numpy(), u.numpy(), dt, start=st.numpy(), mode=mode)
-    for k in ("host", "path_len", "status"):
-        assert np.array_equal(ref[k], alone[0][k])
+    for i in range(6):
+        m, x, u, st, dt, mode, f = reqs[i]
+        ref = ctx.track_host(m, x.numpy(), u.numpy(), dt, start=st.numpy(), mode=mode, field=f)
+        for k in ("host", "path_len", "status"):
+            assert np.array_equal(ref[k], alone[i][k]), (i, mode, k)
 
 
 def test_admission_by_footprint(setup):
     import paper_2412_18379_gb300 as cs
-    ctx, meshes = setup
-    c, m, node_elem = meshes[0]
+    ctx, meshes, (big, mb) = setup
+    c, m, node_elem, _ = meshes[0]
     # an arena that fits about two of these requests at a time
     n = c.n_particles
     per = n * (2 * 2 * 8 + 4 + 4 + 4 + 1 + 4) + 8 * 256
     ctx.serve_start(slots=8, arena_bytes=int(2.5 * per))
     try:
         reqs = [(m, *(__import__("torch").from_numpy(a).pin_memory()
-                      for a in (c.x, c.u, node_elem)), c.dt * (1 + i % 4), "sns")
+                      for a in (c.x, c.u, node_elem)), c.dt * (1 + i % 4), "sns", None)
                 for i in range(10)]
         outs, _ = _run(ctx, reqs, burst=True)       # queues, never deadlocks
         rep = ctx.serve_report()
         assert rep["completed"] == 10 and rep["max_concurrent"] <= 2
         assert rep["peak_bytes"] <= int(2.5 * per)
         # a request that can never fit is refused at once
-        big = make_case("tg2d", n_side=401)
-        mb = ctx.upload_mesh(big.xyz, big.conn)
         import torch
         with pytest.raises(cs.CsError) as e:
             ctx.submit(mb, torch.from_numpy(big.x).pin_memory(),

@@ -235,3 +235,24 @@ def test_full_size_abc3d_parity(ctx):
     want = _oracle_out(om, om.track(c.x, c.u, c.dt, mode="sns"))
     _compare(got, want, "full abc3d sns")
     mesh.release()
+
+
+def test_equal_minima_leave_through_the_lowest_local_index(ctx):
+    """R4 on meshes whose start element has exactly equal smallest
+    coordinates (Eq. 5's ties): the device takes the same exit as the oracle,
+    so paths, statuses, starts and hosts match bit for bit."""
+    import torch
+    from workloads.meshes import tie_meshes
+    for name, xyz, conn, p, face in tie_meshes():
+        mesh = ctx.upload_mesh(xyz, conn)
+        om = oracle.Mesh(xyz, conn, grid=mesh.info()["asg_grid"])
+        pts = np.repeat(p, 64, axis=0)
+        zeros = np.zeros_like(pts)
+        start = np.zeros(pts.shape[0], dtype=np.int32)
+        out = ctx.track(mesh, _dev(pts), _dev(zeros), 0.0, start=_dev(start), start_out=True)
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in out.items()}
+        want = _oracle_out(om, om.track(pts, zeros, 0.0, start=start))
+        _compare(got, want, name)
+        assert (got["path_len"] == (2 if face == 1 else 1)).all(), name
+        mesh.release()

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import metrics
 from workloads import make_case, mesh_2d, mesh_3d
+from workloads.meshes import tie_meshes
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -268,6 +269,33 @@ def test_walk_strip_path_length():
     assert reason[0] == oracle.CAP and it[0] == 5 and end[0] == 4
 
 
+@pytest.mark.parametrize("case", tie_meshes(), ids=lambda c: c[0])
+def test_walk_equal_minima_leave_through_lowest_local_index(case):
+    """R4 (Eq. 5 leaves ties open): among exactly equal smallest coordinates
+    the walk leaves through the lowest local index. In element 0 of each mesh
+    p has equal negative coordinates for faces 1..d (M is the identity, so
+    they are exact). Face 1 is the lowest of them. Where element 1 lies
+    across face 1, the walk steps into it and stops there: I_t = 2,
+    FOUND. Where it lies across a higher face, face 1 is a boundary face,
+    so the walk ends there after one evaluation and the exact search finds
+    element 1 (FOUND_VIA_FALLBACK). Picking the last equal minimum instead,
+    or scanning the faces in reverse, swaps the two outcomes."""
+    name, xyz, conn, p, face = case
+    m = oracle.Mesh(xyz, conn)
+    lam = oracle.bary(m.v0[0], m.M[0], p[0])
+    assert np.all(lam[1:] == lam[1]) and lam[1] < 0
+    assert m.nbr[0][face] == 1 and (m.nbr[0] >= 0).sum() == 1
+    end, it, reason = oracle.walk(m.v0, m.M, m.nbr, p, np.array([0], dtype=np.int32))
+    r = m.track(p, np.zeros_like(p), 0.0, start=np.array([0], dtype=np.int32))
+    assert r["host"][0] == 1
+    if face == 1:
+        assert reason[0] == oracle.CONTAINED and end[0] == 1 and it[0] == 2
+        assert r["status"][0] == oracle.ST_FOUND and r["path_len"][0] == 2
+    else:
+        assert reason[0] == oracle.BOUNDARY and end[0] == 0 and it[0] == 1
+        assert r["status"][0] == oracle.ST_FALLBACK and r["path_len"][0] == 1
+
+
 def test_walk_start_inside_is_one_step():
     c = make_case("rotation2d")
     m = oracle.Mesh(c.xyz, c.conn)
@@ -368,3 +396,19 @@ def test_err_is_centroid_distance():
     assert np.allclose(cent, [[2 / 3, 1 / 3], [1 / 3, 2 / 3]])
     e = metrics.err(cent, np.array([0, 1, 0, -1]), np.array([1, 1, 0, 0]))
     assert np.allclose(e[:3], [np.sqrt(2) / 3, 0, 0]) and np.isnan(e[3])
+
+
+def test_displacement_error_closed_forms():
+    """A prediction equal to the true displacement (exact in float32 here:
+    dyadic values) has error 0; one off by (3, 4) cells of size (0.5, 0.25)
+    has error |(1.5, 1.0)| = sqrt(3.25); a non-finite departure point gives NaN."""
+    x = np.array([[0.25, 0.5], [0.0, 0.0], [1.0, 1.0]])
+    xp = np.array([[0.75, 0.0], [0.5, -0.5], [np.inf, 1.0]])
+    s = np.array([0.5, 0.25])
+    exact = (xp - x) / s
+    exact[2] = 0.0
+    e = metrics.displacement_error(exact.astype(np.float32), s, x, xp)
+    assert e[0] == 0.0 and e[1] == 0.0 and np.isnan(e[2])
+    off = exact + np.array([3.0, 4.0])
+    e = metrics.displacement_error(off.astype(np.float32), s, x, xp)
+    assert np.isclose(e[0], np.sqrt(3.25), rtol=0, atol=1e-15)

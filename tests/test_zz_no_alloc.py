@@ -77,14 +77,60 @@ def test_noalloc_explicit_starts_and_limit(ctx):
     big = torch.zeros((4, 2), dtype=torch.float64, device="cuda")
     h = torch.full((4,), -7, dtype=torch.int32, device="cuda")
     for n in (N_LIMIT, -1):
-        rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, n, big.data_ptr(), big.data_ptr(),
-                                      0.1, start.data_ptr(), cs.CS_SNS, h.data_ptr(),
-                                      h.data_ptr(), h.data_ptr(), None, None)
+        rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, cs.CS_NO_FIELD, n, big.data_ptr(),
+                                      big.data_ptr(), 0.1, start.data_ptr(), cs.CS_SNS,
+                                      h.data_ptr(), h.data_ptr(), h.data_ptr(), None, None)
         assert rc == -1                               # CS_EINVAL
         assert "2^31 - 2" in ctx.lib.cs_last_error(ctx.h).decode()
+    # CNN-SNS needs a predicted displacement grid this call would have to
+    # allocate: refused with a clear error, with or without a loaded predictor
+    from workloads.weights import init_weights
+    for loaded in (False, True):
+        if loaded:
+            ctx.load_predictor(2, init_weights(2, 1))
+        for n in (0, 4):
+            rc = ctx.lib.cs_track_noalloc(ctx.h, mesh.id, cs.CS_NO_FIELD, n, big.data_ptr(),
+                                          big.data_ptr(), 0.1, start.data_ptr(), cs.CS_CNN_SNS,
+                                          h.data_ptr(), h.data_ptr(), h.data_ptr(), None, None)
+            assert rc == -1                           # CS_EINVAL
+            assert "CS_CNN_SNS is not supported" in ctx.lib.cs_last_error(ctx.h).decode()
     torch.cuda.synchronize()
     assert (h.cpu().numpy() == -7).all()
     mesh.release()
+
+
+def test_noalloc_allocates_no_device_memory(ctx):
+    """The defining property: with outputs preallocated, a call leaves the
+    device's free memory unchanged (measured around a call after a first one,
+    so that lazily loaded kernels are already resident), while cs_track's
+    first call on a fresh context allocates its scratch."""
+    import torch
+    import paper_2412_18379_gb300 as cs
+    c = make_case("tg2d", n_side=201, cfl=8)
+    fresh = cs.Context(0)
+    try:
+        mesh = fresh.upload_mesh(c.xyz, c.conn)
+        x, u = _dev(c.x), _dev(c.u)
+        n = c.n_particles
+        out = dict(host=torch.empty(n, dtype=torch.int32, device="cuda"),
+                   path_len=torch.empty(n, dtype=torch.int32, device="cuda"),
+                   status=torch.empty(n, dtype=torch.uint8, device="cuda"))
+        fresh.track_noalloc(mesh, x, u, c.dt, out=out)
+        torch.cuda.synchronize()
+        before = fresh.memory_usage()[0]
+        free0 = torch.cuda.mem_get_info()[0]
+        for mode in ("sns", "asg"):
+            fresh.track_noalloc(mesh, x, u, c.dt, mode=mode, out=out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert fresh.memory_usage()[0] == before
+        # the allocating entry point, for contrast, takes its scratch on first use
+        fresh.track(mesh, x, u, c.dt, out=out)
+        torch.cuda.synchronize()
+        assert fresh.memory_usage()[0] > before
+        mesh.release()
+    finally:
+        fresh.close()
 
 
 def test_noalloc_three_million_particles(ctx):

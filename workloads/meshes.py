@@ -169,3 +169,34 @@ def _mesh_3d_cached(n_side, jitter, seed):
 def mesh_3d(n_side, jitter=0.1, seed=3):
     """(xyz, conn, h) of the jittered Kuhn cube (read-only, cached)."""
     return _mesh_3d_cached(int(n_side), float(jitter), int(seed))
+
+
+def tie_meshes():
+    """Two-element meshes in which the start element's smallest barycentric
+    coordinates are exactly equal at the query point: element 0 is the unit
+    simplex (v0 at the origin, so M is the identity and lambda_k = p_k for
+    k >= 1, computed without rounding) and p has equal negative coordinates.
+    Element 1 lies across exactly one face of element 0 and contains p; every
+    other face of element 0 is on the boundary.
+
+    Returns a list of (name, xyz, conn, p, face): `face` is the local face of
+    element 0 that element 1 lies across."""
+    out = []
+    # 2-D, p = (-1/2, -1/2): lambda = (2, -1/2, -1/2)
+    p2 = np.array([[-0.5, -0.5]])
+    out.append(("2d-across-face-1",
+                np.array([[0, 0], [1, 0], [0, 1], [-2, -3]], dtype=np.float64),
+                np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32), p2, 1))
+    out.append(("2d-across-face-2",
+                np.array([[0, 0], [1, 0], [0, 1], [-3, -2]], dtype=np.float64),
+                np.array([[0, 1, 2], [0, 3, 1]], dtype=np.int32), p2, 2))
+    # 3-D, p = (-1/4, -1/4, -1/4): lambda = (7/4, -1/4, -1/4, -1/4)
+    p3 = np.array([[-0.25, -0.25, -0.25]])
+    unit = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    out.append(("3d-across-face-1",
+                np.array(unit + [[-3, -4, -4]], dtype=np.float64),
+                np.array([[0, 1, 2, 3], [0, 3, 2, 4]], dtype=np.int32), p3, 1))
+    out.append(("3d-across-face-3",
+                np.array(unit + [[-4, -4, -3]], dtype=np.float64),
+                np.array([[0, 1, 2, 3], [0, 2, 1, 4]], dtype=np.int32), p3, 3))
+    return out
