@@ -274,6 +274,29 @@ class Mesh:
             c = c * int(self.pgrid[k]) + t[:, k]
         return c
 
+    def cnn_origin_cells(self, x, dhat):
+        """Algorithm 2's origin under reading R23 (single precision; the paper
+        fixes none and the origin only chooses the start element): x
+        truncated toward zero to float32, its predictor cell, y = x + dhat *
+        ps with dhat the prediction at that cell, and the ASG cell of y. All
+        arithmetic in float32, each operation rounded to nearest; the grid
+        origin, cell sizes and their inverses are the float64 values rounded
+        to float32. Returns (predictor cells, ASG cells of y)."""
+        xt = trunc_f32(x)
+        lo = self.lo.astype(np.float32)
+        pinv = (1.0 / self.ps).astype(np.float32)
+        pc = np.zeros(xt.shape[0], dtype=np.int64)
+        for k in range(self.dim - 1, -1, -1):
+            pc = pc * int(self.pgrid[k]) + cell_f32(xt[:, k], lo[k], pinv[k], int(self.pgrid[k]))
+        d = np.asarray(dhat, dtype=np.float32).reshape(-1, self.dim)[pc]
+        ps = self.ps.astype(np.float32)
+        inv = (1.0 / ((self.hi - self.lo) / self.grid)).astype(np.float32)
+        c = np.zeros(xt.shape[0], dtype=np.int64)
+        for k in range(self.dim - 1, -1, -1):
+            y = xt[:, k] + d[:, k] * ps[k]
+            c = c * int(self.grid[k]) + cell_f32(y, lo[k], inv[k], int(self.grid[k]))
+        return pc, c
+
     def locate(self, pts, eps=EPS):
         if self.brute:
             return locate_bruteforce(self.v0, self.M, pts, eps)
@@ -298,9 +321,10 @@ class Mesh:
 
         mode 'sns': start = the given start (user ids) or the node's element;
         'asg': start = seed grid cell of x_p itself; 'cnn': start = seed grid
-        cell of x + dhat * ps (dhat per particle, in predictor cell units, ps
-        the predictor cell size). A seed of -1 falls back to
-        the plain start. Returns dict of host, path_len, status, start, xp."""
+        cell of x + dhat * ps (dhat the prediction at every predictor cell, in
+        predictor cell units, ps the predictor cell size; single precision,
+        see cnn_origin_cells). A seed of -1 falls back to the plain start.
+        Returns dict of host, path_len, status, start, xp."""
         x, u = _f(x), _f(u)
         n = x.shape[0]
         xp = departure(x, u, dt)
@@ -317,9 +341,8 @@ class Mesh:
             s = self.seed[c]
             st = np.where(s >= 0, s, plain).astype(np.int32)
         elif mode == "cnn":
-            # dhat: per particle, in predictor cell units
-            y = x + (np.asarray(dhat, dtype=np.float32).astype(np.float64) * self.ps)
-            c = self.cells(y)
+            # dhat: the prediction at every predictor cell, in cell units
+            _, c = self.cnn_origin_cells(x, dhat)
             s = self.seed[c]
             st = np.where(s >= 0, s, plain).astype(np.int32)
         else:
@@ -336,6 +359,34 @@ class Mesh:
         it[~finite] = 0
         return dict(host=host, path_len=it, status=status, start=st, xp=xp,
                     end=end, reason=reason)
+
+
+def trunc_f32(x):
+    """x truncated toward zero to float32: the significand cut to 24 bits;
+    magnitudes below 2^-126 give a signed zero, finite magnitudes of 2^128 and
+    more a signed infinity; infinities and NaN stay what they are."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = x.view(np.uint64)
+    e = ((b >> np.uint64(52)) & np.uint64(0x7ff)).astype(np.int64) - 1023
+    t = (b & ~np.uint64((1 << 29) - 1)).view(np.float64)
+    neg = np.signbit(x)
+    with np.errstate(over="ignore"):
+        out = t.astype(np.float32)
+    out = np.where(e < -126, np.where(neg, np.float32(-0.0), np.float32(0.0)), out)
+    big = (e > 127) & np.isfinite(x)
+    out = np.where(big, np.where(neg, np.float32(-np.inf), np.float32(np.inf)), out)
+    return out.astype(np.float32)
+
+
+def cell_f32(v, lo, inv, g):
+    """floor((v - lo) * inv) in float32 (each operation rounded to nearest),
+    clamped to [0, g - 1]; negative and NaN quotients give 0."""
+    v = np.asarray(v, dtype=np.float32)
+    q = (v - np.float32(lo)) * np.float32(inv)
+    with np.errstate(invalid="ignore"):
+        f = np.floor(q)
+        ok = q >= np.float32(0.0)
+    return np.where(ok, np.minimum(f, np.float32(g - 1)), np.float32(0.0)).astype(np.int64)
 
 
 def default_grid(n_v, dim):

@@ -293,6 +293,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         d.pga[k] = d.ga[k];
         d.psa[k] = d.sa[k];
         d.pinv_sa[k] = d.inv_sa[k];
+        d.psa_f[k] = static_cast<float>(d.psa[k]);
     }
     d.n_pasg = n_asg;
     d.pseed = seed;

@@ -85,6 +85,7 @@ struct DevMesh {
     int32_t pga[3];           // ga / pstride (at least 1)
     double psa[3];            // sa * pstride
     float pinv_sa[3];         // 1 / psa rounded to float
+    float psa_f[3];           // psa rounded to float
     int64_t n_pasg;
     const int32_t *pseed;     // [n_pasg] host of each cell centre (the seed of its middle ASG cell)
 };

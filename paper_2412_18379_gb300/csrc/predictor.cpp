@@ -620,6 +620,7 @@ cs_status cs_predictor_grid(cs_ctx *ctx, int32_t mesh_id, int32_t stride) {
         d.pga[k] = k < d.dim ? d.ga[k] / stride : 1;
         d.psa[k] = k < d.dim ? d.sa[k] * double(stride) : 1.0;
         d.pinv_sa[k] = static_cast<float>(1.0 / d.psa[k]);
+        d.psa_f[k] = static_cast<float>(d.psa[k]);
         n *= d.pga[k];
         m->info.pred_grid[k] = d.pga[k];
     }

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) stats_kernel(int64_t n, const int32_t *pa
 // of a particle is the distance between the centroids of its tracking origin
 // (the walk's start element) and of its host; the displacement error is
 // |dhat * s - (x_p - x)|, the predicted displacement at the predictor cell of
-// x (in length units) against the true one. Sums and maxima go to out[0..3]
+// x (the cell CNN-SNS reads, in length units) against the true one. Sums and maxima go to out[0..3]
 // (FP64, maxima as the bit patterns of non-negative doubles), counts to
 // cnt[0..1].
 template <int D>
@@ -108,7 +108,11 @@ __global__ void __launch_bounds__(256) error_stats_kernel(
                 finite = finite && isfinite(xp);
             }
             if (finite) {
-                const int64_t c = grid_cell<D>(xv, m.lo, m.psa, m.pga);
+                // the predictor cell the walk's CNN-SNS start rule reads (R23)
+                int64_t c = 0;
+                #pragma unroll
+                for (int k = D - 1; k >= 0; --k)
+                    c = c * m.pga[k] + cell_f32(trunc_to_float(xv[k]), m.lo_h[k], m.pinv_sa[k], m.pga[k]);
                 double q = 0.0;
                 #pragma unroll
                 for (int k = 0; k < D; ++k) {

@@ -106,26 +106,40 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
             plain = kPrefetch<D> ? f.start[lane] : __ldg(m.node_elem + pp);
         }
         s = plain;
+        int64_t c1 = -1;    // ASG cell whose seed starts the walk (ASG, CNN-SNS)
         if (finite && a.mode == CS_ASG_DIRECT) {
-            const int32_t sd = __ldg(m.seed + grid_cell_f<D>(xp, xh, xl, m));
-            if (sd >= 0) s = sd;
+            c1 = grid_cell_f<D>(xp, xh, xl, m);
         } else if (finite && a.mode == CS_CNN_SNS) {
-            double x0[D], y[D];
-            float h0[D], l0[D], yh[D], yl[D];
+            // Algorithm 2's origin, in FP32 (reading R23: it selects the start
+            // element only, never the host, and FP64 costs GB300 1/64 of the
+            // FP32 rate): x truncated to float, its predictor cell, then the
+            // ASG seed of y = x + dhat * (predictor cell size)
+            float xt[D];
             #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                x0[k] = kPrefetch<D> ? f.x[lane * D + k] : __ldg(a.x + pp * D + k);
-                split_double(x0[k], h0[k], l0[k]);
-            }
-            // predictor cell of x, then the ASG seed of x + dhat * (predictor cell size)
-            const int64_t c0 = grid_cell_cert<D>(x0, h0, l0, m, m.psa, m.pinv_sa, m.pga);
+            for (int k = 0; k < D; ++k)
+                xt[k] = trunc_to_float(kPrefetch<D> ? f.x[lane * D + k] : __ldg(a.x + pp * D + k));
+            int64_t c0 = 0;
             #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const double dh = widen_float(__ldg(a.dhat + c0 * D + k));
-                y[k] = __dadd_rn(x0[k], __dmul_rn(dh, m.psa[k]));
-                split_double(y[k], yh[k], yl[k]);
+            for (int k = D - 1; k >= 0; --k)
+                c0 = c0 * m.pga[k] + cell_f32(xt[k], m.lo_h[k], m.pinv_sa[k], m.pga[k]);
+            float dh[D];
+            if constexpr (D == 2) {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(a.dhat) + c0);
+                dh[0] = v.x;
+                dh[D - 1] = v.y;
+            } else {
+                #pragma unroll
+                for (int k = 0; k < D; ++k) dh[k] = __ldg(a.dhat + c0 * D + k);
             }
-            const int32_t sd = __ldg(m.seed + grid_cell_f<D>(y, yh, yl, m));
+            c1 = 0;
+            #pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+                const float y = __fadd_rn(xt[k], __fmul_rn(dh[k], m.psa_f[k]));
+                c1 = c1 * m.ga[k] + cell_f32(y, m.lo_h[k], m.inv_sa[k], m.ga[k]);
+            }
+        }
+        if (c1 >= 0) {
+            const int32_t sd = __ldg(m.seed + c1);
             if (sd >= 0) s = sd;
         }
         if (!finite) {

@@ -71,27 +71,34 @@ template <int D> struct WalkE {
     int32_t uid;
 };
 
-__device__ __forceinline__ void load_walk(const WalkRec2 *__restrict__ r, int32_t e,
-                                          WalkE<2> &o) {
-    const float4 *p = reinterpret_cast<const float4 *>(r + e);
-    const float4 a = __ldg(p + 0), b = __ldg(p + 1);
-    const int4 n = __ldg(reinterpret_cast<const int4 *>(p + 2));
+// walk record fields from its 16-byte words
+__device__ __forceinline__ void decode_walk(const float4 a, const float4 b, const float4 c,
+                                            WalkE<2> &o) {
     o.vh[0] = a.x; o.vh[1] = a.y; o.vl[0] = a.z; o.vl[1] = a.w;
     o.m[0] = b.x; o.m[1] = b.y; o.m[2] = b.z; o.m[3] = b.w;
-    o.nbr[0] = n.x; o.nbr[1] = n.y; o.nbr[2] = n.z; o.uid = n.w;
+    o.nbr[0] = __float_as_int(c.x); o.nbr[1] = __float_as_int(c.y);
+    o.nbr[2] = __float_as_int(c.z); o.uid = __float_as_int(c.w);
 }
-__device__ __forceinline__ void load_walk(const WalkRec3 *__restrict__ r, int32_t e,
-                                          WalkE<3> &o) {
-    const float4 *p = reinterpret_cast<const float4 *>(r + e);
-    const float4 a = __ldg(p + 0), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
-    const int4 n = __ldg(reinterpret_cast<const int4 *>(p + 4));
+__device__ __forceinline__ void decode_walk(const float4 a, const float4 b, const float4 c,
+                                            const float4 d, const float4 n, WalkE<3> &o) {
     o.vh[0] = a.x; o.vh[1] = a.y; o.vh[2] = a.z; o.vl[0] = a.w;
     o.vl[1] = b.x; o.vl[2] = b.y; o.m[0] = b.z; o.m[1] = b.w;
     o.m[2] = c.x; o.m[3] = c.y; o.m[4] = c.z; o.m[5] = c.w;
     o.m[6] = d.x; o.m[7] = d.y; o.m[8] = d.z; o.uid = __float_as_int(d.w);
-    o.nbr[0] = n.x; o.nbr[1] = n.y; o.nbr[2] = n.z; o.nbr[3] = n.w;
+    o.nbr[0] = __float_as_int(n.x); o.nbr[1] = __float_as_int(n.y);
+    o.nbr[2] = __float_as_int(n.z); o.nbr[3] = __float_as_int(n.w);
 }
 
+__device__ __forceinline__ void load_walk(const WalkRec2 *__restrict__ r, int32_t e,
+                                          WalkE<2> &o) {
+    const float4 *p = reinterpret_cast<const float4 *>(r + e);
+    decode_walk(__ldg(p + 0), __ldg(p + 1), __ldg(p + 2), o);
+}
+__device__ __forceinline__ void load_walk(const WalkRec3 *__restrict__ r, int32_t e,
+                                          WalkE<3> &o) {
+    const float4 *p = reinterpret_cast<const float4 *>(r + e);
+    decode_walk(__ldg(p + 0), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3), __ldg(p + 4), o);
+}
 // FP64 coordinates from the exact record (the arbiter).
 __device__ __forceinline__ void bary64(const ExactRec2 *__restrict__ r, int32_t e,
                                        const double *x, double *lam) {
@@ -220,31 +227,6 @@ __device__ __forceinline__ bool finite_bits(double x) {
     return (bh & 0x7ff00000u) != 0x7ff00000u;
 }
 
-// The double equal to f (exact), built from f's bit pattern on the integer
-// pipe instead of an FP64-pipe conversion. NaN gives a quiet NaN.
-__device__ __forceinline__ double widen_float(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint32_t sign = b & 0x80000000u, e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-    uint32_t hi, lo;
-    if (e == 0xffu) {                       // inf, NaN
-        hi = sign | 0x7ff00000u | (m ? 0x80000u : 0u) | (m >> 3);
-        lo = m << 29;
-    } else if (e != 0u) {                   // normal: rebias 127 -> 1023
-        hi = sign | ((e + 896u) << 20) | (m >> 3);
-        lo = m << 29;
-    } else if (m == 0u) {                   // +-0
-        hi = sign;
-        lo = 0u;
-    } else {                                // subnormal: m * 2^-149, leading one at bit t
-        const int t = 31 - __clz(int(m));
-        const unsigned long long frac =
-            (static_cast<unsigned long long>(m) << (52 - t)) & 0xfffffffffffffull;
-        hi = sign | (unsigned(t + 874) << 20) | unsigned(frac >> 32);
-        lo = unsigned(frac);
-    }
-    return __hiloint2double(int(hi), int(lo));
-}
-
 // Cell index of one axis, FP64: floor((x - lo) / s) clamped, NaN -> 0.
 __device__ __forceinline__ int64_t cell_axis64(double x, double lo, double s, int32_t g) {
     const double t = floor(__ddiv_rn(__dsub_rn(x, lo), s));
@@ -297,6 +279,16 @@ template <int D>
 __device__ __forceinline__ int64_t grid_cell_f(const double *x, const float *xh, const float *xl,
                                                const DevMesh &m) {
     return grid_cell_cert<D>(x, xh, xl, m, m.sa, m.inv_sa, m.ga);
+}
+
+// Cell index of one axis in FP32 (the CNN-SNS origin, reading R23):
+// floor((v - lo) * inv) with each operation rounded to nearest float,
+// clamped to [0, g - 1]; negative and NaN quotients give 0. lo and inv are
+// the FP64 grid origin and 1 / cell size rounded to float.
+__device__ __forceinline__ int cell_f32(float v, float lo, float inv, int32_t g) {
+    const float q = __fmul_rn(__fsub_rn(v, lo), inv);
+    const int i = __float2int_rd(q);   // saturates at the int32 range
+    return q >= 0.0f ? min(i, g - 1) : 0;
 }
 
 // Monotone integer key of a non-NaN double: a < b <=> key(a) < key(b), with

@@ -157,7 +157,7 @@ def test_track_with_given_displacements(ctx, name, kw):
     out = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=_dev(dhat), start_out=True)
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.cells(c.x)])
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat)
     start = np.where(want["path_len"] > 0, want["start"], -1)
     for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                    ("status", want["status"]), ("start", start)):
@@ -187,7 +187,7 @@ def test_track_with_special_displacements(ctx):
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
     with np.errstate(invalid="ignore", over="ignore"):
-        want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.cells(c.x)])
+        want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat)
     start = np.where(want["path_len"] > 0, want["start"], -1)
     for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                    ("status", want["status"]), ("start", start)):
@@ -229,7 +229,7 @@ def test_cnn_start_cells_next_to_cell_faces(ctx, name, kw, stride):
                              start_out=True)
         torch.cuda.synchronize()
         got = {k: v.cpu().numpy() for k, v in out.items()}
-        want = om.track(x, u, c.dt, start=start, mode="cnn", dhat=dhat[om.pred_cells(x)])
+        want = om.track(x, u, c.dt, start=start, mode="cnn", dhat=dhat)
         st = np.where(want["path_len"] > 0, want["start"], -1)
         for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                        ("status", want["status"]), ("start", st)):
@@ -239,10 +239,10 @@ def test_cnn_start_cells_next_to_cell_faces(ctx, name, kw, stride):
 
 
 def _oracle_cnn_dhat(om, case, flat):
-    """Oracle of the predictor stage: FP64 grid velocity, windows at the
-    particles' cells, FP64 forward."""
+    """Oracle of the predictor stage: FP64 grid velocity, the window of every
+    ASG cell, FP64 forward (the prediction grid)."""
     U = _oracle_grid_u(om, case.u)
-    cells = om.cells(case.x)
+    cells = np.arange(int(np.prod(om.grid)))
     scale = case.dt / ((om.hi - om.lo) / om.grid)
     G = tuple(int(v) for v in om.grid[::-1])
     win = cnn.windows(U.reshape(G + (case.dim,)), cells, case.dim, scale)
@@ -262,8 +262,9 @@ def test_cnn_sns_matches_oracle(ctx):
     out = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn", start_out=True)
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
-    dref = _oracle_cnn_dhat(om, c, flat)
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dref)
+    dgrid = _oracle_cnn_dhat(om, c, flat)
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dgrid)
+    dref = dgrid[om.cnn_origin_cells(c.x, dgrid)[0]]
     plain = om.track(c.x, c.u, c.dt, mode="sns")
     assert np.array_equal(got["host"], want["host"])
     assert np.array_equal(got["host"], plain["host"])          # SNS == CNN-SNS hosts
@@ -451,7 +452,7 @@ def test_track_with_displacements_on_predictor_grid(ctx, name, kw):
     out = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=_dev(dhat), start_out=True)
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat[om.pred_cells(c.x)])
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat)
     start = np.where(want["path_len"] > 0, want["start"], -1)
     for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                    ("status", want["status"]), ("start", start)):
@@ -527,7 +528,7 @@ def test_cnn_sns_on_predictor_grid_keeps_hosts(ctx):
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
     om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy())
     plain = om.track(c.x, c.u, c.dt, mode="sns")
     assert np.array_equal(got["host"], plain["host"])
     for k in ("host", "path_len", "status"):
@@ -592,7 +593,7 @@ def test_cnn_sns_3d_on_tiles_keeps_hosts(ctx):
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
     om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=3)
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy())
     plain = om.track(c.x, c.u, c.dt, mode="sns")
     assert np.array_equal(got["host"], plain["host"])
     for k in ("host", "path_len", "status"):
@@ -620,7 +621,7 @@ def test_full_size_cnn_sns_parity(ctx):
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
     om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"], pred_stride=5)
-    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+    want = om.track(c.x, c.u, c.dt, mode="cnn", dhat=dhat.cpu().numpy())
     start = np.where(want["path_len"] > 0, want["start"], -1)
     for k, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                    ("status", want["status"]), ("start", start)):

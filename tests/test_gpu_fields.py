@@ -82,7 +82,7 @@ def test_two_fields_give_each_call_its_own_predictions(ctx, name, kw, stride):
         got = {kk: v.cpu().numpy() for kk, v in got.items()}
         dh = dhat.cpu().numpy()
         preds.append(dh)
-        want = om.track(x, u, c.dt, start=start, mode="cnn", dhat=dh[om.pred_cells(x)])
+        want = om.track(x, u, c.dt, start=start, mode="cnn", dhat=dh)
         st = np.where(want["path_len"] > 0, want["start"], -1)
         for kk, ref in (("host", want["host"]), ("path_len", want["path_len"]),
                         ("status", want["status"]), ("start", st)):
@@ -125,7 +125,7 @@ def test_field_follows_a_predictor_grid_change(ctx):
         ctx.predict(mesh, c.dt, out=dhat)
         torch.cuda.synchronize()
         want = om.track(c.x, c.u, c.dt, start=start, mode="cnn",
-                        dhat=dhat.cpu().numpy()[om.pred_cells(c.x)])
+                        dhat=dhat.cpu().numpy())
         for k in ("host", "path_len", "status"):
             assert np.array_equal(got[k].cpu().numpy(), want[k]), (stride, k)
     mesh.release()
@@ -226,7 +226,9 @@ def test_error_statistics_match_the_oracle(ctx, name, kw):
         assert np.isclose(st["err_max"], e[ok].max(), rtol=1e-12, atol=0)
         if mode == "cnn":
             xp = c.x - c.u * c.dt
-            dd = metrics.displacement_error(dhat.cpu().numpy()[om.pred_cells(c.x)], om.ps, c.x, xp)
+            dh = dhat.cpu().numpy()
+            pc = om.cnn_origin_cells(c.x, dh)[0]    # the cell the walk's start rule reads
+            dd = metrics.displacement_error(dh[pc], om.ps, c.x, xp)
             assert st["n_disp"] == np.isfinite(dd).sum() == c.n_particles
             assert np.isclose(st["disp_mean"], np.nanmean(dd), rtol=1e-12, atol=0)
             assert np.isclose(st["disp_max"], np.nanmax(dd), rtol=1e-12, atol=0)
