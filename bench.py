@@ -122,6 +122,8 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    result = None
+
     def stop(self):
         if self.proc is None:
             return None
@@ -148,8 +150,9 @@ class ClockSampler:
         os.unlink(self.path)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        self.result = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx,
+                       "reasons": sorted(reasons), "samples": len(sm)}
+        return self.result
 
 
 def particle_set(case, kind):
@@ -161,33 +164,46 @@ def particle_set(case, kind):
     return case.x, case.u, None
 
 
-def cpu_oracle_rate(case, sample_n, seed=0, particles="nodes"):
-    """The oracle as it stands (single-threaded C through ctypes) on a bounded
-    sample of the workload's particles: departure point, Algorithm 1 walk from
-    the plain start, exact host. Returns particles/s and seconds."""
+def cpu_oracle_rate(case, sample_n, seed=0, particles="nodes", threads=1, om=None):
+    """The oracle as it stands (plain C through ctypes; its particle loops on
+    `threads` OpenMP threads) on a bounded sample of the workload's particles:
+    departure point, Algorithm 1 walk from the plain start, exact host.
+    Returns (particles/s, seconds, threads used)."""
     import oracle
-    om = oracle.Mesh(case.xyz, case.conn)
+    if om is None:
+        om = oracle.Mesh(case.xyz, case.conn)
     px, pu, pstart = particle_set(case, particles)
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(px.shape[0], size=min(sample_n, px.shape[0]), replace=False))
     start = om.node_elem[idx] if pstart is None else pstart[idx]
-    t0 = time.perf_counter()
-    om.track(px[idx], pu[idx], case.dt, start=start, mode="sns")
-    dt = time.perf_counter() - t0
-    return idx.size / dt, dt
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        om.track(px[idx], pu[idx], case.dt, start=start, mode="sns")
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return idx.size / dt, dt, used
 
 
 def run_reference(args):
+    """The reference arm: the oracle timed on every host core of the box (no
+    reference code exists besides the paper), each step a bounded sample of
+    the workload."""
     r, w, _ = rank_info()
     if r != 0:
         return 0
+    import oracle
     from workloads import make_case
     wl = WORKLOADS[args.workload]
     case = make_case(wl["name"], cfl=args.cfl, n_side=wl["n_side"])
+    om = oracle.Mesh(case.xyz, case.conn)
+    cores = os.cpu_count() or 1
     sample = args.ref_sample
-    times = []
+    times, used = [], 1
     for i in range(args.warmup + args.steps):
-        _, dt = cpu_oracle_rate(case, sample, seed=i, particles=args.particles)
+        _, dt, used = cpu_oracle_rate(case, sample, seed=i, particles=args.particles,
+                                      threads=cores, om=om)
         if i >= args.warmup:
             times.append(dt)
     per_step = float(np.mean(times))
@@ -200,8 +216,9 @@ def run_reference(args):
         "config": {"workload": wl["desc"] + ", CFL %g" % args.cfl,
                    "mode": "sns (the oracle's Algorithm 1 walk + exact host)",
                    "sample_particles": sample},
-        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d particles drawn from the workload per step" % sample},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": used, "kind": "oracle",
+                         "sample": "%d particles drawn from the workload per step, on %d "
+                                   "OpenMP threads" % (sample, used)},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -320,6 +337,176 @@ def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed, pred_s
     return rep
 
 
+class Runner:
+    """Times tracking steps of one workload through the library's C ABI.
+
+    A step locates every particle once (cs_track, inputs resident in HBM) on
+    the current stream; L2 is flushed by a 256 MB write before every timed
+    step, outside the step's events. The timed steps run uninstrumented; the
+    per-stage device times (and each roofline's kernel time) come from a
+    second, profiled pass over the same steps, whose event records would
+    otherwise sit between the kernels of every timed step. An untimed pass
+    with start_out then gives the error statistics of Sec. 3.1."""
+
+    def __init__(self, ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks):
+        import torch
+        self.torch = torch
+        self.ctx, self.mesh, self.case, self.field = ctx, mesh, case, field
+        self.flush, self.dev, self.dist, self.max_over_ranks = flush, dev, dist, max_over_ranks
+        self.x = torch.from_numpy(px).to(dev)
+        self.u = torch.from_numpy(pu).to(dev)
+        self.start = None if pstart is None else torch.from_numpy(pstart).to(dev)
+        self.n = px.shape[0]
+        n = self.n
+        self.out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
+                        path_len=torch.empty(n, dtype=torch.int32, device=dev),
+                        status=torch.empty(n, dtype=torch.uint8, device=dev))
+        self.stream = torch.cuda.current_stream(dev)
+        self.world = dist.get_world_size() if dist is not None else 1
+
+    def step(self, mode, dt, out=None, start_out=False):
+        return self.ctx.track(self.mesh, self.x, self.u, dt, start=self.start, mode=mode,
+                              out=out if out is not None else self.out, stream=self.stream,
+                              field=self.field, start_out=start_out)
+
+    def run_steps(self, mode, dt, steps):
+        torch = self.torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for i in range(steps):
+            self.flush.fill_(i & 0xff)
+            ev[i][0].record(self.stream)
+            self.step(mode, dt)
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    def measure(self, mode, steps, warmup, sampler=None, dt=None):
+        torch, ctx = self.torch, self.ctx
+        dt = self.case.dt if dt is None else dt
+        for _ in range(warmup):
+            self.step(mode, dt)
+        torch.cuda.synchronize()
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.start()
+        l0 = ctx.launches
+        # an NVTX range names the timed steps, so that a profiler can select
+        # them (ncu --nvtx --nvtx-include "timed_cnn/")
+        marked = nvtx_push("timed_" + mode)
+        total = self.run_steps(mode, dt, steps)
+        if marked:
+            torch.cuda.nvtx.range_pop()
+        launches = ctx.launches - l0
+        if sampler is not None:
+            sampler.stop()
+        if self.dist is not None:
+            total = self.max_over_ranks(total, device=self.dev)
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        st = ctx.stats(self.out["path_len"], self.out["status"])
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        self.run_steps(mode, dt, min(steps, 200))
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        # error statistics (untimed): origin error err for every start rule,
+        # the predictor's displacement error for CNN-SNS
+        o = ctx.track(self.mesh, self.x, self.u, dt, start=self.start, mode=mode,
+                      stream=self.stream, field=self.field, start_out=True)
+        dhat = None
+        if mode == "cnn" and self.field is None:
+            # the prediction of this call: the same kernel on the mesh's stored
+            # grid velocity, which the call has just resampled from u
+            cells = int(np.prod(self.mesh.info()["pred_grid"]))
+            dhat = torch.empty((cells, self.case.dim), dtype=torch.float32, device=self.dev)
+            ctx.predict(self.mesh, dt, out=dhat)
+        err = ctx.track_error(self.mesh, self.x, self.u, dt, o["host"], start=o["start"], dhat=dhat)
+        mps = total / steps
+        n = self.n
+        r = dict(particles_per_s=self.world * n / (mps * 1e-3), ms_per_step=mps,
+                 mean_path_len=st["sum"] / n, max_path_len=st["max"],
+                 status_counts=[st["found"], st["outside"], st["fallback"], st["invalid"]],
+                 stage_ms_per_step={k: v[1] / max(1, v[0]) for k, v in prof.items() if v[0]},
+                 err_mean=err["err_mean"], err_max=err["err_max"])
+        if err["n_disp"]:
+            r["disp_err_mean"] = err["disp_mean"]
+            r["disp_err_max"] = err["disp_max"]
+            r["disp_err_mean_cells"] = err["disp_mean"] / float(np.mean(
+                (np.array(self.mesh.info()["hi"]) - np.array(self.mesh.info()["lo"]))
+                / np.array(self.mesh.info()["pred_grid"])))
+        return r, prof, launches
+
+
+def opt_rates(results):
+    """Opt(C) = (C(SNS) - C(CNN-SNS)) / C(SNS) (Sec. 3.1) for the mean path
+    length, the step time and the origin error err, and the same rates of
+    CNN-SNS against the non-learned ASG-direct start."""
+    out = {}
+    if "cnn" not in results:
+        return out
+    c = results["cnn"]
+    for base in ("sns", "asg"):
+        if base in results:
+            b = results[base]
+            out["vs_" + base] = {
+                "opt_mean_path": (b["mean_path_len"] - c["mean_path_len"]) / b["mean_path_len"],
+                "opt_time": (b["ms_per_step"] - c["ms_per_step"]) / b["ms_per_step"],
+                "opt_err": ((b["err_mean"] - c["err_mean"]) / b["err_mean"]
+                            if b["err_mean"] > 0 else None),
+                "speedup": b["ms_per_step"] / c["ms_per_step"]}
+    return out
+
+
+def sweep(ctx, cs, args, rank, dev, dist, max_over_ranks, flush, tg_case, tg_mesh):
+    """The configuration list beside the headline: the 1001^2 Taylor-Green
+    mesh at CFL 1, 4, 8, 16 and the 101^3 ABC cube at CFL 4, 8, 12, 16, 20,
+    each in plain SNS, ASG-direct and CNN-SNS (the 2-D predictor trained for
+    the headline; a 3-D one trained here the same way)."""
+    from workloads import make_case
+    from workloads.fields import dt_for_cfl
+    steps = max(10, min(args.steps, 50))
+    out = []
+    for wname, mesh, case, cfls in (("tg2d", tg_mesh, tg_case, (1, 4, 8, 16)),
+                                    ("abc3d", None, None, (4, 8, 12, 16, 20))):
+        t0 = time.perf_counter()
+        training = None
+        if mesh is None:
+            case = make_case(wname, cfl=8.0, n_side=WORKLOADS[wname]["n_side"])
+            mesh = ctx.upload_mesh(case.xyz, case.conn)
+            mesh.set_predictor_grid(args.pred_stride_3d)
+            training = train_predictor(ctx, mesh, case, args.train_fields_3d,
+                                       args.train_steps_3d, args.train_batch, seed=rank)
+        run = Runner(ctx, mesh, case, case.x, case.u, None, None, flush, dev, dist,
+                     max_over_ranks)
+        rows = []
+        for cfl in cfls:
+            dt = dt_for_cfl(case.u, case.h, cfl)
+            res = {}
+            for mode in ("sns", "asg", "cnn"):
+                r, _, _ = run.measure(mode, steps, 3, dt=dt)
+                res[mode] = {k: r[k] for k in ("ms_per_step", "particles_per_s", "mean_path_len",
+                                               "max_path_len", "err_mean", "stage_ms_per_step")
+                             if k in r}
+                for k in ("disp_err_mean", "disp_err_max"):
+                    if k in r:
+                        res[mode][k] = r[k]
+            rows.append({"cfl": cfl, "modes": res, "opt": opt_rates(res)})
+        entry = {"workload": WORKLOADS[wname]["desc"], "n_particles": case.n_particles,
+                 "n_elements": case.n_elements,
+                 "predictor_grid": mesh.info()["pred_grid"], "steps_per_point": steps,
+                 "rows": rows, "seconds": time.perf_counter() - t0}
+        if training is not None:
+            entry["training"] = training
+        out.append(entry)
+        if wname != "tg2d":
+            mesh.release()
+        del run
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,11 +521,18 @@ def main():
                          "((d + 1) n_e particles, each starting from its element)")
     ap.add_argument("--pred-stride", type=int, default=5,
                     help="ASG cells per predictor cell and axis (odd)")
+    ap.add_argument("--pred-stride-3d", type=int, default=7,
+                    help="the same for the 3-D workload of the sweep")
+    ap.add_argument("--train-fields-3d", type=int, default=4)
+    ap.add_argument("--train-steps-3d", type=int, default=3000)
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the CFL sweep over the 2-D and 3-D workloads")
     ap.add_argument("--train-fields", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
-    ap.add_argument("--ref-sample", type=int, default=200000)
+    ap.add_argument("--ref-sample", type=int, default=1002001)
     ap.add_argument("--cpu-sample", type=int, default=200000)
+    ap.add_argument("--cpu-sample-all", type=int, default=1002001)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
@@ -349,6 +543,7 @@ def main():
     args = ap.parse_args()
     if args.quick:
         args.no_cpu_baseline = True
+        args.no_sweep = True
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -386,88 +581,29 @@ def main():
                                    args.train_batch, seed=rank)
 
     px, pu, pstart = particle_set(case, args.particles)
-    x = torch.from_numpy(px).to(dev)
-    u = torch.from_numpy(pu).to(dev)
-    start = None if pstart is None else torch.from_numpy(pstart).to(dev)
-    n = px.shape[0]
     field = None
-    if start is not None and "cnn" in modes:
+    if pstart is not None and "cnn" in modes:
         # particles that are not the mesh nodes: the predictor reads the
         # resident field of the nodal velocity
         field = ctx.upload_field(mesh, case.u)
-    out = dict(host=torch.empty(n, dtype=torch.int32, device=dev),
-               path_len=torch.empty(n, dtype=torch.int32, device=dev),
-               status=torch.empty(n, dtype=torch.uint8, device=dev))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step(mode):
-        ctx.track(mesh, x, u, case.dt, start=start, mode=mode, out=out, stream=stream,
-                  field=field)
-
-    def run_steps(mode, steps):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        for i in range(steps):
-            flush.fill_(i & 0xff)
-            ev[i][0].record(stream)
-            step(mode)
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev)
-
-    def timed(mode, steps, warmup):
-        """The timed steps run uninstrumented; the per-stage device times (and
-        the kernel time of the rooflines) come from a second, profiled pass
-        over the same steps, whose event records would otherwise sit between
-        the kernels of every timed step."""
-        for _ in range(warmup):
-            step(mode)
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        l0 = ctx.launches
-        # an NVTX range names the timed steps, so that a profiler can select
-        # them (ncu --nvtx --nvtx-include "timed_cnn/")
-        marked = nvtx_push("timed_" + mode)
-        total = run_steps(mode, steps)
-        if marked:
-            torch.cuda.nvtx.range_pop()
-        launches = ctx.launches - l0
-        if dist is not None:
-            total = max_over_ranks(total, device=dev)
-            dist.barrier()
-        torch.cuda.synchronize()
-        st = ctx.stats(out["path_len"], out["status"])
-        ctx.profile(True)
-        ctx.profile_read(reset=True)
-        run_steps(mode, min(steps, 200))
-        prof = ctx.profile_read(reset=True)
-        ctx.profile(False)
-        return total, prof, launches, st
+    run = Runner(ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks)
 
     results = {}
     main_prof = main_launches = None
     clocks = None
     for mode in [args.mode] + [m for m in modes if m != args.mode]:
         steps = args.steps if mode == args.mode else max(3, args.steps // 4)
-        if mode == args.mode:
-            sampler = ClockSampler(lrank)
-            sampler.start()
-        total, prof, launches, st = timed(mode, steps, args.warmup)
-        if mode == args.mode:
-            clocks = sampler.stop()
+        sampler = ClockSampler(lrank) if mode == args.mode else None
+        r, prof, launches = run.measure(mode, steps, args.warmup, sampler)
+        if sampler is not None:
+            clocks = sampler.result
             main_prof, main_launches = prof, launches
-        mps = total / steps
-        results[mode] = dict(particles_per_s=world * n / (mps * 1e-3), ms_per_step=mps,
-                             mean_path_len=st["sum"] / n, max_path_len=st["max"],
-                             status_counts=[st["found"], st["outside"], st["fallback"],
-                                            st["invalid"]],
-                             stage_ms_per_step={k: v[1] / max(1, v[0])
-                                                for k, v in prof.items() if v[0]})
+        results[mode] = r
     ctx.device_status()
     main = results[args.mode]
+    n = px.shape[0]
+    opt = opt_rates(results)
 
     # rooflines: the walk (HBM gather) and the grid predictor (tensor cores)
     hbm_peak, bf16_peak, peak_kind = peaks()
@@ -523,13 +659,24 @@ def main():
         serving = serve_bench(ctx, mesh, case, args.serve_requests, args.serve_rate,
                               args.serve_slots, seed=100 + rank, pred_stride=args.pred_stride)
 
+    sweep_rows = None
+    if not args.no_sweep and args.particles == "nodes" and args.workload == "tg2d":
+        sweep_rows = sweep(ctx, cs, args, rank, dev, dist, max_over_ranks, flush, case, mesh)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt_cpu = cpu_oracle_rate(case, args.cpu_sample, particles=args.particles)
-        cpu = {"value": rate, "unit": "particles/s", "cores": 1, "kind": "oracle",
-               "sample": "%d of the %d particles (seeded draw), the oracle's plain SNS: "
-                         "departure point + Algorithm 1 walk + exact host, %.2f s"
-                         % (args.cpu_sample, n, dt_cpu)}
+        import oracle
+        om = oracle.Mesh(case.xyz, case.conn)
+        rate1, dt1, _ = cpu_oracle_rate(case, args.cpu_sample, particles=args.particles, om=om)
+        cores = os.cpu_count() or 1
+        rate_all, dt_all, used = cpu_oracle_rate(case, args.cpu_sample_all,
+                                                 particles=args.particles, threads=cores, om=om)
+        cpu = {"value": rate_all, "unit": "particles/s", "cores": used, "kind": "oracle",
+               "sample": "%d of the %d particles (seeded draw), the oracle's plain SNS: departure "
+                         "point + Algorithm 1 walk + exact host, its particle loops on %d OpenMP "
+                         "threads, %.2f s" % (min(args.cpu_sample_all, n), n, used, dt_all),
+               "single_core": {"value": rate1, "unit": "particles/s", "cores": 1,
+                               "sample": "%d particles, %.2f s" % (min(args.cpu_sample, n), dt1)}}
 
     if rank == 0:
         line = {
@@ -556,7 +703,8 @@ def main():
                            "predictor BF16 x BF16 -> FP32 on tcgen05" if dim == 2 else
                            "predictor BF16-operand window GEMMs, FP32 accumulation, CUDA cores")},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],
-            "modes": results, "training": training, "serving": serving,
+            "err_mean": main["err_mean"], "modes": results, "opt": opt,
+            "training": training, "serving": serving, "sweep": sweep_rows,
             "rooflines": rooflines,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": main_launches, "clocks": clocks,

@@ -38,6 +38,7 @@ def lib():
     path = _build.build()
     L = ctypes.CDLL(path)
     sig = {
+        "or_set_threads": (ctypes.c_int, [ctypes.c_int]),
         "or_neighbors": (ctypes.c_int, [ctypes.c_int, _i64t, _i32, _i32]),
         "or_neighbors_bruteforce": (ctypes.c_int, [ctypes.c_int, _i64t, _i32, _i32]),
         "or_inverse_affine": (_i64t, [ctypes.c_int, _f64, _i64t, _i32, _f64, _f64]),
@@ -64,6 +65,12 @@ def lib():
         fn.restype = res
         fn.argtypes = args
     return L
+
+
+def set_threads(n):
+    """Threads of the walk and exact-location loops (1 by default); returns
+    the count in effect (1 when the library has no OpenMP)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def _p(a, ct):

@@ -10,6 +10,23 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Threads of the particle loops of or_walk and or_locate_bucketed (OpenMP,
+ * when the library is built with it). The particles are independent, so the
+ * results do not depend on the count; it is 1 unless or_set_threads raises
+ * it (the benchmark's all-core CPU baseline). */
+static int g_threads = 1;
+
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n > 0 ? n : 1;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Neighbour table (Sec. 2.2: m_1^l..m_4^l, -1 for a boundary face)          */
 /* ------------------------------------------------------------------------ */
@@ -260,6 +277,9 @@ void or_locate_bruteforce(int dim, int64_t n_e, const double *v0,
                           const double *M, int64_t n, const double *pts,
                           double eps, int32_t *host)
 {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t q = 0; q < n; ++q) {
         const double *p = pts + q * dim;
         host[q] = -1;
@@ -341,6 +361,9 @@ int or_locate_bucketed(int dim, int64_t n_v, const double *xyz, int64_t n_e,
                     items[fill[c]++] = (int32_t)l;
                 }
     }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t q = 0; q < n; ++q) {
         const double *p = pts + q * dim;
         host[q] = -1;
@@ -379,6 +402,9 @@ void or_walk(int dim, const double *v0, const double *M, const int32_t *nbr,
              int32_t cap, int32_t *end, int32_t *path_len, uint8_t *reason)
 {
     const int nv = dim + 1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(g_threads) if (g_threads > 1)
+#endif
     for (int64_t q = 0; q < n; ++q) {
         const double *p = pts + q * dim;
         int32_t cur = start[q];

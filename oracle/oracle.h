@@ -76,6 +76,10 @@ int or_locate_bucketed(int dim, int64_t n_v, const double *xyz, int64_t n_e,
                        int32_t *host);
 
 /* Algorithm 1 (SNS) from start[p]; end element, I_t and exit reason. */
+/* Threads of the particle loops (OpenMP builds; 1 otherwise); returns the
+ * count in effect. Results do not depend on it. */
+int or_set_threads(int n);
+
 void or_walk(int dim, const double *v0, const double *M, const int32_t *nbr,
              int64_t n, const double *pts, const int32_t *start, double eps,
              int32_t cap, int32_t *end, int32_t *path_len, uint8_t *reason);

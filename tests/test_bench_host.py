@@ -66,5 +66,20 @@ def test_committed_summaries_name_their_sources():
 @pytest.mark.parametrize("particles", ["nodes", "element-nodes"])
 def test_cpu_baseline_on_a_sample(particles):
     c = make_case("rotation2d")
-    rate, seconds = bench.cpu_oracle_rate(c, 500, seed=1, particles=particles)
-    assert rate > 0 and seconds > 0
+    rate, seconds, used = bench.cpu_oracle_rate(c, 500, seed=1, particles=particles)
+    assert rate > 0 and seconds > 0 and used == 1
+    rate, seconds, used = bench.cpu_oracle_rate(c, 500, seed=1, particles=particles, threads=2)
+    assert rate > 0 and seconds > 0 and used in (1, 2)
+
+
+def test_opt_rates_follow_the_paper_definition():
+    """Opt(C) = (C(SNS) - C(CNN-SNS)) / C(SNS), Sec. 3.1; checked on the
+    lid-driven cavity values of Table 1 (N_e 8.192e7): mean I_t 11.561 ->
+    4.305 gives 62.8%, time 137.233 -> 72.814 s gives 46.9%."""
+    res = {"sns": dict(mean_path_len=11.561, ms_per_step=137.233, err_mean=0.0123),
+           "cnn": dict(mean_path_len=4.305, ms_per_step=72.814, err_mean=0.0058)}
+    o = bench.opt_rates(res)["vs_sns"]
+    assert abs(o["opt_mean_path"] - 0.628) < 5e-4
+    assert abs(o["opt_time"] - 0.469) < 5e-4
+    assert abs(o["opt_err"] - 0.528) < 5e-4
+    assert abs(o["speedup"] - 137.233 / 72.814) < 1e-12

@@ -50,7 +50,8 @@ def _check(got, want, what):
 
 @pytest.mark.parametrize("name,kw", [("tg2d", {"n_side": 101, "cfl": 8}),
                                      ("abc3d", {"n_side": 11, "cfl": 8}),
-                                     ("hole2d", {"n_side": 61})])
+                                     ("hole2d", {"n_side": 61}),
+                                     ("sphere3d", {"n_side": 21})])
 def test_element_node_particles(ctx, name, kw):
     c = make_case(name, **kw)
     mesh = ctx.upload_mesh(c.xyz, c.conn)

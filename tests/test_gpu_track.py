@@ -61,6 +61,8 @@ CASES = [
     ("abc3d", {"n_side": 21, "cfl": 20}),
     ("hole2d", {"n_side": 61}),      # non-convex: walks blocked by the hole
     ("hole2d", {"n_side": 121}),
+    ("sphere3d", {"n_side": 25}),    # non-convex in 3-D: walks blocked by the ball
+    ("sphere3d", {"n_side": 41}),
 ]
 
 
@@ -256,3 +258,16 @@ def test_equal_minima_leave_through_the_lowest_local_index(ctx):
         _compare(got, want, name)
         assert (got["path_len"] == (2 if face == 1 else 1)).all(), name
         mesh.release()
+
+
+def test_non_convex_3d_domain_uses_the_exact_search(ctx):
+    """The cube with a ball taken out: walks that meet the ball's surface with
+    the departure point beyond it end in the exact search (FOUND_VIA_FALLBACK),
+    bit for bit with the oracle, and are a visible share of the particles."""
+    c = make_case("sphere3d", n_side=41)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    om = oracle.Mesh(c.xyz, c.conn, grid=mesh.info()["asg_grid"])
+    got = _run(ctx, mesh, c)
+    _compare(got, _oracle_out(om, om.track(c.x, c.u, c.dt)), "sphere3d")
+    assert (got["status"] == 2).sum() > 100
+    mesh.release()

@@ -54,3 +54,58 @@ def test_walks_blocked_by_the_hole_end_in_the_exact_search():
     assert np.array_equal(r["status"][blocked] == oracle.ST_FALLBACK, r["host"][blocked] >= 0)
     assert (r["status"] == oracle.ST_FALLBACK).sum() > 20
     assert (r["status"][~blocked] == oracle.ST_FOUND).all()
+
+
+# --- 3-D: the cube with a ball taken out (the flow past a sphere, Sec. 3.2) --
+
+def test_sphere_mesh_is_valid_and_has_the_ball():
+    """Every tetrahedron keeps a non-zero volume, every vertex is used, the
+    volume is the cube's minus exactly the dropped tetrahedra, and no
+    remaining tetrahedron has its centroid in the ball."""
+    from workloads.meshes import mesh_3d_sphere, mesh_3d
+    xyz, conn, h = mesh_3d_sphere(17, 0.25)
+    full_xyz, full_conn, _ = mesh_3d(17, 0.1, 11)
+    def vol(x, c):
+        a = x[c[:, 1]] - x[c[:, 0]]
+        b = x[c[:, 2]] - x[c[:, 0]]
+        d = x[c[:, 3]] - x[c[:, 0]]
+        return np.einsum("ij,ij->i", a, np.cross(b, d)) / 6.0
+    v = vol(xyz, conn)
+    assert (np.abs(v) > 0).all()
+    assert np.array_equal(np.unique(conn), np.arange(xyz.shape[0]))
+    assert np.linalg.norm(xyz[conn].mean(axis=1) - 0.5, axis=1).min() > 0.25
+    vf = vol(full_xyz, full_conn)
+    cen = full_xyz[full_conn].mean(axis=1)
+    dropped = np.linalg.norm(cen - 0.5, axis=1) <= 0.25
+    assert abs(np.abs(vf).sum() - 1.0) < 1e-12
+    assert abs(np.abs(v).sum() - (1.0 - np.abs(vf[dropped]).sum())) < 1e-12
+    assert dropped.sum() > 100
+
+
+def test_sphere_exact_location_against_brute_force_and_the_ball():
+    from workloads.meshes import mesh_3d_sphere
+    xyz, conn, h = mesh_3d_sphere(17, 0.25)
+    om = oracle.Mesh(xyz, conn, brute_limit=0)            # bucketed search
+    rng = np.random.default_rng(4)
+    pts = rng.random((4000, 3)) * 1.1 - 0.05
+    got = om.locate(pts)
+    v0, M = oracle.inverse_affine(xyz, conn)
+    ref = oracle.locate_bruteforce(v0, M, pts, oracle.EPS)
+    assert np.array_equal(got, ref)
+    r = np.linalg.norm(pts - 0.5, axis=1)
+    inside_cube = (pts >= 0).all(axis=1) & (pts <= 1).all(axis=1)
+    # a tetrahedron is dropped only if its centroid is in the ball, so its
+    # points lie within radius + (its size, < 2h) of the centre; one kept has
+    # its centroid outside, so it covers no point deeper than radius - 2h
+    assert (got[(r < 0.25 - 2 * h) | ~inside_cube] == -1).all()
+    assert (got[inside_cube & (r > 0.25 + 2 * h)] >= 0).all()
+
+
+def test_sphere_walks_blocked_by_the_ball_end_in_the_exact_search():
+    c = make_case("sphere3d", n_side=21)
+    om = oracle.Mesh(c.xyz, c.conn)
+    r = om.track(c.x, c.u, c.dt, mode="sns")
+    blocked = r["reason"] == oracle.BOUNDARY
+    assert np.array_equal(r["status"][blocked] == oracle.ST_FALLBACK, r["host"][blocked] >= 0)
+    assert (r["status"] == oracle.ST_FALLBACK).sum() > 20
+    assert (r["status"][~blocked] == oracle.ST_FOUND).all()

@@ -412,3 +412,21 @@ def test_displacement_error_closed_forms():
     off = exact + np.array([3.0, 4.0])
     e = metrics.displacement_error(off.astype(np.float32), s, x, xp)
     assert np.isclose(e[0], np.sqrt(3.25), rtol=0, atol=1e-15)
+
+
+def test_oracle_threads_do_not_change_results():
+    """The all-core CPU baseline runs the oracle's particle loops on OpenMP
+    threads; particles are independent, so every output is the same bits as
+    the single-threaded run."""
+    c = make_case("tg2d", n_side=151, cfl=8)
+    m = oracle.Mesh(c.xyz, c.conn, brute_limit=0)
+    oracle.set_threads(1)
+    one = m.track(c.x, c.u, c.dt)
+    try:
+        used = oracle.set_threads(4)
+        many = m.track(c.x, c.u, c.dt)
+    finally:
+        oracle.set_threads(1)
+    assert used in (1, 4)
+    for k in ("host", "path_len", "status", "start"):
+        assert np.array_equal(one[k], many[k]), k

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .meshes import mesh_2d, mesh_2d_hole, mesh_3d
+from .meshes import mesh_2d, mesh_2d_hole, mesh_3d, mesh_3d_sphere
 from .fields import (rotation, taylor_green, abc_flow, fourier_modes_2d,
                      fourier_modes_3d, dt_for_cfl)
 
@@ -71,6 +71,16 @@ def make_case(name, cfl=None, n_side=None, seed=None, field_seed=None):
         xyz, conn, h = mesh_2d_hole(n_side, 0.1, 0.3, 7 if seed is None else seed)
         u = np.ascontiguousarray(np.broadcast_to(np.array([0.94, 0.34]), xyz.shape))
         cfl = 16.0 if cfl is None else cfl
+    elif name == "sphere3d":
+        # uniform flow past a ball-shaped hole in the cube (the geometry of
+        # the paper's second benchmark): walks behind the ball meet its
+        # boundary, and some departure points fall into it
+        n_side = n_side or 51
+        xyz, conn, h = mesh_3d_sphere(n_side, 0.2, 0.1, 11 if seed is None else seed)
+        d = np.array([0.90, 0.35, 0.25])
+        u = np.ascontiguousarray(np.broadcast_to(d / np.linalg.norm(d), xyz.shape))
+        cfl = 0.16 / h if cfl is None else cfl      # a displacement of 0.16
+
     elif name == "modes3d":
         n_side = n_side or 41
         xyz, conn, h = mesh_3d(n_side, 0.1, 200 if seed is None else seed)

@@ -171,6 +171,31 @@ def mesh_3d(n_side, jitter=0.1, seed=3):
     return _mesh_3d_cached(int(n_side), float(jitter), int(seed))
 
 
+@functools.lru_cache(maxsize=4)
+def _mesh_3d_sphere_cached(n_side, radius, jitter, seed):
+    xyz, conn, h = kuhn_3d(n_side, jitter, seed)
+    c = np.array([0.5, 0.5, 0.5])
+    cen = xyz[conn].mean(axis=1)
+    conn = conn[np.linalg.norm(cen - c, axis=1) > radius]
+    used = np.unique(conn)                       # drop vertices no tetrahedron uses
+    remap = np.full(xyz.shape[0], -1, dtype=np.int64)
+    remap[used] = np.arange(used.shape[0])
+    xyz = np.ascontiguousarray(xyz[used])
+    conn = np.ascontiguousarray(remap[conn].astype(np.int32))
+    xyz.setflags(write=False)
+    conn.setflags(write=False)
+    return xyz, conn, h
+
+
+def mesh_3d_sphere(n_side, radius=0.2, jitter=0.1, seed=11):
+    """(xyz, conn, h): the jittered Kuhn cube with a ball of `radius` at its
+    centre taken out, the obstacle of the flow past a sphere (a non-convex
+    domain: walks can meet the ball's boundary while the departure point lies
+    in the domain beyond it). Tetrahedra whose centroid lies in the ball are
+    dropped, then the vertices no tetrahedron uses (read-only, cached)."""
+    return _mesh_3d_sphere_cached(int(n_side), float(radius), float(jitter), int(seed))
+
+
 def tie_meshes():
     """Two-element meshes in which the start element's smallest barycentric
     coordinates are exactly equal at the query point: element 0 is the unit
