@@ -521,7 +521,7 @@ def main():
                          "((d + 1) n_e particles, each starting from its element)")
     ap.add_argument("--pred-stride", type=int, default=5,
                     help="ASG cells per predictor cell and axis (odd)")
-    ap.add_argument("--pred-stride-3d", type=int, default=7,
+    ap.add_argument("--pred-stride-3d", type=int, default=5,
                     help="the same for the 3-D workload of the sweep")
     ap.add_argument("--train-fields-3d", type=int, default=4)
     ap.add_argument("--train-steps-3d", type=int, default=3000)
@@ -699,9 +699,8 @@ def main():
                        "parallelism": ("%d replicas: every rank locates its own batch of %d particles "
                                         "against its own copy of the mesh, no collective"
                                         % (world, n)) if world > 1 else "1 GPU",
-                       "arithmetic": "walk decisions FP64 (certified FP32 filter); " + (
-                           "predictor BF16 x BF16 -> FP32 on tcgen05" if dim == 2 else
-                           "predictor BF16-operand window GEMMs, FP32 accumulation, CUDA cores")},
+                       "arithmetic": "walk decisions FP64 (certified FP32 filter); predictor "
+                                     "BF16 x BF16 -> FP32 on tcgen05"},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],
             "err_mean": main["err_mean"], "modes": results, "opt": opt,
             "training": training, "serving": serving, "sweep": sweep_rows,

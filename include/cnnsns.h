@@ -251,10 +251,12 @@ cs_status cs_track_noalloc(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64
 /* ------------------------------------------------------------------------ */
 
 /* Engine of grid prediction (cs_predict, CS_CNN_SNS): 1 (default) = fully
- * convolutional over the predictor grid: the fused tensor-core kernel
- * (tcgen05) in 2-D, cubic tiles of im2col + GEMM layers on CUDA cores in 3-D;
- * 0 = every cell's own window through the same GEMM layers (both dims; the
- * reference the grid engines are tested against). */
+ * convolutional over the predictor grid on the tensor cores (fused tcgen05
+ * kernels, 2-D and 3-D); 2 = the same fully convolutional pass in 3-D as
+ * cubic tiles of implicit-GEMM layers on CUDA cores (2-D runs the tensor
+ * cores); 0 = every cell's own window through the same GEMM layers (both
+ * dims; the reference the grid engines are tested against). CS_EBUSY while
+ * serving. */
 cs_status cs_predictor_engine(cs_ctx *ctx, int engine);
 
 /* Output rows per tile of the 2-D tensor-core grid kernel: 24, 13 or 8, or
@@ -262,6 +264,11 @@ cs_status cs_predictor_engine(cs_ctx *ctx, int engine);
  * waves of one tile per SM, weighted by each height's pipeline length).
  * Results do not depend on it. CS_EINVAL for any other value. */
 cs_status cs_predictor_tile_rows(cs_ctx *ctx, int rows);
+
+/* Side of the cubic output tiles of the 3-D tensor-core grid kernel: 4, 3 or
+ * 2 cells, or 0 (default) for the side whose tiles best fill the GPU's SMs.
+ * Results do not depend on it. CS_EINVAL for any other value. */
+cs_status cs_predictor_tile3(cs_ctx *ctx, int side);
 
 /* Synchronise the device and report whether a bounded device-side wait gave
  * up since the last call (CS_EDEVICE, message in cs_last_error) or CS_OK. */
@@ -375,11 +382,12 @@ cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
 /* are identical to cs_track_host on the same inputs. Meshes, fields and     */
 /* predictor weights must be resident before cs_serve_start and unchanged    */
 /* while serving (mesh, field and predictor-grid changes return CS_EBUSY).   */
-/* A CNN-SNS request runs the grid predictor of its dimension (tensor cores  */
-/* in 2-D, the tile engine in 3-D, whose shared workspace serialises the 3-D */
-/* predictions while the walks still overlap) on its field's grid velocity,  */
-/* or on its own u when its particles are the mesh nodes; without a loaded  */
-/* predictor, or with neither, it falls back to plain SNS.                   */
+/* A CNN-SNS request runs the grid predictor of its dimension on the tensor  */
+/* cores (with engine 2 the 3-D tile engine, whose shared workspace           */
+/* serialises the 3-D predictions while the walks still overlap) on its      */
+/* field's grid velocity, or on its own u when its particles are the mesh    */
+/* nodes; without a loaded predictor, or with neither, it falls back to      */
+/* plain SNS.                                                                */
 /* ------------------------------------------------------------------------ */
 typedef struct cs_serve_cfg {
     int32_t slots;          /* concurrent requests on the GPU (1..64)        */

@@ -317,10 +317,16 @@ class Context:
 
     # ---------------- start predictor ----------------
     def predictor_engine(self, engine):
-        """'grid' (alias 'tc'): fully convolutional over the predictor grid
-        (tensor cores in 2-D, CUDA-core tiles in 3-D); 'window': every cell's
-        own window through CUDA-core GEMMs."""
-        self._check(self.lib.cs_predictor_engine(self.h, 1 if engine in ("tc", "grid") else 0))
+        """'grid' (alias 'tc'): fully convolutional over the predictor grid on
+        the tensor cores; 'tiles': the same pass on CUDA cores in 3-D;
+        'window': every cell's own window through CUDA-core GEMMs."""
+        code = {"tc": 1, "grid": 1, "tiles": 2, "window": 0}[engine]
+        self._check(self.lib.cs_predictor_engine(self.h, code))
+
+    def predictor_tile3(self, side=0):
+        """Side of the 3-D tensor-core kernel's output tiles: 4, 3, 2 or 0
+        (automatic)."""
+        self._check(self.lib.cs_predictor_tile3(self.h, int(side)))
 
     def predictor_tile_rows(self, rows=0):
         """Tile height of the 2-D tensor-core grid kernel: 24, 13 or 8 rows,

@@ -68,6 +68,13 @@ int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *
                     float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st);
 // the tile height with the least estimated cost on a grid (24, 13 or 8)
 int tc_pick_tile_rows(const DevMesh &m, int sm_count);
+// tensor-core grid inference of the 3-D predictor (cnn3d_tc.cu); tile: side of
+// the cubic output tiles (4, 3 or 2), 0 = tc3_pick_tile
+int64_t tc3_packed_bytes();
+int launch_pack_tc3(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
+int launch_cnn3d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+                    float *dhat, int *err, int sm_count, int tile, cudaStream_t st);
+int tc3_pick_tile(const DevMesh &m, int sm_count);
 int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, double dt,
                  int64_t *cells, float *target, int sm_count, cudaStream_t st);
 int launch_gather_rows(const float *src, int64_t row, const int64_t *idx, int64_t B, float *dst,

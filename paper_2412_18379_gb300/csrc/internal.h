@@ -255,8 +255,9 @@ struct cs_ctx {
     cs::Scratch scratch;
     cs::Profiler prof;
     cs::Predictor pred[2];   // dim 2, dim 3
-    int engine = 1;          // grid prediction: 1 tensor cores (2-D), 0 window GEMMs
-    int tc_tile_rows = 0;    // tensor-core predictor tile height, 0 = automatic
+    int engine = 1;          // grid prediction: 1 tensor cores, 0 window GEMMs, 2 CUDA-core tiles (3-D)
+    int tc_tile_rows = 0;    // 2-D tensor-core predictor tile height, 0 = automatic
+    int tc3_tile = 0;        // 3-D tensor-core predictor tile side, 0 = automatic
     int *dev_err = nullptr;  // device error flag of bounded waits
     cs::Server *server = nullptr;   // serving loop (serve.cpp), if started
     std::atomic<int64_t> launches{0};

@@ -376,10 +376,11 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
     Predictor *P = get_pred(ctx, m->d.dim);
     if (!P || !P->loaded) return fail(ctx, CS_ENOPRED, "no predictor loaded for this dimension");
     if (!grid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
-    if (m->d.dim == 2 && ctx->engine == 1) {
-        // tensor-core grid kernel: weights repacked after every load / training
+    if (ctx->engine == 1) {
+        // tensor-core grid kernels: weights repacked after every load / training
+        const int64_t bytes = m->d.dim == 2 ? tc_packed_bytes() : tc3_packed_bytes();
         if (!P->packed) {
-            cs_status rc = dalloc(ctx, &P->packed, size_t(tc_packed_bytes()));
+            cs_status rc = dalloc(ctx, &P->packed, size_t(bytes));
             if (rc) return rc;
         }
         if (!ctx->dev_err) {
@@ -388,14 +389,19 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
             PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
         }
         if (P->packed_dirty) {
-            ctx->launches += launch_pack_tc(P->w, NetShape(2), P->packed, st);
+            ctx->launches += m->d.dim == 2 ? launch_pack_tc(P->w, NetShape(2), P->packed, st)
+                                           : launch_pack_tc3(P->w, NetShape(3), P->packed, st);
             P->packed_dirty = false;
         }
-        ctx->launches += launch_cnn2d_tc(pred_view(m->d), grid, dt, P->packed, dhat, ctx->dev_err,
-                                         ctx->sm_count, ctx->tc_tile_rows, st);
+        if (m->d.dim == 2)
+            ctx->launches += launch_cnn2d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
+                                             ctx->dev_err, ctx->sm_count, ctx->tc_tile_rows, st);
+        else
+            ctx->launches += launch_cnn3d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
+                                             ctx->dev_err, ctx->sm_count, ctx->tc3_tile, st);
         return CS_OK;
     }
-    if (m->d.dim == 3 && ctx->engine == 1) return predict_tiles(ctx, *P, m, grid, dt, dhat, st);
+    if (m->d.dim == 3 && ctx->engine == 2) return predict_tiles(ctx, *P, m, grid, dt, dhat, st);
     const int64_t chunk = 8192;
     cs_status rc = ensure_workspace(ctx, *P, chunk);
     if (rc) return rc;
@@ -414,7 +420,7 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
 }
 
 cs_status reserve_tiles(cs_ctx *ctx, cs::Mesh *m) {
-    if (m->d.dim != 3 || ctx->engine != 1) return CS_OK;
+    if (m->d.dim != 3 || ctx->engine != 2) return CS_OK;
     Predictor *P = get_pred(ctx, 3);
     if (!P || !P->loaded) return CS_OK;
     return grow_tiles(ctx, *P, plan_tiles(pred_view(m->d)));
@@ -422,18 +428,19 @@ cs_status reserve_tiles(cs_ctx *ctx, cs::Mesh *m) {
 
 bool serving_predictor_ready(cs_ctx *ctx, const cs::Mesh *m) {
     const Predictor &P = ctx->pred[m->d.dim - 2];
-    if (!P.loaded || ctx->engine != 1 || !m->interp_node) return false;
-    if (m->d.dim == 2) return P.packed && !P.packed_dirty && ctx->dev_err;
-    return !P.tiles.empty();
+    if (!P.loaded || !m->interp_node) return false;
+    if (ctx->engine == 1) return P.packed && !P.packed_dirty && ctx->dev_err;
+    return ctx->engine == 2 && m->d.dim == 3 && !P.tiles.empty();
 }
 
 cs_status prepare_serving(cs_ctx *ctx) {
     for (int dim = 2; dim <= 3; ++dim) {
         Predictor &P = ctx->pred[dim - 2];
-        if (!P.loaded || ctx->engine != 1) continue;
-        if (dim == 2) {
+        if (!P.loaded || (ctx->engine != 1 && ctx->engine != 2)) continue;
+        if (ctx->engine == 1) {
+            const int64_t bytes = dim == 2 ? tc_packed_bytes() : tc3_packed_bytes();
             if (!P.packed) {
-                cs_status rc = dalloc(ctx, &P.packed, size_t(tc_packed_bytes()));
+                cs_status rc = dalloc(ctx, &P.packed, size_t(bytes));
                 if (rc) return rc;
             }
             if (!ctx->dev_err) {
@@ -442,7 +449,8 @@ cs_status prepare_serving(cs_ctx *ctx) {
                 PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
             }
             if (P.packed_dirty) {
-                ctx->launches += launch_pack_tc(P.w, NetShape(2), P.packed, nullptr);
+                ctx->launches += dim == 2 ? launch_pack_tc(P.w, NetShape(2), P.packed, nullptr)
+                                          : launch_pack_tc3(P.w, NetShape(3), P.packed, nullptr);
                 P.packed_dirty = false;
             }
         }
@@ -511,8 +519,17 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const float *grid, const double 
 extern "C" {
 
 cs_status cs_predictor_engine(cs_ctx *ctx, int engine) {
-    if (!ctx || (engine != 0 && engine != 1)) return CS_EINVAL;
+    if (!ctx || engine < 0 || engine > 2) return CS_EINVAL;
+    if (ctx->server) return fail(ctx, CS_EBUSY, "cs_predictor_engine: stop serving first");
     ctx->engine = engine;
+    return CS_OK;
+}
+
+cs_status cs_predictor_tile3(cs_ctx *ctx, int side) {
+    if (!ctx) return CS_EINVAL;
+    if (side != 0 && side != 2 && side != 3 && side != 4)
+        return fail(ctx, CS_EINVAL, "cs_predictor_tile3: side must be 0, 2, 3 or 4");
+    ctx->tc3_tile = side;
     return CS_OK;
 }
 

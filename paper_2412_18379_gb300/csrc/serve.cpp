@@ -101,8 +101,8 @@ struct Server {
     std::map<int64_t, Request *> all;
     int64_t next_ticket = 1;
     bool stop = false;
-    // the 3-D predictor's workspace is shared: each 3-D prediction waits for
-    // the one enqueued before it (worker thread only)
+    // the 3-D CUDA-core tile engine's workspace is shared: each of its
+    // predictions waits for the one enqueued before it (worker thread only)
     cudaEvent_t pred3_ev = nullptr;
     bool pred3_any = false;
     // statistics
@@ -170,12 +170,12 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
                                              ctx->sm_count, st);
             grid = own_grid;
         }
-        if (d == 3) {
-            if (S.pred3_any) cudaStreamWaitEvent(st, S.pred3_ev, 0);
-        }
+        // the CUDA-core tile engine (3-D, engine 2) shares one workspace
+        const bool shared_ws = d == 3 && ctx->engine == 2;
+        if (shared_ws && S.pred3_any) cudaStreamWaitEvent(st, S.pred3_ev, 0);
         const cs_status rc = predict_grid(ctx, &m, grid, r.dt, dhat, st);
         if (rc) return rc;
-        if (d == 3) {
+        if (shared_ws) {
             cudaEventRecord(S.pred3_ev, st);
             S.pred3_any = true;
         }

@@ -551,11 +551,13 @@ def test_tile_engine_3d_matches_windows(ctx, n_side, stride):
     n_cells = int(np.prod(om.pgrid))
     tile = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
     win = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
-    ctx.predictor_engine("tc")
-    ctx.predict(mesh, c.dt, out=tile)
-    ctx.predictor_engine("window")
-    ctx.predict(mesh, c.dt, out=win)
-    ctx.predictor_engine("tc")
+    try:
+        ctx.predictor_engine("tiles")
+        ctx.predict(mesh, c.dt, out=tile)
+        ctx.predictor_engine("window")
+        ctx.predict(mesh, c.dt, out=win)
+    finally:
+        ctx.predictor_engine("tc")
     torch.cuda.synchronize()
     tile, win = tile.cpu().numpy(), win.cpu().numpy()
     assert np.isfinite(tile).all()
@@ -634,15 +636,16 @@ def test_full_size_cnn_sns_parity(ctx):
 
 # ---- direct oracle parity of every grid engine ------------------------------
 
+@pytest.mark.parametrize("engine", ["tc", "tiles"])
 @pytest.mark.parametrize("n_side,stride", [(13, 1), (31, 3)])
-def test_tile_engine_3d_matches_oracle_on_every_cell(ctx, n_side, stride):
-    """The 3-D fully convolutional tile engine against the FP64 forward pass
-    (oracle.cnn.forward on oracle windows of the oracle's grid velocity) on
-    every predictor cell. Tolerance: the engine rounds the input window and
-    every layer's operands to BF16 (relative 2^-9 each): five layers x two
-    operands plus the input, 11 x 2^-9 ~ 2.1e-2 of the output scale; the
-    bound allows the worst cell 5e-2, the 2-D bound's margin (4e-2 for 7
-    roundings there) scaled alike."""
+def test_tile_engine_3d_matches_oracle_on_every_cell(ctx, n_side, stride, engine):
+    """The 3-D fully convolutional engines (the tcgen05 kernel, and the tile
+    engine on CUDA cores) against the FP64 forward pass (oracle.cnn.forward on
+    oracle windows of the oracle's grid velocity) on every predictor cell.
+    Tolerance: both round the input window and every layer's operands to BF16
+    (relative 2^-9 each): five layers x two operands plus the input,
+    11 x 2^-9 ~ 2.1e-2 of the output scale; the bound allows the worst cell
+    5e-2, the 2-D bound's margin (4e-2 for 7 roundings there) scaled alike."""
     import torch
     c = make_case("abc3d", n_side=n_side, cfl=6)
     flat = init_weights(3, 41)
@@ -653,8 +656,12 @@ def test_tile_engine_3d_matches_oracle_on_every_cell(ctx, n_side, stride):
     ctx.grid_velocity(mesh, _dev(c.u))
     n_cells = int(np.prod(om.pgrid))
     tile = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
-    ctx.predictor_engine("tc")
-    ctx.predict(mesh, c.dt, out=tile)
+    try:
+        ctx.predictor_engine(engine)
+        ctx.predict(mesh, c.dt, out=tile)
+        ctx.device_status()
+    finally:
+        ctx.predictor_engine("tc")
     torch.cuda.synchronize()
     tile = tile.cpu().numpy()
     U = _oracle_pred_u(om, c.u)
@@ -740,3 +747,42 @@ def test_adam_steps_against_the_oracle(ctx, dim):
         # continue from the device's weights so that the comparison stays per step
         w_ref = w_dev.copy()
     assert opt.t == 5
+
+
+@pytest.mark.parametrize("n_side,stride", [(29, 1), (61, 3)])
+def test_tensor_core_3d_tile_sides_agree(ctx, n_side, stride):
+    """The 3-D tcgen05 grid kernel with output tiles of side 4, 3 and 2 and
+    the automatic choice: every cell gets the same bits (a cell's MMAs and
+    their order do not depend on where the tiles cut the grid), all finite,
+    and against the CUDA-core tile engine within the BF16 bound (1e-2 of the
+    output scale: the same roundings, FP32 sums in another order)."""
+    import torch
+    c = make_case("abc3d", n_side=n_side, cfl=8)
+    flat = init_weights(3, 43)
+    ctx.load_predictor(3, flat)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(stride)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    n_cells = int(np.prod(mesh.info()["pred_grid"]))
+    outs = {}
+    try:
+        for side in (0, 4, 3, 2):
+            o = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
+            ctx.predictor_tile3(side)
+            ctx.predict(mesh, c.dt, out=o)
+            outs[side] = o.cpu().numpy()
+        tiles = torch.full((n_cells, 3), float("nan"), dtype=torch.float32, device="cuda")
+        ctx.predictor_engine("tiles")
+        ctx.predict(mesh, c.dt, out=tiles)
+    finally:
+        ctx.predictor_engine("tc")
+        ctx.predictor_tile3(0)
+    ctx.device_status()
+    tiles = tiles.cpu().numpy()
+    for side in (0, 3, 2):
+        assert np.isfinite(outs[side]).all(), side
+        assert np.array_equal(outs[side].view(np.uint32), outs[4].view(np.uint32)), side
+    assert np.abs(outs[4] - tiles).max() <= 1e-2 * np.abs(tiles).max()
+    with pytest.raises(Exception):
+        ctx.predictor_tile3(5)
+    mesh.release()
