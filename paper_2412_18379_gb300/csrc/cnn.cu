@@ -1,7 +1,9 @@
 // Learned start predictor (Sec. 2.3, Algorithm 2): the velocity field on the
-// ASG grid, input windows, and the CUDA-core kernels of training (forward,
-// backward and Adam on batches of windows, BF16 operands with FP32
-// accumulation, FP32 master weights).
+// ASG grid, input windows, and the kernels of training around its GEMMs
+// (im2col / col2im, ReLU and its gradient, bias gradients, the loss, Adam on
+// the FP32 master weights). The GEMMs run on the tensor cores with BF16
+// operands and FP32 accumulation (tc_gemm.cu); the CUDA-core GEMMs here take
+// the shapes too small for them and the FP32-operand accuracy mode.
 //
 // Network (regressor form): a window of the grid velocity around the cell of
 // the particle, channels u_k * dt / s_k, zero outside the grid, goes through
@@ -288,8 +290,8 @@ __global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restric
 // C[M][N] = op(A) op(B) (+ bias[N]) with operands rounded to BF16 and FP32
 // accumulation. A is [M][K] (transA: [K][M]); B is [K][N] (transB: [N][K]).
 // 64x64 output tile, 16-deep K slabs in shared memory, 4x4 per thread.
-// Split-K: block z sums K-range [z*kc, (z+1)*kc) and adds into C atomically
-// (C zeroed by the launcher; the bias is added by z = 0).
+// Split-K: block z sums K-range [z*kc, (z+1)*kc) into partial product z
+// (C + z M N, no bias); launch_reduce_splits sums them in order.
 __global__ void __launch_bounds__(kThreads) gemm_kernel(const float *__restrict__ A,
                                                         const float *__restrict__ Bm, float *C,
                                                         const float *__restrict__ bias, int64_t M,
@@ -341,9 +343,9 @@ __global__ void __launch_bounds__(kThreads) gemm_kernel(const float *__restrict_
         for (int s = 0; s < 4; ++s) {
             const int64_t gn = n0 + tx * 4 + s;
             if (gn >= N) continue;
-            float v = acc[r][s] + (bias && blockIdx.z == 0 ? bias[gn] : 0.f);
+            float v = acc[r][s] + (bias ? bias[gn] : 0.f);
             if (split) {
-                atomicAdd(&C[gm * N + gn], v);
+                C[(int64_t(blockIdx.z) * M + gm) * N + gn] = v;   // partial product z
             } else {
                 if (accumulate) v += C[gm * N + gn];
                 C[gm * N + gn] = v;
@@ -382,8 +384,9 @@ __global__ void colsum_kernel(const float *__restrict__ x, int64_t M, int64_t N,
     }
 }
 
-// dL/dout of L = mean over batch and components of (out - target)^2, and the
-// per-block partial sums of the squared error.
+// dL/dout of L = mean over batch and components of (out - target)^2, and L
+// added to *loss. One block: its fixed-order reduction gives the same loss
+// bits on every run (the outputs are a batch of a few thousand values).
 __global__ void mse_grad_kernel(const float *__restrict__ out, const float *__restrict__ tgt,
                                 int64_t n, float *__restrict__ g, float *__restrict__ loss) {
     __shared__ float red[kThreads];
@@ -400,7 +403,7 @@ __global__ void mse_grad_kernel(const float *__restrict__ out, const float *__re
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(loss, red[0] / float(n));
+    if (threadIdx.x == 0) *loss += red[0] / float(n);
 }
 
 // Adam on the FP32 master weights (Sec. 2.3 names Adam; constants are the
@@ -818,26 +821,34 @@ void set_gemm_bf16(bool on) { g_gemm_bf16 = on; }
 
 int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
                 int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
-                cudaStream_t st) {
+                cudaStream_t st, int *err, int sm_count, float *work, int64_t work_floats) {
+    if (g_gemm_bf16 && err && !accumulate && tc_gemm_fits(M, N, K))
+        return launch_tc_gemm(A, Bm, C, bias, M, N, K, transA, transB, err, sm_count, work,
+                               work_floats, st);
     if (!transA && transB && !accumulate && N <= 32) {
         gemm_nt32_kernel<<<unsigned((M + 31) / 32), 64, 0, st>>>(A, Bm, C, bias, M, int(N), K,
                                                                  g_gemm_bf16);
         return 1;
     }
-    // split K when the output has few tiles and K is long (weight gradients)
+    // split K when the output has few tiles and K is long (weight gradients):
+    // the splits write partial products to the workspace, summed in order
     const int64_t tiles = ((N + 63) / 64) * ((M + 63) / 64);
     int64_t splits = 1;
-    if (tiles < 512 && K > 2048) splits = std::min<int64_t>((K + 1023) / 1024, (1024 + tiles - 1) / tiles);
+    if (tiles < 512 && K > 2048 && work && !accumulate)
+        splits = std::min<int64_t>((K + 1023) / 1024, (1024 + tiles - 1) / tiles);
+    splits = std::max<int64_t>(1, std::min<int64_t>(splits, work_floats / std::max<int64_t>(1, M * N)));
     const int64_t kc = ((K + splits - 1) / splits + 15) / 16 * 16;
     splits = (K + kc - 1) / kc;
-    int n = 1;
-    if (splits > 1 && !accumulate) {
-        cudaMemsetAsync(C, 0, size_t(M) * size_t(N) * sizeof(float), st);
-    }
     const dim3 grid(unsigned((N + 63) / 64), unsigned((M + 63) / 64), unsigned(splits));
-    gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, C, bias, M, N, K, transA, transB, accumulate,
+    if (splits == 1) {
+        gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, C, bias, M, N, K, transA, transB, accumulate,
+                                               g_gemm_bf16, kc);
+        return 1;
+    }
+    gemm_kernel<<<grid, kThreads, 0, st>>>(A, Bm, work, nullptr, M, N, K, transA, transB, false,
                                            g_gemm_bf16, kc);
-    return n;
+    launch_reduce_splits(work, splits, M, N, bias, C, sm_count, st);
+    return 2;
 }
 
 int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, int Si,
@@ -882,7 +893,8 @@ int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t
 
 int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,
                     int sm_count, cudaStream_t st) {
-    mse_grad_kernel<<<grid_for(n, sm_count, 1), kThreads, 0, st>>>(out, tgt, n, g, loss);
+    (void)sm_count;
+    mse_grad_kernel<<<1, kThreads, 0, st>>>(out, tgt, n, g, loss);
     return 1;
 }
 

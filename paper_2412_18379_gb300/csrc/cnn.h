@@ -41,9 +41,24 @@ int launch_im2col(int dim, const float *x, int64_t B, int C, int Si, bool chfirs
                   int sm_count, cudaStream_t st);
 int launch_col2im(int dim, const float *dcol, int64_t B, int C, int Si, float *dx, int sm_count,
                   cudaStream_t st);
+// C[M][N] = op(A) op(B) (+ bias[N]), A [M][K] (transA: [K][M]), B [K][N]
+// (transB: [N][K]). With BF16 operands the tensor-core GEMM takes every shape
+// it fits (tc_gemm_fits); the rest, and FP32 operands, run on CUDA cores.
+// err: device flag a bounded wait of the tensor-core GEMM raises. A long K
+// is split over CTAs only with a workspace (work, work_floats): the partial
+// products are summed in a fixed order, so every run gives the same bits.
 int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
                 int64_t N, int64_t K, bool transA, bool transB, bool accumulate,
-                cudaStream_t st);
+                cudaStream_t st, int *err, int sm_count, float *work, int64_t work_floats);
+// the tensor-core GEMM (tc_gemm.cu)
+bool tc_gemm_fits(int64_t M, int64_t N, int64_t K);
+int64_t tc_gemm_work_floats(int sm_count);   // workspace that allows every split
+// C[M][N] = sum over z, in order, of part[z][M][N] (+ bias[N])
+void launch_reduce_splits(const float *part, int64_t splits, int64_t M, int64_t N,
+                          const float *bias, float *C, int sm_count, cudaStream_t st);
+int launch_tc_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
+                   int64_t N, int64_t K, bool transA, bool transB, int *err, int sm_count,
+                   float *work, int64_t work_floats, cudaStream_t st);
 void set_gemm_bf16(bool on);
 int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st);
 // ReLU(conv(x) + bias) of one valid 3^D convolution of 32 output channels,

@@ -144,6 +144,8 @@ struct Predictor {
     float *dcol = nullptr, *dy0 = nullptr, *dy1 = nullptr, *da5 = nullptr, *win = nullptr,
           *tgt = nullptr;
     int64_t *idx = nullptr;
+    float *splitk = nullptr;     // partial products of the GEMMs' K splits
+    int64_t splitk_n = 0;
     std::vector<float *> tiles;  // workspace of the tile engine (fully convolutional)
     std::vector<int64_t> tiles_cap;   // floats held by each buffer of `tiles`
     uint8_t *packed = nullptr;   // weights in the tensor-core kernel's layout

@@ -77,6 +77,9 @@ void free_workspace(cs_ctx *ctx, Predictor &P) {
     }
     dfree(ctx, P.idx);
     P.idx = nullptr;
+    dfree(ctx, P.splitk);
+    P.splitk = nullptr;
+    P.splitk_n = 0;
     P.cap = 0;
     for (float *p : P.tiles) dfree(ctx, p);
     P.tiles.clear();
@@ -84,6 +87,13 @@ void free_workspace(cs_ctx *ctx, Predictor &P) {
 }
 
 cs_status ensure_workspace(cs_ctx *ctx, Predictor &P, int64_t B) {
+    // the error flag of the tensor-core GEMMs' bounded waits
+    if (!ctx->dev_err) {
+        cs_status rc = dalloc(ctx, &ctx->dev_err, 1);
+        if (rc) return rc;
+        if (cudaMemset(ctx->dev_err, 0, sizeof(int)) != cudaSuccess)
+            return fail(ctx, CS_ECUDA, "cudaMemset of the device error flag failed");
+    }
     if (P.cap >= B) return CS_OK;
     free_workspace(ctx, P);
     NetShape S(P.dim);
@@ -113,10 +123,20 @@ cs_status ensure_workspace(cs_ctx *ctx, Predictor &P, int64_t B) {
         (rc = dalloc(ctx, &P.dcol, size_t(max_col))) || (rc = dalloc(ctx, &P.dy0, size_t(max_dy))) ||
         (rc = dalloc(ctx, &P.dy1, size_t(max_dy))) || (rc = dalloc(ctx, &P.da5, size_t(B * S.hidden))) ||
         (rc = dalloc(ctx, &P.win, size_t(B * win))) || (rc = dalloc(ctx, &P.tgt, size_t(B * S.dim))) ||
-        (rc = dalloc(ctx, &P.idx, size_t(B))))
+        (rc = dalloc(ctx, &P.idx, size_t(B))) ||
+        (rc = dalloc(ctx, &P.splitk, size_t(tc_gemm_work_floats(ctx->sm_count)))))
         return rc;
+    P.splitk_n = tc_gemm_work_floats(ctx->sm_count);
     P.cap = B;
     return CS_OK;
+}
+
+// C = op(A) op(B) (+ bias) of the predictor's workspace: BF16 operands on the
+// tensor cores where the shape fits, K splits summed in a fixed order
+int gemm(cs_ctx *ctx, Predictor &P, const float *A, const float *Bm, float *C, const float *bias,
+         int64_t M, int64_t N, int64_t K, bool transA, bool transB, cudaStream_t st) {
+    return launch_gemm(A, Bm, C, bias, M, N, K, transA, transB, false, st, ctx->dev_err,
+                       ctx->sm_count, P.splitk, P.splitk_n);
 }
 
 // forward of B windows (device, [B][cin][S0^dim]) into P.out [B][dim]
@@ -131,8 +151,8 @@ int forward(cs_ctx *ctx, Predictor &P, int64_t B, const float *win, cudaStream_t
         const int So = Si - 2;
         const int64_t Po = S.positions(So), K = int64_t(C) * S.taps();
         launches += launch_im2col(P.dim, x, B, C, Si, chfirst, P.col[l], sm, st);
-        launches += launch_gemm(P.col[l], P.w + S.w_off[l], P.z[l], P.w + S.b_off[l], B * Po, S.ch,
-                                K, false, true, false, st);
+        launches += gemm(ctx, P, P.col[l], P.w + S.w_off[l], P.z[l], P.w + S.b_off[l],
+                         B * Po, S.ch, K, false, true, st);
         launches += launch_relu(P.z[l], P.y[l], B * Po * S.ch, sm, st);
         x = P.y[l];
         chfirst = false;
@@ -140,11 +160,11 @@ int forward(cs_ctx *ctx, Predictor &P, int64_t B, const float *win, cudaStream_t
         Si = So;
     }
     const int f1 = S.n_conv, f2 = S.n_conv + 1;
-    launches += launch_gemm(x, P.w + S.w_off[f1], P.z5, P.w + S.b_off[f1], B, S.hidden, S.ch,
-                            false, true, false, st);
+    launches += gemm(ctx, P, x, P.w + S.w_off[f1], P.z5, P.w + S.b_off[f1],
+                     B, S.hidden, S.ch, false, true, st);
     launches += launch_relu(P.z5, P.a5, B * S.hidden, sm, st);
-    launches += launch_gemm(P.a5, P.w + S.w_off[f2], P.out, P.w + S.b_off[f2], B, S.dim,
-                            S.hidden, false, true, false, st);
+    launches += gemm(ctx, P, P.a5, P.w + S.w_off[f2], P.out, P.w + S.b_off[f2],
+                     B, S.dim, S.hidden, false, true, st);
     return launches;
 }
 
@@ -156,19 +176,17 @@ int backward(cs_ctx *ctx, Predictor &P, int64_t B, const float *tgt, float *loss
     int n = 0;
     const int f1 = S.n_conv, f2 = S.n_conv + 1;
     n += launch_mse_grad(P.out, tgt, B * S.dim, P.gout, loss, sm, st);
-    n += launch_gemm(P.gout, P.a5, P.g + S.w_off[f2], nullptr, S.dim, S.hidden, B, true, false,
-                     false, st);
+    n += gemm(ctx, P, P.gout, P.a5, P.g + S.w_off[f2], nullptr,
+              S.dim, S.hidden, B, true, false, st);
     n += launch_colsum(P.gout, B, S.dim, P.g + S.b_off[f2], st);
-    n += launch_gemm(P.gout, P.w + S.w_off[f2], P.da5, nullptr, B, S.hidden, S.dim, false, false,
-                     false, st);
+    n += gemm(ctx, P, P.gout, P.w + S.w_off[f2], P.da5, nullptr,
+              B, S.hidden, S.dim, false, false, st);
     n += launch_relu_back(P.z5, P.da5, B * S.hidden, sm, st);
     const float *h4 = P.y[S.n_conv - 1];
-    n += launch_gemm(P.da5, h4, P.g + S.w_off[f1], nullptr, S.hidden, S.ch, B, true, false, false,
-                     st);
+    n += gemm(ctx, P, P.da5, h4, P.g + S.w_off[f1], nullptr, S.hidden, S.ch, B, true, false, st);
     n += launch_colsum(P.da5, B, S.hidden, P.g + S.b_off[f1], st);
     float *dy = P.dy0, *dnext = P.dy1;
-    n += launch_gemm(P.da5, P.w + S.w_off[f1], dy, nullptr, B, S.ch, S.hidden, false, false, false,
-                     st);
+    n += gemm(ctx, P, P.da5, P.w + S.w_off[f1], dy, nullptr, B, S.ch, S.hidden, false, false, st);
     // conv layers, last to first; edge of layer l's input
     std::vector<int> Sin(S.n_conv);
     int Si = S.S0;
@@ -181,12 +199,12 @@ int backward(cs_ctx *ctx, Predictor &P, int64_t B, const float *tgt, float *loss
         const int C = l == 0 ? S.cin : S.ch;
         const int64_t Po = S.positions(So), K = int64_t(C) * S.taps();
         n += launch_relu_back(P.z[l], dy, B * Po * S.ch, sm, st);
-        n += launch_gemm(dy, P.col[l], P.g + S.w_off[l], nullptr, S.ch, K, B * Po, true, false,
-                         false, st);
+        n += gemm(ctx, P, dy, P.col[l], P.g + S.w_off[l], nullptr,
+                  S.ch, K, B * Po, true, false, st);
         n += launch_colsum(dy, B * Po, S.ch, P.g + S.b_off[l], st);
         if (l > 0) {
-            n += launch_gemm(dy, P.w + S.w_off[l], P.dcol, nullptr, B * Po, K, S.ch, false, false,
-                             false, st);
+            n += gemm(ctx, P, dy, P.w + S.w_off[l], P.dcol, nullptr,
+                      B * Po, K, S.ch, false, false, st);
             n += launch_col2im(P.dim, P.dcol, B, S.ch, Sin[l], dnext, sm, st);
             std::swap(dy, dnext);
         }
@@ -550,7 +568,7 @@ cs_status cs_device_status(cs_ctx *ctx) {
     PCHK(cudaMemcpy(&e, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
         PCHK(cudaMemset(ctx->dev_err, 0, sizeof(int)));
-        return fail(ctx, CS_EDEVICE, "a bounded device wait gave up (tensor-core predictor)");
+        return fail(ctx, CS_EDEVICE, "a bounded device wait gave up (tensor-core kernel)");
     }
     return CS_OK;
 }

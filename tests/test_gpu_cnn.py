@@ -716,37 +716,58 @@ def test_tensor_core_at_the_benchmark_configuration(ctx):
 
 @pytest.mark.parametrize("dim", [2, 3])
 def test_adam_steps_against_the_oracle(ctx, dim):
-    """Five training steps on the device against oracle.cnn.Adam. Each step
-    trains on the whole batch, so its gradient is the one cs_predictor_grad
-    returns at the step's weights (up to the FP32 summation order of the
-    shuffled batch); the oracle's Adam takes those gradients from the same
-    start, keeping its own FP64 moments and bias corrections. The weights
-    after every step agree to 2e-6 (lr = 1e-3 steps, FP32 updates) wherever
-    the gradient is not tiny; elsewhere Adam's normalised step is sensitive to
-    the summation order; there every step of the device stays within Adam's
-    bound lr (1 - beta1) / sqrt(1 - beta2) ~ 3.2 lr."""
+    """Five training steps on the device against oracle.cnn.Adam. With a
+    batch of one pair the step's gradient is, bit for bit, the one
+    cs_predictor_grad returns at the step's weights (no shuffle, no
+    reordered sums); the oracle's Adam takes those gradients from the same
+    start and keeps its own FP64 moments and bias corrections. The device
+    updates its FP32 master weights with FP32 arithmetic: each step is off by
+    a few units in the last place of a 1e-3 update and of weights of order
+    0.1, so the weights agree to 1e-7 after every step, with the moments of
+    all five steps carried on both sides."""
     rng = np.random.default_rng(60 + dim)
     flat = init_weights(dim, 9)
     ctx.load_predictor(dim, flat)
     S = cnn.patch_size(dim)
-    B = 64
-    win = _dev(rng.standard_normal((B, dim) + (S,) * dim).astype(np.float32))
-    tgt = _dev(rng.standard_normal((B, dim)).astype(np.float32))
+    win = _dev(rng.standard_normal((1, dim) + (S,) * dim).astype(np.float32))
+    tgt = _dev(rng.standard_normal((1, dim)).astype(np.float32))
     opt = cnn.Adam(flat.size, lr=1e-3)
-    w_ref = flat.astype(np.float64)
+    w_ref = flat.astype(np.float32).astype(np.float64)
+    moved = np.zeros(flat.size, dtype=bool)
     for step in range(5):
         g, _ = ctx.predictor_grad(dim, win, tgt)
         g = g.cpu().numpy().astype(np.float64)
-        w_prev = w_ref
         w_ref = opt.step(w_ref, g)
-        ctx.train(dim, win, tgt, batch=B, steps=1, lr=1e-3, seed=step)
+        ctx.train(dim, win, tgt, batch=1, steps=1, lr=1e-3, seed=step)
         w_dev = ctx.save_predictor(dim).astype(np.float64)
-        big = np.abs(g) > 1e-5 * np.abs(g).max()
-        assert np.allclose(w_dev[big], w_ref[big], rtol=0, atol=2e-6), step
-        assert np.all(np.abs(w_dev - w_prev) <= 3.2e-3), step
-        # continue from the device's weights so that the comparison stays per step
+        assert np.allclose(w_dev, w_ref, rtol=0, atol=1e-7), (step, np.abs(w_dev - w_ref).max())
+        moved |= w_dev != flat
+        # the device follows the oracle's moments: continue from its own weights
         w_ref = w_dev.copy()
-    assert opt.t == 5
+    assert opt.t == 5 and moved.mean() > 0.5
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_training_is_bit_reproducible(ctx, dim):
+    """The K splits of the training GEMMs are summed in a fixed order, so a
+    gradient, and a whole training run from the same weights and seed, give
+    the same bits every time."""
+    rng = np.random.default_rng(80 + dim)
+    S = cnn.patch_size(dim)
+    B = 1024 if dim == 2 else 256
+    win = _dev(rng.standard_normal((4 * B, dim) + (S,) * dim).astype(np.float32))
+    tgt = _dev(rng.standard_normal((4 * B, dim)).astype(np.float32))
+    flat = init_weights(dim, 19)
+    runs = []
+    for _ in range(2):
+        ctx.load_predictor(dim, flat)
+        g, loss = ctx.predictor_grad(dim, win[:B].contiguous(), tgt[:B].contiguous())
+        losses = ctx.train(dim, win, tgt, batch=B, steps=6, lr=1e-3, seed=5)
+        runs.append((g.cpu().numpy(), loss, losses, ctx.save_predictor(dim)))
+    (g0, l0, ls0, w0), (g1, l1, ls1, w1) = runs
+    assert np.array_equal(g0.view(np.uint32), g1.view(np.uint32)) and l0 == l1
+    assert np.array_equal(ls0.view(np.uint32), ls1.view(np.uint32))
+    assert np.array_equal(w0.view(np.uint32), w1.view(np.uint32))
 
 
 @pytest.mark.parametrize("n_side,stride", [(29, 1), (61, 3)])
@@ -786,3 +807,35 @@ def test_tensor_core_3d_tile_sides_agree(ctx, n_side, stride):
     with pytest.raises(Exception):
         ctx.predictor_tile3(5)
     mesh.release()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tensor_core_gradients_at_training_batch(ctx, dim):
+    """The training GEMMs on the tensor cores at a batch that splits the weight
+    gradients' long K (the batch positions) over CTAs: every layer's gradient
+    against the FP64 backward within the BF16 bound of the per-layer test
+    (1.5e-1 relative for the deepest layer, 5e-2 for the others), and the loss
+    within 4e-2."""
+    rng = np.random.default_rng(70 + dim)
+    flat = init_weights(dim, 17).astype(np.float64)
+    flat += 0.02 * rng.standard_normal(flat.size)
+    flat = flat.astype(np.float32)
+    ctx.load_predictor(dim, flat)
+    S = cnn.patch_size(dim)
+    B = 2048 if dim == 2 else 512
+    win = rng.standard_normal((B, dim) + (S,) * dim).astype(np.float32)
+    tgt = rng.standard_normal((B, dim)).astype(np.float32)
+    params = cnn.unpack(dim, flat)
+    ref, acts = cnn.forward(dim, params, win.astype(np.float64), keep=True)
+    gref = cnn.pack(cnn.backward(dim, params, acts, ref, tgt.astype(np.float64)))
+    g, loss = ctx.predictor_grad(dim, _dev(win), _dev(tgt))
+    ctx.device_status()
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - cnn.mse(ref, tgt)) <= 4e-2 * cnn.mse(ref, tgt)
+    o = 0
+    for li, (_, ws, bs) in enumerate(cnn.spec(dim)):
+        n = int(np.prod(ws)) + int(np.prod(bs))
+        a, b = g[o:o + n], gref[o:o + n]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert rel <= (1.5e-1 if li == 0 else 5e-2), (li, rel)
+        o += n
