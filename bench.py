@@ -277,64 +277,93 @@ def train_predictor(ctx, mesh, case, n_fields, steps, batch, seed):
                 "hosts_identical": agree}}
 
 
-def serve_bench(ctx, base_mesh, base_case, n_requests, rate, slots, seed, pred_stride):
-    """Poisson stream of tracking requests over resident meshes (a scaled
-    version of the serving workload: 2 triangle meshes of 2.0M and 0.2M
-    elements, 2 tetrahedral meshes of 0.75M and 2.06M, 8-mode fields, CFL
-    1-16, request sizes log-uniform in [1e4, min(2e6, n_v)]). CNN-SNS on the
-    2-D meshes, plain SNS (the fallback) on the 3-D ones. Each request is a
-    contiguous range of a mesh's nodes; inputs sit in pinned host memory and
-    every request copies its inputs in and its results out."""
+def serve_bench(ctx, n_requests, rate, slots, seed, pred_stride, repeats):
+    """The serving workload: a Poisson stream of tracking requests over 32
+    device-resident meshes (16 triangle meshes of 0.1M-4M elements, jittered
+    lattices split along the diagonals, and 16 Kuhn tetrahedral meshes of
+    0.5M-6M elements, sizes log-uniform), each with its own resident 8-mode
+    velocity field; requests of 1e4-2e6 particles (log-uniform, at most the
+    mesh's nodes: a contiguous range of its nodes with their elements as the
+    plain starts), CFL U(1, 16), CNN-SNS on the request's mesh and field (the
+    2-D and 3-D tensor-core predictors), inputs in pinned host memory, every
+    request copying its inputs in and its results out. p50/p99 are the
+    medians over `repeats` streams of n_requests each."""
     import torch
-    from workloads import make_case
-    from workloads.fields import fourier_modes_2d, fourier_modes_3d, dt_for_cfl
+    from workloads.meshes import lattice_tris_2d, kuhn_3d, serving_mesh_sizes
+    from workloads.fields import fourier_modes_2d, fourier_modes_3d
+    t0 = time.perf_counter()
     rng = np.random.default_rng(seed)
     entries = []
-    specs = [(None, base_case), ("modes2d", dict(n_side=317)), ("abc3d", dict(n_side=51)),
-             ("abc3d", dict(n_side=71))]
-    for i, (name, kw) in enumerate(specs):
-        if name is None:
-            c, m = base_case, base_mesh
-            u = fourier_modes_2d(c.xyz, 77)
+    n_elems = {2: 0, 3: 0}
+    for i, (dim, n_side) in enumerate(serving_mesh_sizes(5)):
+        if dim == 2:
+            xyz, conn, h = lattice_tris_2d(n_side, 0.25, 500 + i)
+            u = fourier_modes_2d(xyz, 700 + i)
         else:
-            c = make_case(name, **kw)
-            m = ctx.upload_mesh(c.xyz, c.conn)
-            if c.dim == 2:
-                m.set_predictor_grid(pred_stride)
-            u = (fourier_modes_2d if c.dim == 2 else fourier_modes_3d)(c.xyz, 77 + i)
-        field = ctx.upload_field(m, u) if c.dim == 2 else None
-        entries.append(dict(case=c, mesh=m, field=field, x=torch.from_numpy(c.x).pin_memory(),
+            xyz, conn, h = kuhn_3d(n_side, 0.1, 500 + i)
+            u = fourier_modes_3d(xyz, 700 + i)
+        m = ctx.upload_mesh(xyz, conn)
+        m.set_predictor_grid(pred_stride)
+        f = ctx.upload_field(m, u)
+        n_elems[dim] += conn.shape[0]
+        entries.append(dict(mesh=m, field=f, h=h, n=xyz.shape[0],
+                            x=torch.from_numpy(np.ascontiguousarray(xyz)).pin_memory(),
                             u=torch.from_numpy(np.ascontiguousarray(u)).pin_memory(),
                             start=torch.from_numpy(m.node_start_elements()).pin_memory(),
                             umax=float(np.sqrt((u * u).sum(axis=1)).max())))
     torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    used, _ = ctx.memory_usage()
+    # warm-up: one small request per mesh, so that no timed request pays a
+    # kernel's first launch
     ctx.serve_start(slots=slots, arena_bytes=4 << 30)
-    tickets = []
-    t0 = time.perf_counter()
-    t_next = t0
     try:
-        for _ in range(n_requests):
-            e = entries[rng.integers(len(entries))]
-            nv = e["case"].n_particles
-            n = int(np.exp(rng.uniform(np.log(1e4), np.log(min(2e6, nv)))))
-            off = int(rng.integers(0, nv - n + 1))
-            dt = rng.uniform(1.0, 16.0) * e["case"].h / e["umax"]
-            t_next += rng.exponential(1.0 / rate)
-            while time.perf_counter() < t_next:
-                pass
-            sl = slice(off, off + n)
-            t, _ = ctx.submit(e["mesh"], e["x"][sl], e["u"][sl], dt, start=e["start"][sl],
-                              mode="cnn", field=e["field"])
-            tickets.append(t)
-        for t in tickets:
+        warm = [ctx.submit(e["mesh"], e["x"][:10000], e["u"][:10000], 0.5 * e["h"] / e["umax"],
+                           start=e["start"][:10000], mode="cnn", field=e["field"])[0]
+                for e in entries]
+        for t in warm:
             ctx.wait(t, timeout_ms=120000)
-        rep = ctx.serve_report()
     finally:
         ctx.serve_stop()
-    rep.update(requests=n_requests, arrival_rate_per_s=rate, slots=slots,
-               meshes="2-D 2.0M + 0.2M triangles (CNN-SNS), 3-D 0.75M + 2.06M tets (SNS)",
-               includes="H2D of inputs, start rule, walk, D2H of outputs")
-    return rep
+    reps = []
+    for rep in range(repeats):
+        ctx.serve_start(slots=slots, arena_bytes=4 << 30)
+        tickets = []
+        t_next = time.perf_counter()
+        try:
+            for _ in range(n_requests):
+                e = entries[rng.integers(len(entries))]
+                n = int(np.exp(rng.uniform(np.log(1e4), np.log(min(2e6, e["n"])))))
+                off = int(rng.integers(0, e["n"] - n + 1))
+                dt = rng.uniform(1.0, 16.0) * e["h"] / e["umax"]
+                t_next += rng.exponential(1.0 / rate)
+                while time.perf_counter() < t_next:
+                    pass
+                sl = slice(off, off + n)
+                t, _ = ctx.submit(e["mesh"], e["x"][sl], e["u"][sl], dt, start=e["start"][sl],
+                                  mode="cnn", field=e["field"])
+                tickets.append(t)
+            modes = [ctx.wait(t, timeout_ms=120000) for t in tickets]
+            r = ctx.serve_report()
+        finally:
+            ctx.serve_stop()
+        r["cnn_sns_share"] = float(np.mean(np.array(modes) == 1))
+        reps.append(r)
+    med = lambda k: float(np.median([r[k] for r in reps]))
+    out = {"p50_ms": med("p50_ms"), "p99_ms": med("p99_ms"), "mean_ms": med("mean_ms"),
+           "max_ms": med("max_ms"), "particles_per_s": med("particles_per_s"),
+           "repeats": [{k: r[k] for k in ("p50_ms", "p99_ms", "max_ms", "particles_per_s",
+                                          "completed", "rejected", "max_concurrent", "peak_bytes",
+                                          "cnn_sns_share")} for r in reps],
+           "requests_per_repeat": n_requests, "arrival_rate_per_s": rate, "slots": slots,
+           "meshes": "16 triangle meshes (%.1fM triangles) + 16 tetrahedral meshes (%.1fM tets), "
+                     "each with its own resident 8-mode field" % (n_elems[2] / 1e6, n_elems[3] / 1e6),
+           "device_bytes_resident": used, "setup_s": setup_s,
+           "includes": "H2D of inputs, CNN-SNS start rule on the request's field, walk, D2H of "
+                       "outputs"}
+    for e in entries:
+        e["mesh"].release()
+    return out
 
 
 class Runner:
@@ -537,6 +566,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rate", type=float, default=1000.0)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-repeats", type=int, default=3)
     ap.add_argument("--quick", action="store_true",
                     help="time the main mode only (no other modes, e2e or CPU leg); "
                          "used for profiler captures")
@@ -652,16 +682,23 @@ def main():
     e2e = {"value": world * n / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": n * dim * 16 + (0 if sh is None else n * 4),
            "d2h_bytes_per_step": n * 9,
-           "entry_point": "cs_track_host"}
-
-    serving = None
-    if not args.quick and dim == 2 and args.serve_requests > 0:
-        serving = serve_bench(ctx, mesh, case, args.serve_requests, args.serve_rate,
-                              args.serve_slots, seed=100 + rank, pred_stride=args.pred_stride)
+           "entry_point": "cs_track_host",
+           "transfer": "page-locked host buffers; the call copies the inputs to a device "
+                       "staging buffer and the results back (cudaMemcpyAsync), then synchronises"}
 
     sweep_rows = None
     if not args.no_sweep and args.particles == "nodes" and args.workload == "tg2d":
         sweep_rows = sweep(ctx, cs, args, rank, dev, dist, max_over_ranks, flush, case, mesh)
+
+    serving = None
+    if not args.quick and args.serve_requests > 0:
+        if sweep_rows is None:
+            from workloads.weights import init_weights
+            ctx.load_predictor(3, init_weights(3, rank))      # untrained: exact, longer walks
+        torch.cuda.empty_cache()
+        serving = serve_bench(ctx, args.serve_requests, args.serve_rate, args.serve_slots,
+                              seed=100 + rank, pred_stride=args.pred_stride,
+                              repeats=args.serve_repeats)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

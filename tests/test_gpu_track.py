@@ -271,3 +271,41 @@ def test_non_convex_3d_domain_uses_the_exact_search(ctx):
     _compare(got, _oracle_out(om, om.track(c.x, c.u, c.dt)), "sphere3d")
     assert (got["status"] == 2).sum() > 100
     mesh.release()
+
+
+@pytest.mark.parametrize("mode", ["sns", "asg", "cnn"])
+def test_host_entry_point_matches_the_device_one(ctx, mode):
+    """cs_track_host (copies through a device staging buffer) on page-locked
+    and on pageable host arrays: results equal the device entry point's bit
+    for bit, for the mesh nodes and for explicit starts with a resident
+    field."""
+    import torch
+    from workloads.weights import init_weights
+    from workloads import element_node_particles
+    c = make_case("tg2d", n_side=401, cfl=8)
+    ctx.load_predictor(2, init_weights(2, 12))
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    want = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode=mode, start_out=True)
+    torch.cuda.synchronize()
+    want = {k: v.cpu().numpy() for k, v in want.items()}
+    n = c.n_particles
+    pinned = dict(host=torch.full((n,), -7, dtype=torch.int32).pin_memory(),
+                  path_len=torch.full((n,), -7, dtype=torch.int32).pin_memory(),
+                  status=torch.full((n,), 9, dtype=torch.uint8).pin_memory(),
+                  start=torch.full((n,), -7, dtype=torch.int32).pin_memory())
+    for xs, us, out in ((torch.from_numpy(c.x).pin_memory(), torch.from_numpy(c.u).pin_memory(),
+                         pinned), (c.x, c.u, None)):
+        got = ctx.track_host(mesh, xs, us, c.dt, mode=mode, start_out=True, out=out)
+        for k in ("host", "path_len", "status", "start"):
+            g = got[k].numpy() if hasattr(got[k], "numpy") else got[k]
+            assert np.array_equal(g, want[k]), (mode, out is None, k)
+    # explicit starts (element-node particles) with a resident field
+    x, u, start = element_node_particles(c)
+    f = ctx.upload_field(mesh, c.u)
+    want = ctx.track(mesh, _dev(x), _dev(u), c.dt, start=_dev(start), mode=mode, field=f)
+    torch.cuda.synchronize()
+    got = ctx.track_host(mesh, x, u, c.dt, start=start, mode=mode, field=f)
+    for k in ("host", "path_len", "status"):
+        assert np.array_equal(got[k], want[k].cpu().numpy()), (mode, "pairs", k)
+    mesh.release()

@@ -171,6 +171,60 @@ def mesh_3d(n_side, jitter=0.1, seed=3):
     return _mesh_3d_cached(int(n_side), float(jitter), int(seed))
 
 
+def lattice_tris_2d(n_side, jitter, seed, max_redraw=64):
+    """(xyz, conn, h): the unit square's n x n lattice, interior points jittered
+    uniformly by up to jitter * h, each lattice square split along its
+    rising diagonal into two triangles (a structured triangulation, fast at
+    any size). Interior points of a triangle that would flip are redrawn."""
+    xyz, h = lattice_2d(n_side, 0.0, seed)
+    n = n_side
+    i = np.arange(n - 1)
+    ix = np.tile(i, n - 1)
+    iy = np.repeat(i, n - 1)
+    v00 = iy * n + ix
+    v10, v01, v11 = v00 + 1, v00 + n, v00 + n + 1
+    conn = np.concatenate([np.stack([v00, v10, v11], axis=1),
+                           np.stack([v00, v11, v01], axis=1)]).astype(np.int32)
+    base = xyz.copy()
+    gx = np.tile(np.arange(n), n)
+    gy = np.repeat(np.arange(n), n)
+    interior = (gx > 0) & (gx < n - 1) & (gy > 0) & (gy < n - 1)
+    rng = np.random.default_rng(seed)
+    dj = rng.uniform(-jitter * h, jitter * h, size=base.shape)
+    dj[~interior] = 0.0
+    xyz = base + dj
+
+    def area2(p):
+        q = p[conn]
+        return ((q[:, 1, 0] - q[:, 0, 0]) * (q[:, 2, 1] - q[:, 0, 1]) -
+                (q[:, 1, 1] - q[:, 0, 1]) * (q[:, 2, 0] - q[:, 0, 0]))
+    for _ in range(max_redraw):
+        bad = area2(xyz) <= 0
+        if not bad.any():
+            break
+        verts = np.unique(conn[bad].ravel())
+        verts = verts[interior[verts]]
+        xyz[verts] = base[verts] + rng.uniform(-jitter * h, jitter * h, size=(verts.size, 2))
+    else:
+        raise RuntimeError("could not draw a valid jittered lattice triangulation")
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(conn), h
+
+
+def serving_mesh_sizes(seed=5):
+    """The serving workload's 32 meshes: 16 triangle meshes with 0.1M-4M
+    elements and 16 tetrahedral meshes with 0.5M-6M elements, sizes drawn
+    log-uniformly (seeded). Returns [(dim, n_side)] with n_side the lattice
+    points per axis that give about that many elements (2 (n-1)^2 triangles,
+    6 (n-1)^3 tetrahedra)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for dim, lo, hi in ((2, 1e5, 4e6), (3, 5e5, 6e6)):
+        for ne in np.exp(rng.uniform(np.log(lo), np.log(hi), size=16)):
+            per = 2.0 if dim == 2 else 6.0
+            out.append((dim, int(round((ne / per) ** (1.0 / dim))) + 1))
+    return out
+
+
 @functools.lru_cache(maxsize=4)
 def _mesh_3d_sphere_cached(n_side, radius, jitter, seed):
     xyz, conn, h = kuhn_3d(n_side, jitter, seed)
