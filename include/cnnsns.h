@@ -270,6 +270,15 @@ cs_status cs_predictor_tile_rows(cs_ctx *ctx, int rows);
  * Results do not depend on it. CS_EINVAL for any other value. */
 cs_status cs_predictor_tile3(cs_ctx *ctx, int side);
 
+/* Test hook of the bounded device-side waits (a property of the library; the
+ * paper has none): with on != 0 the tensor-core predictor kernels (2-D and
+ * 3-D) first wait, for about 17 ms, for a device flag that nothing sets. The
+ * wait runs out, the kernel ends through its abort path before any MMA
+ * (freeing its TMEM) and raises the device error flag, which
+ * cs_device_status reports as CS_EDEVICE; the context stays usable. on == 0
+ * restores normal launches. Synchronises the device. */
+cs_status cs_debug_hold_predictor(cs_ctx *ctx, int on);
+
 /* Synchronise the device and report whether a bounded device-side wait gave
  * up since the last call (CS_EDEVICE, message in cs_last_error) or CS_OK. */
 cs_status cs_device_status(cs_ctx *ctx);

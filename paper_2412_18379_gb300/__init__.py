@@ -336,6 +336,11 @@ class Context:
     def device_status(self):
         self._check(self.lib.cs_device_status(self.h))
 
+    def debug_hold_predictor(self, on=True):
+        """Test hook: the tensor-core predictor kernels first wait for a device
+        flag that nothing sets, so that the wait runs out (CS_EDEVICE)."""
+        self._check(self.lib.cs_debug_hold_predictor(self.h, 1 if on else 0))
+
     def predictor_precision(self, bf16=True):
         self._check(self.lib.cs_predictor_precision(self.h, 1 if bf16 else 0))
 

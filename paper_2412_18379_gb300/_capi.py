@@ -74,6 +74,7 @@ SIGNATURES = {
     "cs_predictor_engine": (_i32, [_vp, ctypes.c_int]),
     "cs_predictor_tile_rows": (_i32, [_vp, ctypes.c_int]),
     "cs_predictor_tile3": (_i32, [_vp, ctypes.c_int]),
+    "cs_debug_hold_predictor": (_i32, [_vp, ctypes.c_int]),
     "cs_device_status": (_i32, [_vp]),
     "cs_predictor_size": (_i64, [ctypes.c_int]),
     "cs_predictor_load": (_i32, [_vp, ctypes.c_int, _vp, _i64]),

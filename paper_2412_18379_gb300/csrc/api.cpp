@@ -154,6 +154,7 @@ void cs_destroy(cs_ctx *ctx) {
     for (auto &kv : ctx->meshes) free_mesh(ctx, kv.second);
     for (auto &p : ctx->pred) cs::predictor_release(ctx, p);
     cs::dfree(ctx, ctx->dev_err);
+    cs::dfree(ctx, ctx->hold_flag);
     cs::dfree(ctx, ctx->scratch.counters);
     cs::dfree(ctx, ctx->scratch.stats);
     cs::dfree(ctx, ctx->scratch.stage);

@@ -75,12 +75,21 @@ int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, flo
                     int sm_count, cudaStream_t st);
 int launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,
                 int sm_count, cudaStream_t st);
+// Test hook of the tensor-core predictor kernels: when flag is not null, the
+// kernel first waits (bounded, `polls` polls) for *flag != 0 before any MMA;
+// nothing sets the flag, so the wait runs out and the kernel ends through its
+// abort path with the device error flag raised.
+struct TcHold {
+    const int *flag = nullptr;
+    uint32_t polls = 0;
+};
 // tensor-core grid inference of the 2-D predictor (cnn_tc.cu)
 int64_t tc_packed_bytes();
 int launch_pack_tc(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
 // tile_rows: output rows per tile (24, 13 or 8), 0 = tc_pick_tile_rows
 int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st);
+                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st,
+                    TcHold hold = TcHold());
 // the tile height with the least estimated cost on a grid (24, 13 or 8)
 int tc_pick_tile_rows(const DevMesh &m, int sm_count);
 // tensor-core grid inference of the 3-D predictor (cnn3d_tc.cu); tile: side of
@@ -88,7 +97,8 @@ int tc_pick_tile_rows(const DevMesh &m, int sm_count);
 int64_t tc3_packed_bytes();
 int launch_pack_tc3(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
 int launch_cnn3d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, int tile, cudaStream_t st);
+                    float *dhat, int *err, int sm_count, int tile, cudaStream_t st,
+                    TcHold hold = TcHold());
 int tc3_pick_tile(const DevMesh &m, int sm_count);
 int launch_pairs(const DevMesh &m, int64_t n, const double *x, const double *u, double dt,
                  int64_t *cells, float *target, int sm_count, cudaStream_t st);

@@ -145,7 +145,7 @@ __device__ __forceinline__ bool epi3_or(bool flag) {
 template <int T>
 __global__ void __launch_bounds__(kThreads3, 1) cnn3d_tc_kernel(
     const DevMesh m, const float *__restrict__ U, float s0, float s1, float s2,
-    const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err) {
+    const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err, TcHold hold) {
     using G = Geo3<T>;
     constexpr int D = G::D;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -229,7 +229,10 @@ __global__ void __launch_bounds__(kThreads3, 1) cnn3d_tc_kernel(
             const uint64_t d_wc = sdesc(smem_addr(wsm + Tc3Layout::wc), 32 * 16, 128);
             const uint64_t d_f1 = sdesc(smem_addr(wsm + Tc3Layout::f1), 256 * 16, 128);
             constexpr uint32_t id32 = idesc_bf16(128, 32), id256 = idesc_bf16(128, 256);
-            for (int j = 0; j < G::kItems; ++j) {
+            // test hook: a wait for a flag that nothing sets runs out before any MMA
+            const bool held = hold.flag && k == 0 &&
+                              !__all_sync(kFull, wait_flag(hold.flag, hold.polls, abort_flag, err));
+            for (int j = 0; j < G::kItems && !held; ++j) {
                 if (!wait_count(epi_done, base + uint32_t(G::need(j)), abort_flag, err)) break;
                 fence_after();
                 int l, mt;
@@ -410,7 +413,7 @@ int64_t cost3(const DevMesh &m, int sm_count) {
 
 template <int T>
 int launch3(const DevMesh &m, const float *U, double dt, const uint8_t *packed, float *dhat,
-            int *err, int sm_count, cudaStream_t st) {
+            int *err, int sm_count, cudaStream_t st, TcHold hold) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(cnn3d_tc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -419,7 +422,8 @@ int launch3(const DevMesh &m, const float *U, double dt, const uint8_t *packed, 
     }
     const int grid = int(std::min<int64_t>(tiles3<T>(m), sm_count));
     launch_pdl(cnn3d_tc_kernel<T>, dim3(grid), dim3(kThreads3), size_t(Geo3<T>::kSmTotal), st, m,
-               U, float(dt / m.sa[0]), float(dt / m.sa[1]), float(dt / m.sa[2]), packed, dhat, err);
+               U, float(dt / m.sa[0]), float(dt / m.sa[1]), float(dt / m.sa[2]), packed, dhat, err,
+               hold);
     return 1;
 }
 
@@ -440,11 +444,11 @@ int tc3_pick_tile(const DevMesh &m, int sm_count) {
 }
 
 int launch_cnn3d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, int tile, cudaStream_t st) {
+                    float *dhat, int *err, int sm_count, int tile, cudaStream_t st, TcHold hold) {
     const int t = tile ? tile : tc3_pick_tile(m, sm_count);
-    if (t == 4) return launch3<4>(m, U, dt, packed, dhat, err, sm_count, st);
-    if (t == 3) return launch3<3>(m, U, dt, packed, dhat, err, sm_count, st);
-    return launch3<2>(m, U, dt, packed, dhat, err, sm_count, st);
+    if (t == 4) return launch3<4>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    if (t == 3) return launch3<3>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    return launch3<2>(m, U, dt, packed, dhat, err, sm_count, st, hold);
 }
 
 }  // namespace cs

@@ -241,7 +241,7 @@ __device__ __forceinline__ void issue_fc1(uint32_t dcol, uint64_t adesc, uint64_
 template <int TH>
 __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     const DevMesh m, const float *__restrict__ U, float scale0, float scale1,
-    const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err) {
+    const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err, TcHold hold) {
     using G = Geo<TH>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *x0 = smem + G::kSmX0;
@@ -439,6 +439,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
         //      for mt = 6, conv1 for mt = 7); conv2..conv4 M-tile mt needs the
         //      previous layer's M-tiles mt and mt + 1 ----
         bool ok = true, stop = false;
+        // test hook: a wait for a flag that nothing sets runs out; the first
+        // handoff then stops the conv warp before any MMA
+        if (hold.flag) ok = __all_sync(kFull, wait_flag(hold.flag, hold.polls, abort_flag, err)) != 0;
         for (int k = 0; !stop; ++k) {
             const int tile = blockIdx.x + k * gridDim.x;
             if (tile >= n_tiles) break;
@@ -675,7 +678,7 @@ int64_t tile_cost(const DevMesh &m, int sm_count) {
 
 template <int TH>
 int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *packed, float *dhat,
-                int *err, int sm_count, cudaStream_t st) {
+                int *err, int sm_count, cudaStream_t st, TcHold hold) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(cnn2d_tc_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -684,7 +687,7 @@ int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *pack
     }
     const int grid = std::min(tiles_of<TH>(m), sm_count);
     launch_pdl(cnn2d_tc_kernel<TH>, dim3(grid), dim3(kThreadsTC), size_t(Geo<TH>::kSmTotal), st, m,
-               U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err);
+               U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err, hold);
     return 1;
 }
 
@@ -698,11 +701,12 @@ int tc_pick_tile_rows(const DevMesh &m, int sm_count) {
 }
 
 int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
-                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st) {
+                    float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st,
+                    TcHold hold) {
     const int th = tile_rows ? tile_rows : tc_pick_tile_rows(m, sm_count);
-    if (th == 24) return launch_rows<24>(m, U, dt, packed, dhat, err, sm_count, st);
-    if (th == 13) return launch_rows<13>(m, U, dt, packed, dhat, err, sm_count, st);
-    return launch_rows<8>(m, U, dt, packed, dhat, err, sm_count, st);
+    if (th == 24) return launch_rows<24>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    if (th == 13) return launch_rows<13>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    return launch_rows<8>(m, U, dt, packed, dhat, err, sm_count, st, hold);
 }
 
 }  // namespace cs

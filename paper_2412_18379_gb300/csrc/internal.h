@@ -261,6 +261,7 @@ struct cs_ctx {
     int tc_tile_rows = 0;    // 2-D tensor-core predictor tile height, 0 = automatic
     int tc3_tile = 0;        // 3-D tensor-core predictor tile side, 0 = automatic
     int *dev_err = nullptr;  // device error flag of bounded waits
+    int *hold_flag = nullptr;  // test hook: a device flag nothing sets (cs_debug_hold_predictor)
     cs::Server *server = nullptr;   // serving loop (serve.cpp), if started
     std::atomic<int64_t> launches{0};
 };

@@ -411,12 +411,18 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
                                            : launch_pack_tc3(P->w, NetShape(3), P->packed, st);
             P->packed_dirty = false;
         }
+        TcHold hold;
+        if (ctx->hold_flag) {
+            hold.flag = ctx->hold_flag;
+            hold.polls = 1u << 16;
+        }
         if (m->d.dim == 2)
             ctx->launches += launch_cnn2d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
-                                             ctx->dev_err, ctx->sm_count, ctx->tc_tile_rows, st);
+                                             ctx->dev_err, ctx->sm_count, ctx->tc_tile_rows, st,
+                                             hold);
         else
             ctx->launches += launch_cnn3d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
-                                             ctx->dev_err, ctx->sm_count, ctx->tc3_tile, st);
+                                             ctx->dev_err, ctx->sm_count, ctx->tc3_tile, st, hold);
         return CS_OK;
     }
     if (m->d.dim == 3 && ctx->engine == 2) return predict_tiles(ctx, *P, m, grid, dt, dhat, st);
@@ -540,6 +546,23 @@ cs_status cs_predictor_engine(cs_ctx *ctx, int engine) {
     if (!ctx || engine < 0 || engine > 2) return CS_EINVAL;
     if (ctx->server) return fail(ctx, CS_EBUSY, "cs_predictor_engine: stop serving first");
     ctx->engine = engine;
+    return CS_OK;
+}
+
+cs_status cs_debug_hold_predictor(cs_ctx *ctx, int on) {
+    if (!ctx) return CS_EINVAL;
+    PCHK(cudaSetDevice(ctx->device));
+    PCHK(cudaDeviceSynchronize());
+    if (!on) {
+        dfree(ctx, ctx->hold_flag);
+        ctx->hold_flag = nullptr;
+        return CS_OK;
+    }
+    if (!ctx->hold_flag) {
+        cs_status rc = dalloc(ctx, &ctx->hold_flag, 1);
+        if (rc) return rc;
+    }
+    PCHK(cudaMemset(ctx->hold_flag, 0, sizeof(int)));
     return CS_OK;
 }
 

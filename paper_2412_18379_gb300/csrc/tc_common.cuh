@@ -205,5 +205,23 @@ __device__ __forceinline__ void bias_relu_bf16(const float *v, const float *bias
     }
 }
 
+// Bounded wait until the device-memory flag *flag is non-zero (an acquire
+// load per poll, at most `polls` polls ~256 ns apart). Gives up (false) when
+// the CTA's abort flag is raised, or at the limit, raising the abort flag and
+// the device error flag itself.
+__device__ __forceinline__ bool wait_flag(const int *flag, uint32_t polls, volatile int *abort_flag,
+                                          int *err) {
+    for (uint32_t i = 0; i < polls; ++i) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0) return true;
+        if (*abort_flag) return false;
+        __nanosleep(256);
+    }
+    *abort_flag = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
 }  // namespace
 }  // namespace cs

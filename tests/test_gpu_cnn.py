@@ -839,3 +839,42 @@ def test_tensor_core_gradients_at_training_batch(ctx, dim):
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         assert rel <= (1.5e-1 if li == 0 else 5e-2), (li, rel)
         o += n
+
+
+@pytest.mark.parametrize("name,kw,stride", [("tg2d", {"n_side": 201}, 1), ("abc3d", {"n_side": 25}, 1)])
+def test_a_wait_that_runs_out_ends_the_kernel_with_cs_edevice(ctx, name, kw, stride):
+    """The bounded waits of the tensor-core predictor kernels: with the test
+    hook on, each kernel first waits (about 17 ms) for a device flag that
+    nothing sets; the wait runs out, the kernel ends through its abort path
+    (no MMA issued, TMEM freed) and cs_device_status reports CS_EDEVICE. The
+    context stays usable: with the hook off the same prediction gives the bits
+    it gave before, and the device status is clean again."""
+    import time
+    import torch
+    import paper_2412_18379_gb300 as cs
+    c = make_case(name, **kw)
+    ctx.load_predictor(c.dim, init_weights(c.dim, 3))
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(stride)
+    ctx.grid_velocity(mesh, _dev(c.u))
+    cells = int(np.prod(mesh.info()["pred_grid"]))
+    before = torch.empty((cells, c.dim), dtype=torch.float32, device="cuda")
+    ctx.predict(mesh, c.dt, out=before)
+    ctx.device_status()
+    held = torch.full((cells, c.dim), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.debug_hold_predictor(True)
+    try:
+        t0 = time.perf_counter()
+        ctx.predict(mesh, c.dt, out=held)
+        with pytest.raises(cs.CsError) as e:
+            ctx.device_status()
+        assert e.value.code == -8 and "gave up" in str(e.value)
+        assert time.perf_counter() - t0 < 30.0
+    finally:
+        ctx.debug_hold_predictor(False)
+    ctx.device_status()                      # the flag was read and cleared
+    after = torch.full((cells, c.dim), float("nan"), dtype=torch.float32, device="cuda")
+    ctx.predict(mesh, c.dt, out=after)
+    ctx.device_status()
+    assert np.array_equal(before.cpu().numpy().view(np.uint32), after.cpu().numpy().view(np.uint32))
+    mesh.release()
