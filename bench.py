@@ -70,7 +70,8 @@ def source_sha(files):
 
 
 WALK_SOURCES = ("walk.cu", "walk_common.cuh")
-CNN_SOURCES = ("cnn_tc.cu",)
+CNN_SOURCES = ("cnn_tc.cu", "tc_common.cuh")
+CNN3D_SOURCES = ("cnn3d_tc.cu", "tc_common.cuh")
 
 
 def ncu_traffic(profile, sources):
@@ -235,6 +236,8 @@ def train_predictor(ctx, mesh, case, n_fields, steps, batch, seed):
     dim = case.dim
     field = fourier_modes_2d if dim == 2 else fourier_modes_3d
     ctx.load_predictor(dim, init_weights(dim, seed))
+    if n_fields == 0:
+        return {"pairs": 0, "fields": 0, "note": "untrained predictor (profiling runs)"}
     rng = np.random.default_rng(seed)
     x = torch.from_numpy(case.x).cuda()
     wins, tgts = [], []
@@ -556,7 +559,8 @@ def main():
     ap.add_argument("--train-steps-3d", type=int, default=3000)
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the CFL sweep over the 2-D and 3-D workloads")
-    ap.add_argument("--train-fields", type=int, default=4)
+    ap.add_argument("--train-fields", type=int, default=4,
+                    help="8-mode fields of training pairs (0: an untrained predictor)")
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
     ap.add_argument("--ref-sample", type=int, default=1002001)
