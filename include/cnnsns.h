@@ -378,6 +378,123 @@ cs_status cs_track_dhat(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x
                         int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
                         int32_t *start_out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * The paper's classifier predictor (Sec. 2.3, Eq. 7-8)
+ *
+ * A second start predictor, per particle rather than per grid cell: the CNN
+ * classifies x_p among the W^dim ASG cells of a window centred on the ASG
+ * cell of x_p (W = 9 in 2-D, 7 in 3-D). Its inputs are the element centroids
+ * of the window, averaged per ASG cell (average pooling, computed once per
+ * mesh at upload in FP64), each minus x_p in ASG cell units, with a cell
+ * outside the grid or without a centroid padded by its own centre; and x_p's
+ * offset from its cell's centre. Two branches read them: two zero-padded
+ * 3^dim convolutions of 32 channels with ReLU and a 2^dim average pooling on
+ * the window; two fully connected layers of h1 = 256 with ReLU on the offset
+ * (Sec. 3.1). A fully connected layer of h2 = 512 (Sec. 3.1) with ReLU on
+ * their concatenation and one to the W^dim logits follow; the softmax over
+ * them is B_l of Eq. 7. K_p (Eq. 8) is the ASG seed of the most probable
+ * cell. Training minimises the cross-entropy against the window cell that
+ * holds the centroid of the host K_t found by plain SNS (clamped into the
+ * window). Operands of every layer are BF16 with FP32 accumulation; master
+ * weights, Adam state and the softmax are FP32.
+ *
+ * Layout of the parameters (floats): per layer W then b, layers conv1
+ * [32][dim][3^dim], conv2 [32][32][3^dim], xp1 [256][dim], xp2 [256][256],
+ * fuse [512][32 (W/2)^dim + 256], logits [W^dim][512]. Convolution taps are
+ * ordered dz, dy, dx (dx fastest); the pooled features enter fuse as
+ * [channel][z][y][x] (x fastest), followed by the 256 offset features.
+ * Window cells and classes are numbered x fastest.
+ * ------------------------------------------------------------------------- */
+
+/* Number of floats of the classifier of dimension dim (0 for other dim). */
+int64_t cs_classifier_size(int dim);
+
+/* Window edge W of the classifier of dimension dim (9, 7; 0 for other dim). */
+int32_t cs_classifier_window(int dim);
+
+/* Load (replace) the classifier of dimension dim from HOST parameters; resets
+ * the optimiser state. Errors: CS_EINVAL (dim, n != cs_classifier_size),
+ * CS_ENOMEM. */
+cs_status cs_classifier_load(cs_ctx *ctx, int dim, const float *params, int64_t n);
+
+/* Copy the classifier's FP32 master parameters to HOST memory. CS_ENOPRED if
+ * none is loaded, CS_EINVAL if n != cs_classifier_size. */
+cs_status cs_classifier_save(cs_ctx *ctx, int dim, float *params_out, int64_t n);
+
+/* Departure points x_p = x - (u * dt) (Eq. 3, FP64, no fused multiply-add)
+ * of n particles (DEVICE pointers, [n][dim] each). Enqueued on stream. */
+cs_status cs_departure(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                       const double *u, double dt, double *xp_out, void *stream);
+
+/* The classifier's inputs for n departure points xp [n][dim] (DEVICE):
+ * window_out [n][dim][W^dim] (FP32 of the FP64 value (p - x_p) / s_k, p the
+ * pooled centroid or the padding centre, s the ASG cell size), offset_out
+ * [n][dim] (FP32 of (x_p - lo) / s - (cell + 1/2)). No network needed.
+ * Enqueued on stream. */
+cs_status cs_classifier_features(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *xp,
+                                 float *window_out, float *offset_out, void *stream);
+
+/* Logits H [n][W^dim] of n departure points (DEVICE pointers); the softmax of
+ * a row is B_l of Eq. 7. Synchronous (the batch is processed in chunks
+ * through the context's workspace). CS_ENOPRED without a classifier of the
+ * mesh's dimension. */
+cs_status cs_classifier_forward(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *xp,
+                                float *logits_out);
+
+/* Class labels of n departure points with known hosts (DEVICE; host: user
+ * ids from plain SNS): the window cell (x fastest) holding the host's
+ * centroid, its coordinates clamped into the window; -1 where host < 0.
+ * Enqueued on stream. */
+cs_status cs_classifier_labels(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *xp,
+                               const int32_t *host, int32_t *label_out, void *stream);
+
+/* Training pairs of the classifier, by plain SNS (DEVICE pointers): for n
+ * particles at x with velocities u and plain starts `start` (user ids, or
+ * NULL for the mesh nodes), xp_out [n][dim] = x_p and label_out [n] = the
+ * class of x_p's host (cs_classifier_labels; -1 outside the mesh). Enqueued
+ * on stream. */
+cs_status cs_classifier_pairs(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                              const double *u, double dt, const int32_t *start, double *xp_out,
+                              int32_t *label_out, void *stream);
+
+/* Gradient of the cross-entropy (mean over the rows whose label lies in
+ * [0, W^dim); other rows count for nothing) of the classifier on B
+ * (x_p, label) pairs of a mesh (DEVICE xp [B][dim], labels [B]; grad_out
+ * [cs_classifier_size], same layout as the parameters), without updating the
+ * parameters; loss_out (HOST, may be NULL). Synchronous. */
+cs_status cs_classifier_grad(cs_ctx *ctx, int32_t mesh_id, int64_t B, const double *xp,
+                             const int32_t *labels, float *grad_out, float *loss_out);
+
+/* Train the classifier on N (x_p, label) pairs of a mesh (DEVICE) with Adam
+ * (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the cross-entropy, for `steps`
+ * batches of `batch` pairs drawn without replacement per epoch from a
+ * generator seeded by `seed` (the same draw as cs_predictor_train). loss_out
+ * (HOST, may be NULL) receives every step's loss. Synchronous. */
+cs_status cs_classifier_train(cs_ctx *ctx, int32_t mesh_id, const double *xp,
+                              const int32_t *labels, int64_t N, int64_t batch, int64_t steps,
+                              float lr, uint64_t seed, float *loss_out);
+
+/* Start elements K_p (Eq. 8) from given logits (DEVICE): the class of the
+ * largest logit (the lowest class among equal ones; a row without a finite
+ * maximum has none), its window cell's ASG seed as a user id, or fallback[p]
+ * where the cell lies outside the grid, its centre outside the mesh or the
+ * row has no class (fallback: user ids, or NULL for the mesh nodes' plain
+ * starts, n == n_vertices). class_out (may be NULL) receives the class, or
+ * -1. Enqueued on stream. */
+cs_status cs_classifier_start(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *xp,
+                              const float *logits, const int32_t *fallback, int32_t *start_out,
+                              int32_t *class_out, void *stream);
+
+/* CNN-SNS with the classifier (Algorithm 2 with Eq. 7-8's start): departure
+ * points, the classifier's start of every particle (cs_classifier_start with
+ * the plain start as fallback), then Algorithm 1 from it. Arguments, results
+ * and errors as cs_track with CS_SNS (DEVICE pointers); start_out receives
+ * the classifier's start. Hosts are those of plain SNS. Synchronous. */
+cs_status cs_track_classifier(cs_ctx *ctx, int32_t mesh_id, int64_t n, const double *x,
+                              const double *u, double dt, const int32_t *start,
+                              int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                              int32_t *start_out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of tracking requests over resident meshes.   */
 /* (A property of the library: the paper tracks one solver step at a time.) */

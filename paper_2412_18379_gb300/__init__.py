@@ -84,6 +84,26 @@ def check_track_args(dim, x, u, start=None, out=None, on_device=True):
     return n
 
 
+def _check_dev(name, a, dtype, shape, device=None):
+    """A contiguous CUDA tensor of the given dtype and shape (None: any
+    extent on that axis), on `device` if given. Raises ValueError."""
+    if a is None:
+        raise ValueError("%s is missing" % name)
+    if not getattr(a, "is_cuda", False):
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if device is not None and a.device != device:
+        raise ValueError("%s must be on %s" % (name, device))
+    if _dtype_name(a) != dtype:
+        raise ValueError("%s must be %s, not %s" % (name, dtype, _dtype_name(a)))
+    if not _contiguous(a):
+        raise ValueError("%s must be contiguous" % name)
+    if a.ndim != len(shape) or any(s is not None and a.shape[i] != s
+                                   for i, s in enumerate(shape)):
+        raise ValueError("%s must have shape %s, not %s"
+                         % (name, tuple("n" if s is None else s for s in shape),
+                            tuple(a.shape)))
+
+
 class Mesh:
     def __init__(self, ctx, mesh_id, dim, n_v, n_e):
         self.ctx = ctx
@@ -437,6 +457,137 @@ class Context:
             self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(dhat),
             _ptr(out["host"]), _ptr(out["path_len"]), _ptr(out["status"]),
             _ptr(out.get("start")), _stream_ptr(st)))
+        return out
+
+    # ---------------- classifier predictor (Sec. 2.3, Eq. 7-8) ----------------
+    def classifier_size(self, dim):
+        return int(self.lib.cs_classifier_size(dim))
+
+    def classifier_window(self, dim):
+        return int(self.lib.cs_classifier_window(dim))
+
+    def load_classifier(self, dim, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.classifier_size(dim):
+            raise ValueError("the classifier of dim %d has %d parameters, not %d"
+                             % (dim, self.classifier_size(dim), p.size))
+        self._check(self.lib.cs_classifier_load(self.h, dim, _ptr(p), p.size))
+
+    def save_classifier(self, dim):
+        out = np.empty(self.classifier_size(dim), dtype=np.float32)
+        self._check(self.lib.cs_classifier_save(self.h, dim, _ptr(out), out.size))
+        return out
+
+    def _xp_rows(self, mesh, xp, name="xp"):
+        _check_dev(name, xp, "float64", (None, mesh.dim))
+        return int(xp.shape[0])
+
+    def departure(self, mesh, x, u, dt, stream=None):
+        """x_p = x - (u * dt) on the device (float64 CUDA [n, dim])."""
+        import torch
+        n = check_track_args(mesh.dim, x, u)
+        xp = torch.empty((n, mesh.dim), dtype=torch.float64, device=x.device)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        self._check(self.lib.cs_departure(self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt),
+                                          _ptr(xp), _stream_ptr(st)))
+        return xp
+
+    def classifier_features(self, mesh, xp, stream=None):
+        """(window [n, dim, W..W], offset [n, dim]) float32 CUDA tensors."""
+        import torch
+        n = self._xp_rows(mesh, xp)
+        W = self.classifier_window(mesh.dim)
+        win = torch.empty((n, mesh.dim) + (W,) * mesh.dim, dtype=torch.float32, device=xp.device)
+        off = torch.empty((n, mesh.dim), dtype=torch.float32, device=xp.device)
+        st = stream if stream is not None else torch.cuda.current_stream(xp.device)
+        self._check(self.lib.cs_classifier_features(self.h, mesh.id, n, _ptr(xp), _ptr(win),
+                                                    _ptr(off), _stream_ptr(st)))
+        return win, off
+
+    def classifier_forward(self, mesh, xp):
+        """Logits [n, W^dim] (float32 CUDA) of departure points xp."""
+        import torch
+        n = self._xp_rows(mesh, xp)
+        ncls = self.classifier_window(mesh.dim) ** mesh.dim
+        out = torch.empty((n, ncls), dtype=torch.float32, device=xp.device)
+        torch.cuda.current_stream(xp.device).synchronize()
+        self._check(self.lib.cs_classifier_forward(self.h, mesh.id, n, _ptr(xp), _ptr(out)))
+        return out
+
+    def classifier_labels(self, mesh, xp, host, stream=None):
+        import torch
+        n = self._xp_rows(mesh, xp)
+        _check_dev("host", host, "int32", (n,), xp.device)
+        out = torch.empty(n, dtype=torch.int32, device=xp.device)
+        st = stream if stream is not None else torch.cuda.current_stream(xp.device)
+        self._check(self.lib.cs_classifier_labels(self.h, mesh.id, n, _ptr(xp), _ptr(host),
+                                                  _ptr(out), _stream_ptr(st)))
+        return out
+
+    def classifier_pairs(self, mesh, x, u, dt, start=None, stream=None):
+        """(xp [n, dim] float64, labels [n] int32) CUDA tensors by plain SNS."""
+        import torch
+        n = check_track_args(mesh.dim, x, u, start)
+        xp = torch.empty((n, mesh.dim), dtype=torch.float64, device=x.device)
+        lab = torch.empty(n, dtype=torch.int32, device=x.device)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        self._check(self.lib.cs_classifier_pairs(self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt),
+                                                 _ptr(start), _ptr(xp), _ptr(lab),
+                                                 _stream_ptr(st)))
+        return xp, lab
+
+    def classifier_grad(self, mesh, xp, labels):
+        import torch
+        n = self._xp_rows(mesh, xp)
+        _check_dev("labels", labels, "int32", (n,), xp.device)
+        g = torch.empty(self.classifier_size(mesh.dim), dtype=torch.float32, device=xp.device)
+        loss = np.zeros(1, dtype=np.float32)
+        torch.cuda.current_stream(xp.device).synchronize()
+        self._check(self.lib.cs_classifier_grad(self.h, mesh.id, n, _ptr(xp), _ptr(labels),
+                                                _ptr(g), _ptr(loss)))
+        return g, float(loss[0])
+
+    def train_classifier(self, mesh, xp, labels, batch=4096, steps=100, lr=1e-3, seed=0):
+        import torch
+        n = self._xp_rows(mesh, xp)
+        _check_dev("labels", labels, "int32", (n,), xp.device)
+        losses = np.empty(steps, dtype=np.float32)
+        torch.cuda.current_stream(xp.device).synchronize()
+        self._check(self.lib.cs_classifier_train(self.h, mesh.id, _ptr(xp), _ptr(labels), n,
+                                                 int(batch), int(steps), float(lr), int(seed),
+                                                 _ptr(losses)))
+        return losses
+
+    def classifier_start(self, mesh, xp, logits, fallback=None, stream=None):
+        """(start [n] user ids, class [n]) int32 CUDA tensors from logits."""
+        import torch
+        n = self._xp_rows(mesh, xp)
+        _check_dev("logits", logits, "float32",
+                   (n, self.classifier_window(mesh.dim) ** mesh.dim), xp.device)
+        if fallback is not None:
+            _check_dev("fallback", fallback, "int32", (n,), xp.device)
+        elif n != mesh.n_vertices:
+            raise ValueError("fallback is needed unless the particles are the mesh nodes")
+        start = torch.empty(n, dtype=torch.int32, device=xp.device)
+        cls = torch.empty(n, dtype=torch.int32, device=xp.device)
+        st = stream if stream is not None else torch.cuda.current_stream(xp.device)
+        self._check(self.lib.cs_classifier_start(self.h, mesh.id, n, _ptr(xp), _ptr(logits),
+                                                 _ptr(fallback), _ptr(start), _ptr(cls),
+                                                 _stream_ptr(st)))
+        return start, cls
+
+    def track_classifier(self, mesh, x, u, dt, start=None, out=None, start_out=False,
+                         stream=None):
+        """CNN-SNS with the classifier's start (Eq. 8); same arrays as track()."""
+        import torch
+        n = check_track_args(mesh.dim, x, u, start, out)
+        out = self._device_out(n, x.device, out, start_out)
+        check_track_args(mesh.dim, x, u, start, out)
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        self._check(self.lib.cs_track_classifier(
+            self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(out["host"]),
+            _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start")),
+            _stream_ptr(st)))
         return out
 
     # ---------------- serving ----------------

@@ -90,6 +90,21 @@ SIGNATURES = {
     "cs_predictor_grad": (_i32, [_vp, ctypes.c_int, _i64, _vp, _vp, _vp, _vp]),
     "cs_track_dhat": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp, _vp,
                              _vp]),
+    "cs_classifier_size": (_i64, [ctypes.c_int]),
+    "cs_classifier_window": (_i32, [ctypes.c_int]),
+    "cs_classifier_load": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
+    "cs_classifier_save": (_i32, [_vp, ctypes.c_int, _vp, _i64]),
+    "cs_departure": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp]),
+    "cs_classifier_features": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp]),
+    "cs_classifier_forward": (_i32, [_vp, _i32, _i64, _vp, _vp]),
+    "cs_classifier_labels": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp]),
+    "cs_classifier_pairs": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp]),
+    "cs_classifier_grad": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp]),
+    "cs_classifier_train": (_i32, [_vp, _i32, _vp, _vp, _i64, _i64, _i64, ctypes.c_float,
+                                   ctypes.c_uint64, _vp]),
+    "cs_classifier_start": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "cs_track_classifier": (_i32, [_vp, _i32, _i64, _vp, _vp, _dbl, _vp, _vp, _vp, _vp, _vp,
+                                   _vp]),
     "cs_profile_enable": (_i32, [_vp, ctypes.c_int]),
     "cs_profile_read": (_i32, [_vp, _vp, ctypes.c_int]),
 }

@@ -37,6 +37,7 @@ def _cuda_inc():
 CU_FLAGS = {
     "walk.cu": ["--fmad=false"],
     "search.cu": ["--fmad=false"],
+    "classifier.cu": ["--fmad=false"],
 }
 
 

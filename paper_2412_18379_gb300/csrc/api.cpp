@@ -153,6 +153,7 @@ void cs_destroy(cs_ctx *ctx) {
     release_fields(ctx, 0);
     for (auto &kv : ctx->meshes) free_mesh(ctx, kv.second);
     for (auto &p : ctx->pred) cs::predictor_release(ctx, p);
+    cs::classifier_release_all(ctx);
     cs::dfree(ctx, ctx->dev_err);
     cs::dfree(ctx, ctx->hold_flag);
     cs::dfree(ctx, ctx->scratch.counters);
@@ -254,7 +255,9 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         n_asg *= H.ga[k];
         n_b *= H.gb[k];
     }
-    if ((rc = dev_copy<int32_t>(ctx, m, nullptr, size_t(n_asg), &seed))) {
+    double *pool = nullptr;
+    if ((rc = dev_copy<int32_t>(ctx, m, nullptr, size_t(n_asg), &seed)) ||
+        (rc = dev_copy(ctx, m, H.pool.data(), H.pool.size(), &pool))) {
         free_mesh(ctx, m);
         return rc;
     }
@@ -265,6 +268,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     d.iperm = iperm;
     d.node_elem = node;
     d.seed = seed;
+    d.pool = pool;
     d.bstart = bstart;
     d.bitems = bitems;
     for (int k = 0; k < 3; ++k) {

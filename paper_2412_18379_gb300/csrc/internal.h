@@ -64,6 +64,7 @@ struct DevMesh {
     const int32_t *iperm;     // user id -> internal id
     const int32_t *node_elem; // [n_v] internal id of the plain-SNS start
     const int32_t *seed;      // [n_asg] internal id of the host of each cell centre, or -1
+    const double *pool;       // [n_asg][dim] mean element centroid per ASG cell, NaN if none
     const int32_t *bstart;    // [n_bucket + 1] offsets into bitems
     const int32_t *bitems;    // internal ids listed per bucket cell
     double lo[3], hi[3];
@@ -152,6 +153,9 @@ struct Predictor {
     bool packed_dirty = true;
 };
 
+// The classifier start predictor of one dimension (classifier.cpp).
+struct Classifier;
+
 // Device scratch owned by a context.
 struct Scratch {
     int32_t *counters = nullptr;   // [0], [1] work cursors of alternate walks (16 reserved)
@@ -187,6 +191,7 @@ struct HostMesh {
     std::vector<unsigned char> recx; // exact records, internal order
     std::vector<int32_t> conn;       // internal order
     std::vector<double> centroid;    // internal order
+    std::vector<double> pool;        // [n_asg][dim] mean centroid per ASG cell, NaN if none
     std::vector<int32_t> node_elem;  // user ids
     std::vector<int32_t> bstart, bitems;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -257,6 +262,7 @@ struct cs_ctx {
     cs::Scratch scratch;
     cs::Profiler prof;
     cs::Predictor pred[2];   // dim 2, dim 3
+    cs::Classifier *cls[2] = {nullptr, nullptr};   // classifier predictors, dim 2, 3
     int engine = 1;          // grid prediction: 1 tensor cores, 0 window GEMMs, 2 CUDA-core tiles (3-D)
     int tc_tile_rows = 0;    // 2-D tensor-core predictor tile height, 0 = automatic
     int tc3_tile = 0;        // 3-D tensor-core predictor tile side, 0 = automatic
@@ -301,6 +307,8 @@ cs_status prepare_serving(cs_ctx *ctx);
 bool serving_predictor_ready(cs_ctx *ctx, const Mesh *m);
 // serve.cpp
 void serve_release(cs_ctx *ctx);
+// classifier.cpp: free the context's classifiers
+void classifier_release_all(cs_ctx *ctx);
 // CNN-SNS start predictions of mesh m into m->grid_dhat: from the grid velocity
 // `grid` if given, else from the nodal velocity u_nodal, resampled into the
 // mesh's stored grid velocity

@@ -285,6 +285,28 @@ cs_status build_host_mesh(int dim, int64_t n_v, const double *xyz, int64_t n_e,
         }
         keys[l] = {hilbert_key(q, dim, bits), int32_t(l)};
     }
+    // ---- average pooling of the element centroids per ASG cell (Sec. 2.3) ----
+    // The classifier's input: per cell the mean centroid of the elements
+    // whose centroid lies in the cell (FP64, summed in user-id order), NaN
+    // where no centroid lies in it.
+    {
+        std::vector<int32_t> cnt(static_cast<size_t>(n_asg), 0);
+        H.pool.assign(static_cast<size_t>(n_asg) * dim, 0.0);
+        for (int64_t l = 0; l < n_e; ++l) {
+            int64_t c = 0;
+            for (int k = dim - 1; k >= 0; --k) {
+                const double t = std::floor((cent[l * dim + k] - H.lo[k]) / H.sa[k]);
+                int64_t i = 0;
+                if (t >= 0.0) i = t > double(H.ga[k] - 1) ? H.ga[k] - 1 : int64_t(t);
+                c = c * H.ga[k] + i;
+            }
+            cnt[c] += 1;
+            for (int k = 0; k < dim; ++k) H.pool[c * dim + k] += cent[l * dim + k];
+        }
+        for (int64_t c = 0; c < n_asg; ++c)
+            for (int k = 0; k < dim; ++k)
+                H.pool[c * dim + k] = cnt[c] > 0 ? H.pool[c * dim + k] / double(cnt[c]) : NAN;
+    }
     std::sort(keys.begin(), keys.end());
     H.order.resize(size_t(n_e));
     H.iperm.resize(size_t(n_e));

@@ -83,7 +83,8 @@ def test_device_calls_need_cuda_tensors():
         check_track_args(2, x, u, s, on_device=True)
 
 
-@pytest.mark.parametrize("call", ["track", "track_noalloc", "track_dhat", "track_host"])
+@pytest.mark.parametrize("call", ["track", "track_noalloc", "track_dhat", "track_host",
+                                  "track_classifier", "classifier_pairs", "departure"])
 def test_entry_points_raise_before_calling_the_library(call):
     ctx = _ctx()
     mesh = _FakeMesh(2)
@@ -103,3 +104,24 @@ def test_field_upload_checks_shape_before_calling_the_library():
         ctx.upload_field(mesh, np.zeros((9, 2)))
     with pytest.raises(ValueError):
         ctx.upload_field(mesh, torch.zeros((10, 2), dtype=torch.float32))
+
+
+@pytest.mark.parametrize("call", ["classifier_features", "classifier_forward"])
+def test_classifier_calls_check_the_points_first(call):
+    """The classifier's entry points take float64 CUDA departure points of the
+    mesh's width; anything else is refused before the library is called."""
+    ctx = _ctx()
+    mesh = _FakeMesh(2)
+    for xp in (torch.zeros((8, 2), dtype=torch.float64),               # host memory
+               torch.zeros((8, 2), dtype=torch.float32),               # wrong dtype
+               torch.zeros((8, 3), dtype=torch.float64),               # wrong width
+               torch.zeros((2, 8), dtype=torch.float64).t()):          # strided
+        with pytest.raises(ValueError):
+            getattr(ctx, call)(mesh, xp)
+
+
+def test_classifier_parameters_are_sized_before_the_library_is_called():
+    ctx = _ctx()
+    ctx.classifier_size = lambda dim: 100
+    with pytest.raises(ValueError):
+        ctx.load_classifier(2, np.zeros(99, dtype=np.float32))
