@@ -47,6 +47,17 @@ REC_ALG_BYTES = {2: 60, 3: 112}      # v0 + M + neighbours per walk step
 CNN_FLOP_PER_CELL_2D = 2 * (18 * 32 + 3 * 288 * 32 + 32 * 256 + 256 * 2)
 
 
+# useful FLOPs of the classifier predictor per particle: conv1 2*W^d*(d*3^d)*32,
+# conv2 2*W^d*(32*3^d)*32, offset branch 2*(d*256 + 256*256), fusion
+# 2*(32*(W/2)^d + 256)*512, logits 2*512*W^d (W = 9 in 2-D, 7 in 3-D)
+def cls_flops_per_particle(dim):
+    W = 9 if dim == 2 else 7
+    P, taps = W ** dim, 3 ** dim
+    pooled = 32 * (W // 2) ** dim
+    return 2 * (P * dim * taps * 32 + P * 32 * taps * 32 + dim * 256 + 256 * 256
+                + (pooled + 256) * 512 + 512 * P)
+
+
 def rank_info():
     r = int(os.environ.get("RANK", "0"))
     w = int(os.environ.get("WORLD_SIZE", "1"))
@@ -278,6 +289,86 @@ def train_predictor(ctx, mesh, case, n_fields, steps, batch, seed):
                 "mean_path_sns": a["path_len"].double().mean().item(),
                 "mean_path_cnn_sns": b["path_len"].double().mean().item(),
                 "hosts_identical": agree}}
+
+
+def classifier_bench(ctx, mesh, case, flush, n_fields, steps, batch, timed, seed, bf16_peak):
+    """The paper's classifier predictor (Sec. 2.3, Eq. 7-8) on the headline
+    mesh: trained on the GPU on (x_p, label) pairs from plain SNS on random
+    8-mode fields (CFL 2-16), then CNN-SNS through it on the headline
+    particles (timed with CUDA events, L2 flushed before every step), its
+    forward pass timed alone, and the hosts checked against plain SNS."""
+    import torch
+    from workloads.fields import fourier_modes_2d, fourier_modes_3d, dt_for_cfl
+    from workloads.weights import init_classifier
+    dim = case.dim
+    field = fourier_modes_2d if dim == 2 else fourier_modes_3d
+    ctx.load_classifier(dim, init_classifier(dim, seed))
+    rng = np.random.default_rng(seed)
+    xn = torch.from_numpy(case.xyz).cuda()
+    xs, labs = [], []
+    t0 = time.perf_counter()
+    for s in range(n_fields):
+        u = field(case.xyz, 300 + s)
+        dt = dt_for_cfl(u, case.h, rng.uniform(2.0, 16.0))
+        xp, lab = ctx.classifier_pairs(mesh, xn, torch.from_numpy(u).cuda(), dt)
+        xs.append(xp)
+        labs.append(lab)
+    XP = torch.cat(xs)
+    LAB = torch.cat(labs)
+    del xs, labs
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = ctx.train_classifier(mesh, XP, LAB, batch=batch, steps=steps, lr=1e-3, seed=seed)
+    t_train = time.perf_counter() - t0
+    n_pairs = int(XP.shape[0])
+    del XP, LAB
+    torch.cuda.empty_cache()
+    x = torch.from_numpy(case.x).cuda()
+    u = torch.from_numpy(case.u).cuda()
+    n = x.shape[0]
+    stream = torch.cuda.current_stream()
+    out = ctx.track_classifier(mesh, x, u, case.dt, start_out=True)     # warm-up
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(timed)]
+    l0 = ctx.launches
+    for i in range(timed):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        ctx.track_classifier(mesh, x, u, case.dt, out=out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = (ctx.launches - l0) // max(1, timed)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / timed
+    xp = ctx.departure(mesh, x, u, case.dt)
+    fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    fa.record(stream)
+    H = ctx.classifier_forward(mesh, xp)
+    fb.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = fa.elapsed_time(fb)
+    del H
+    sns = ctx.track(mesh, x, u, case.dt, mode="sns")
+    torch.cuda.synchronize()
+    flops = cls_flops_per_particle(dim) * n
+    ach = flops / (fwd_ms * 1e-3) / 1e12
+    return {"workload": "the headline particles and field", "n_particles": n,
+            "window": 9 if dim == 2 else 7, "pairs": n_pairs, "fields": n_fields,
+            "batch": batch, "steps": steps, "pair_generation_s": t_pairs, "train_s": t_train,
+            "train_pairs_per_s": steps * batch / t_train, "loss_first": float(losses[0]),
+            "loss_last": float(losses[-10:].mean()),
+            "ms_per_step": ms, "particles_per_s": n / (ms * 1e-3), "launches_per_step": launches,
+            "forward_ms": fwd_ms, "walk_and_rest_ms": ms - fwd_ms,
+            "mean_path_len": out["path_len"].double().mean().item(),
+            "mean_path_len_sns": sns["path_len"].double().mean().item(),
+            "start_is_host": (out["start"] == out["host"]).double().mean().item(),
+            "hosts_identical_to_sns": bool(torch.equal(out["host"], sns["host"])),
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": bf16_peak,
+                         "unit": "TFLOP/s", "frac": ach / bf16_peak,
+                         "kernel": "classifier forward pass (all its kernels)",
+                         "algorithmic_flops_per_launch": flops, "traffic": None}}
 
 
 def serve_bench(ctx, n_requests, rate, slots, seed, pred_stride, repeats):
@@ -563,6 +654,12 @@ def main():
                     help="8-mode fields of training pairs (0: an untrained predictor)")
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
+    ap.add_argument("--cls-fields", type=int, default=2,
+                    help="random fields whose plain-SNS pairs train the classifier")
+    ap.add_argument("--cls-steps", type=int, default=300)
+    ap.add_argument("--cls-batch", type=int, default=4096)
+    ap.add_argument("--cls-timed", type=int, default=3)
+    ap.add_argument("--no-classifier", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=1002001)
     ap.add_argument("--cpu-sample", type=int, default=200000)
     ap.add_argument("--cpu-sample-all", type=int, default=1002001)
@@ -578,6 +675,7 @@ def main():
     if args.quick:
         args.no_cpu_baseline = True
         args.no_sweep = True
+        args.no_classifier = True
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
@@ -690,6 +788,14 @@ def main():
            "transfer": "page-locked host buffers; the call copies the inputs to a device "
                        "staging buffer and the results back (cudaMemcpyAsync), then synchronises"}
 
+    classifier = None
+    if not args.no_classifier and args.particles == "nodes":
+        classifier = classifier_bench(ctx, mesh, case, flush, args.cls_fields, args.cls_steps,
+                                      args.cls_batch, args.cls_timed, seed=rank,
+                                      bf16_peak=bf16_peak)
+        rooflines["classifier"] = classifier["roofline"]
+        torch.cuda.empty_cache()
+
     sweep_rows = None
     if not args.no_sweep and args.particles == "nodes" and args.workload == "tg2d":
         sweep_rows = sweep(ctx, cs, args, rank, dev, dist, max_over_ranks, flush, case, mesh)
@@ -744,7 +850,8 @@ def main():
                                      "BF16 x BF16 -> FP32 on tcgen05"},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],
             "err_mean": main["err_mean"], "modes": results, "opt": opt,
-            "training": training, "serving": serving, "sweep": sweep_rows,
+            "training": training, "classifier": classifier, "serving": serving,
+            "sweep": sweep_rows,
             "rooflines": rooflines,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": main_launches, "clocks": clocks,

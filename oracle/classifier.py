@@ -217,9 +217,11 @@ def backward(params, P, labels, keep):
 
 def labels(om, xp, host, W=None):
     """Class of each sample: the window cell that holds the centroid of its
-    host K_t (user ids), clamped into the window around xp."""
+    host K_t (user ids), clamped into the window around xp; -1 where the
+    sample has no host (host -1: x_p outside the mesh, so there is no K_t)."""
     W = W or window_size(om.dim)
-    cen = om.centroids()[np.asarray(host)]
+    host = np.asarray(host)
+    cen = om.centroids()[np.maximum(host, 0)]
     centre_cell = cell_coords(om, grid_cells(om.lo, om.hi, om.grid, xp))
     first = centre_cell - W // 2
     cc = cell_coords(om, grid_cells(om.lo, om.hi, om.grid, cen))
@@ -227,7 +229,7 @@ def labels(om, xp, host, W=None):
     cls = np.zeros(len(xp), dtype=np.int64)
     for k in range(om.dim - 1, -1, -1):
         cls = cls * W + rel[:, k]
-    return cls
+    return np.where(host >= 0, cls, -1)
 
 
 def start_elements(om, xp, cls, W=None):

@@ -142,6 +142,18 @@ def test_labels_and_the_perfect_classifier_start(mesh2):
     assert r2["path_len"].mean() < r["path_len"][found].mean()
 
 
+def test_a_sample_without_host_has_no_label(mesh2):
+    """A departure point outside the mesh has host -1 (R8) and so no K_t:
+    its label is -1, and the labels of the other samples do not change."""
+    c, om = mesh2
+    xp = np.array([[0.5, 0.5], [2.0, 0.5], [0.25, 0.75]])
+    host = om.locate(xp)
+    assert host[1] == -1 and host[0] >= 0 and host[2] >= 0
+    lab = C.labels(om, xp, host)
+    assert lab[1] == -1
+    assert np.array_equal(lab[[0, 2]], C.labels(om, xp[[0, 2]], host[[0, 2]]))
+
+
 def test_adam_steps_lower_the_loss(mesh2):
     c, om = mesh2
     xp = c.x - c.u * c.dt
