@@ -6,7 +6,8 @@
 // weights). The strides let one kernel serve every product of training: the
 // forward convolutions and fully connected layers, the transposed operands
 // of the weight gradients (as C^T = B A^T, with the long batch dimension as
-// K, split over CTAs and summed with atomics), and the input gradients.
+// K, split over CTAs into partial products that reduce_splits_kernel sums in
+// a fixed order, so every run gives the same bits), and the input gradients.
 //
 // A CTA computes a 128 x BN tile of C. K runs in chunks of 64: all 256
 // threads load a chunk of A (128 x 64) and B (BN x 64), four elements at a
