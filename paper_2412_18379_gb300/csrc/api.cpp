@@ -256,8 +256,10 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         n_b *= H.gb[k];
     }
     double *pool = nullptr;
+    float *pool_f = nullptr;
     if ((rc = dev_copy<int32_t>(ctx, m, nullptr, size_t(n_asg), &seed)) ||
-        (rc = dev_copy(ctx, m, H.pool.data(), H.pool.size(), &pool))) {
+        (rc = dev_copy(ctx, m, H.pool.data(), H.pool.size(), &pool)) ||
+        (rc = dev_copy(ctx, m, H.pool_f.data(), H.pool_f.size(), &pool_f))) {
         free_mesh(ctx, m);
         return rc;
     }
@@ -269,6 +271,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     d.node_elem = node;
     d.seed = seed;
     d.pool = pool;
+    d.pool_f = pool_f;
     d.bstart = bstart;
     d.bitems = bitems;
     for (int k = 0; k < 3; ++k) {

@@ -64,6 +64,10 @@ struct Classifier {
     double *xp = nullptr;
     int32_t *starts = nullptr;
     int64_t xp_cap = 0;
+    // conv1 and conv2 in the fused kernel's layout, refreshed after the
+    // parameters change
+    uint8_t *packed = nullptr;
+    bool packed_dirty = true;
 };
 
 }  // namespace cs
@@ -108,7 +112,7 @@ void release(cs_ctx *ctx, Classifier *C) {
     for (void *p : {static_cast<void *>(C->w), static_cast<void *>(C->g),
                     static_cast<void *>(C->m), static_cast<void *>(C->v),
                     static_cast<void *>(C->loss), static_cast<void *>(C->xp),
-                    static_cast<void *>(C->starts)})
+                    static_cast<void *>(C->starts), static_cast<void *>(C->packed)})
         dfree(ctx, p);
     delete C;
 }
@@ -175,7 +179,48 @@ int relu(cs_ctx *ctx, const float *z, float *y, int64_t n, cudaStream_t st) {
     return launch_relu(z, y, n, ctx->sm_count, st);
 }
 
-// forward of B rows (particles xp[idx[b]], or xp[b]) into C.H [B][n_cls]
+// module 2, fusion and logits of B rows whose pooled features (C.cat's
+// first n_pool columns) and offsets (C.off) are in place, into C.H
+int forward_fc(cs_ctx *ctx, Classifier &C, int64_t B, cudaStream_t st) {
+    const ClsShape S(C.dim);
+    const int sm = ctx->sm_count, d = C.dim;
+    int n = 0;
+    // module 2: the offset of x_p through two fully connected layers
+    n += gemm(ctx, C, C.off, C.w + S.w_off[2], C.h1, C.w + S.b_off[2], B, kClsH1, d, false, true,
+              st);
+    n += relu(ctx, C.h1, C.r1, B * kClsH1, st);
+    n += gemm(ctx, C, C.r1, C.w + S.w_off[3], C.h2, C.w + S.b_off[3], B, kClsH1, kClsH1, false,
+              true, st);
+    launch_cls_cat_relu(C.h2, B, kClsH1, C.cat, S.ldc, S.n_pool, sm, st);
+    n += 1;
+    // fusion and logits
+    n += gemm(ctx, C, C.cat, C.w + S.w_off[4], C.u, C.w + S.b_off[4], B, kClsH2, S.ldc, false,
+              true, st);
+    n += relu(ctx, C.u, C.ru, B * kClsH2, st);
+    n += gemm(ctx, C, C.ru, C.w + S.w_off[5], C.H, C.w + S.b_off[5], B, S.n_cls, kClsH2, false,
+              true, st);
+    return n;
+}
+
+// inference of B particles xp[b] into C.H: module 1 fused on the tensor cores
+// (BF16 operands), or, with FP32 operands, the training path's kernels
+int forward(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t B, const double *xp,
+            const int64_t *idx, cudaStream_t st);
+int infer(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t B, const double *xp,
+          cudaStream_t st) {
+    if (!gemm_bf16()) return forward(ctx, C, m, B, xp, nullptr, st);
+    const ClsShape S(C.dim);
+    if (C.packed_dirty) {
+        launch_cls_pack(C.dim, C.w, S.w_off[0], S.b_off[0], S.w_off[1], S.b_off[1], C.packed, st);
+        C.packed_dirty = false;
+    }
+    launch_cls_conv_tc(m, m.pool_f, B, xp, C.packed, C.cat, S.ldc, C.off, ctx->dev_err,
+                       ctx->sm_count, st);
+    return 2 + forward_fc(ctx, C, B, st);
+}
+
+// forward of B rows (particles xp[idx[b]], or xp[b]) into C.H [B][n_cls],
+// keeping every activation the backward pass reads
 int forward(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t B, const double *xp,
             const int64_t *idx, cudaStream_t st) {
     const ClsShape S(C.dim);
@@ -196,21 +241,7 @@ int forward(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t B, const doubl
               int64_t(kClsCh) * S.taps, false, true, st);
     launch_cls_pool(d, C.z2, B, C.cat, S.ldc, sm, st);
     n += 1;
-    // module 2: the offset of x_p through two fully connected layers
-    n += gemm(ctx, C, C.off, C.w + S.w_off[2], C.h1, C.w + S.b_off[2], B, kClsH1, d, false, true,
-              st);
-    n += relu(ctx, C.h1, C.r1, B * kClsH1, st);
-    n += gemm(ctx, C, C.r1, C.w + S.w_off[3], C.h2, C.w + S.b_off[3], B, kClsH1, kClsH1, false,
-              true, st);
-    launch_cls_cat_relu(C.h2, B, kClsH1, C.cat, S.ldc, S.n_pool, sm, st);
-    n += 1;
-    // fusion and logits
-    n += gemm(ctx, C, C.cat, C.w + S.w_off[4], C.u, C.w + S.b_off[4], B, kClsH2, S.ldc, false,
-              true, st);
-    n += relu(ctx, C.u, C.ru, B * kClsH2, st);
-    n += gemm(ctx, C, C.ru, C.w + S.w_off[5], C.H, C.w + S.b_off[5], B, S.n_cls, kClsH2, false,
-              true, st);
-    return n;
+    return n + forward_fc(ctx, C, B, st);
 }
 
 // gradients of the cross-entropy of C.H against labels[idx[b]] into C.g;
@@ -273,7 +304,8 @@ uint64_t splitmix(uint64_t &s) {
     return z ^ (z >> 31);
 }
 
-// rows per forward chunk: about 1 GB of workspace
+// rows per forward chunk: about 1 GB of workspace on the training path's
+// kernels (the fused path uses a fraction of it)
 int64_t chunk_rows(int dim) { return dim == 2 ? 8192 : 1024; }
 
 cs_status ensure_xp(cs_ctx *ctx, Classifier &C, int64_t n) {
@@ -301,7 +333,7 @@ cs_status forward_chunks(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t n
     if (rc) return rc;
     for (int64_t r0 = 0; r0 < n; r0 += R) {
         const int64_t B = std::min(R, n - r0);
-        ctx->launches += forward(ctx, C, m, B, xp + r0 * C.dim, nullptr, st);
+        ctx->launches += infer(ctx, C, m, B, xp + r0 * C.dim, st);
         if ((rc = each(r0, B))) return rc;
     }
     return CS_OK;
@@ -347,7 +379,8 @@ cs_status cs_classifier_load(cs_ctx *ctx, int dim, const float *params, int64_t 
     cs_status rc;
     if ((rc = dmalloc_n(ctx, &C->w, size_t(n))) || (rc = dmalloc_n(ctx, &C->g, size_t(n))) ||
         (rc = dmalloc_n(ctx, &C->m, size_t(n))) || (rc = dmalloc_n(ctx, &C->v, size_t(n))) ||
-        (rc = dmalloc_n(ctx, &C->loss, 1))) {
+        (rc = dmalloc_n(ctx, &C->loss, 1)) ||
+        (rc = dmalloc_n(ctx, &C->packed, size_t(cls_packed_bytes(dim))))) {
         release(ctx, C);
         return rc;
     }
@@ -540,6 +573,7 @@ cs_status cs_classifier_train(cs_ctx *ctx, int32_t mesh_id, const double *xp,
         ctx->launches += backward(ctx, *C, B, labels, C->idx, losses + s, nullptr);
         C->t += 1;
         ctx->launches += launch_adam(C->w, C->g, C->m, C->v, C->n, lr, C->t, ctx->sm_count, nullptr);
+        C->packed_dirty = true;
     }
     if (out == CS_OK) {
         cudaError_t e = cudaDeviceSynchronize();

@@ -52,4 +52,16 @@ void launch_cls_start(const DevMesh &m, int64_t n, const double *xp, const float
                       const int32_t *fallback, int64_t row0, int32_t *start, int32_t *cls,
                       int sm_count, cudaStream_t st);
 
+// module 1 fused on the tensor cores (classifier_tc.cu): conv1 and conv2
+// weights packed for the kernel (bytes, and the packing from the FP32
+// parameters), then per particle the window inputs, both convolutions and the
+// pooling into cat[b][0, 32 (W/2)^dim) (row stride ldc) and the offset into
+// off[b][dim]. pool_f: the mesh's pooled centroids as float hi + lo.
+int64_t cls_packed_bytes(int dim);
+void launch_cls_pack(int dim, const float *w, int64_t off_w1, int64_t off_b1, int64_t off_w2,
+                     int64_t off_b2, uint8_t *packed, cudaStream_t st);
+void launch_cls_conv_tc(const DevMesh &m, const float *pool_f, int64_t B, const double *xp,
+                        const uint8_t *packed, float *cat, int64_t ldc, float *off, int *err,
+                        int sm_count, cudaStream_t st);
+
 }  // namespace cs

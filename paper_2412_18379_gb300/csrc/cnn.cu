@@ -818,6 +818,7 @@ __global__ void __launch_bounds__(256) head_kernel(const float *__restrict__ y,
 // accuracy check; process-wide.
 static bool g_gemm_bf16 = true;
 void set_gemm_bf16(bool on) { g_gemm_bf16 = on; }
+bool gemm_bf16() { return g_gemm_bf16; }
 
 int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, int64_t M,
                 int64_t N, int64_t K, bool transA, bool transB, bool accumulate,

@@ -60,6 +60,7 @@ int launch_tc_gemm(const float *A, const float *Bm, float *C, const float *bias,
                    int64_t N, int64_t K, bool transA, bool transB, int *err, int sm_count,
                    float *work, int64_t work_floats, cudaStream_t st);
 void set_gemm_bf16(bool on);
+bool gemm_bf16();   // the current operand precision (true: BF16)
 int launch_relu(const float *z, float *y, int64_t n, int sm_count, cudaStream_t st);
 // ReLU(conv(x) + bias) of one valid 3^D convolution of 32 output channels,
 // without an im2col copy (inference). x: [B][C][Si^D] (chfirst) or

@@ -65,6 +65,7 @@ struct DevMesh {
     const int32_t *node_elem; // [n_v] internal id of the plain-SNS start
     const int32_t *seed;      // [n_asg] internal id of the host of each cell centre, or -1
     const double *pool;       // [n_asg][dim] mean element centroid per ASG cell, NaN if none
+    const float *pool_f;      // [n_asg][dim][2] the same as float hi + lo (NaN hi if none)
     const int32_t *bstart;    // [n_bucket + 1] offsets into bitems
     const int32_t *bitems;    // internal ids listed per bucket cell
     double lo[3], hi[3];
@@ -192,6 +193,7 @@ struct HostMesh {
     std::vector<int32_t> conn;       // internal order
     std::vector<double> centroid;    // internal order
     std::vector<double> pool;        // [n_asg][dim] mean centroid per ASG cell, NaN if none
+    std::vector<float> pool_f;       // [n_asg][dim][2] the same as float hi, lo
     std::vector<int32_t> node_elem;  // user ids
     std::vector<int32_t> bstart, bitems;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};

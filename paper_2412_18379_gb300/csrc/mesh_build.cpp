@@ -306,6 +306,14 @@ cs_status build_host_mesh(int dim, int64_t n_v, const double *xyz, int64_t n_e,
         for (int64_t c = 0; c < n_asg; ++c)
             for (int k = 0; k < dim; ++k)
                 H.pool[c * dim + k] = cnt[c] > 0 ? H.pool[c * dim + k] / double(cnt[c]) : NAN;
+        // the same values as float hi + lo pairs (lo = the remainder rounded)
+        H.pool_f.resize(H.pool.size() * 2);
+        for (size_t i = 0; i < H.pool.size(); ++i) {
+            const float hi = static_cast<float>(H.pool[i]);
+            H.pool_f[2 * i] = hi;
+            H.pool_f[2 * i + 1] = std::isnan(H.pool[i]) ? 0.f
+                                                        : static_cast<float>(H.pool[i] - double(hi));
+        }
     }
     std::sort(keys.begin(), keys.end());
     H.order.resize(size_t(n_e));
