@@ -176,6 +176,17 @@ def particle_set(case, kind):
     return case.x, case.u, None
 
 
+def shard_particles(px, pu, pstart, node_starts, rank, world):
+    """This rank's contiguous slice [lo, hi) of one particle batch
+    (shard_range); particles that are mesh nodes get their node's element as
+    an explicit start. Returns (x, u, start, (lo, hi))."""
+    from paper_2412_18379_gb300.shard import shard_range
+    lo, hi = shard_range(px.shape[0], rank, world)
+    st = pstart if pstart is not None else node_starts
+    return (np.ascontiguousarray(px[lo:hi]), np.ascontiguousarray(pu[lo:hi]),
+            np.ascontiguousarray(st[lo:hi], dtype=np.int32), (lo, hi))
+
+
 def cpu_oracle_rate(case, sample_n, seed=0, particles="nodes", threads=1, om=None):
     """The oracle as it stands (plain C through ctypes; its particle loops on
     `threads` OpenMP threads) on a bounded sample of the workload's particles:
@@ -471,7 +482,8 @@ class Runner:
     otherwise sit between the kernels of every timed step. An untimed pass
     with start_out then gives the error statistics of Sec. 3.1."""
 
-    def __init__(self, ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks):
+    def __init__(self, ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks,
+                 units_total=None):
         import torch
         self.torch = torch
         self.ctx, self.mesh, self.case, self.field = ctx, mesh, case, field
@@ -486,6 +498,9 @@ class Runner:
                         status=torch.empty(n, dtype=torch.uint8, device=dev))
         self.stream = torch.cuda.current_stream(dev)
         self.world = dist.get_world_size() if dist is not None else 1
+        # particles the whole job locates per step: every rank's batch
+        # (replicas), or the one batch the ranks share (shards)
+        self.units = units_total if units_total is not None else self.world * self.n
 
     def step(self, mode, dt, out=None, start_out=False):
         return self.ctx.track(self.mesh, self.x, self.u, dt, start=self.start, mode=mode,
@@ -549,7 +564,7 @@ class Runner:
         err = ctx.track_error(self.mesh, self.x, self.u, dt, o["host"], start=o["start"], dhat=dhat)
         mps = total / steps
         n = self.n
-        r = dict(particles_per_s=self.world * n / (mps * 1e-3), ms_per_step=mps,
+        r = dict(particles_per_s=self.units / (mps * 1e-3), ms_per_step=mps,
                  mean_path_len=st["sum"] / n, max_path_len=st["max"],
                  status_counts=[st["found"], st["outside"], st["fallback"], st["invalid"]],
                  stage_ms_per_step={k: v[1] / max(1, v[0]) for k, v in prof.items() if v[0]},
@@ -654,6 +669,9 @@ def main():
                     help="8-mode fields of training pairs (0: an untrained predictor)")
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--train-batch", type=int, default=4096)
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split one particle batch over the ranks "
+                         "(shard_range; strong scaling) instead of one batch per rank")
     ap.add_argument("--cls-fields", type=int, default=2,
                     help="random fields whose plain-SNS pairs train the classifier")
     ap.add_argument("--cls-steps", type=int, default=300)
@@ -713,13 +731,19 @@ def main():
                                    args.train_batch, seed=rank)
 
     px, pu, pstart = particle_set(case, args.particles)
+    n_total = px.shape[0]
+    shard = None
+    if args.shard:
+        px, pu, pstart, shard = shard_particles(px, pu, pstart, mesh.node_start_elements(),
+                                                rank, world)
     field = None
     if pstart is not None and "cnn" in modes:
         # particles that are not the mesh nodes: the predictor reads the
         # resident field of the nodal velocity
         field = ctx.upload_field(mesh, case.u)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    run = Runner(ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks)
+    run = Runner(ctx, mesh, case, px, pu, pstart, field, flush, dev, dist, max_over_ranks,
+                 units_total=n_total if args.shard else None)
 
     results = {}
     main_prof = main_launches = None
@@ -781,7 +805,7 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist is not None:
         e2e_s = max_over_ranks(e2e_s, device=dev)
-    e2e = {"value": world * n / e2e_s, "unit": "particles/s",
+    e2e = {"value": (n_total if args.shard else world * n) / e2e_s, "unit": "particles/s",
            "h2d_bytes_per_step": n * dim * 16 + (0 if sh is None else n * 4),
            "d2h_bytes_per_step": n * 9,
            "entry_point": "cs_track_host",
@@ -789,7 +813,7 @@ def main():
                        "staging buffer and the results back (cudaMemcpyAsync), then synchronises"}
 
     classifier = None
-    if not args.no_classifier and args.particles == "nodes":
+    if not args.no_classifier and args.particles == "nodes" and not args.shard:
         classifier = classifier_bench(ctx, mesh, case, flush, args.cls_fields, args.cls_steps,
                                       args.cls_batch, args.cls_timed, seed=rank,
                                       bf16_peak=bf16_peak)
@@ -797,7 +821,7 @@ def main():
         torch.cuda.empty_cache()
 
     sweep_rows = None
-    if not args.no_sweep and args.particles == "nodes" and args.workload == "tg2d":
+    if not args.no_sweep and args.particles == "nodes" and args.workload == "tg2d" and not args.shard:
         sweep_rows = sweep(ctx, cs, args, rank, dev, dist, max_over_ranks, flush, case, mesh)
 
     serving = None
@@ -830,22 +854,27 @@ def main():
             "metric": "particles located/s", "value": main["particles_per_s"],
             "unit": "particles/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong" if args.shard else "weak",
+            "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": wl["desc"] + ", CFL %g" % args.cfl,
                        "mode": {"cnn": "CNN-SNS (Algorithm 2)", "sns": "plain SNS",
                                 "asg": "ASG-direct"}[args.mode],
                        "particles": ("one per mesh node, from the node's element"
-                                     if pstart is None else
+                                     if args.particles == "nodes" else
                                      "one per (element, node) pair, from the element"),
-                       "n_particles": n, "n_elements": case.n_elements,
+                       "n_particles": n_total, "n_elements": case.n_elements,
                        "asg_grid": info["asg_grid"],
                        "predictor_grid": {"stride": info["pred_stride"],
                                           "cells": info["pred_grid"]},
                        "l2": "flushed by a 256 MB write before every timed step",
-                       "parallelism": ("%d replicas: every rank locates its own batch of %d particles "
-                                        "against its own copy of the mesh, no collective"
-                                        % (world, n)) if world > 1 else "1 GPU",
+                       "parallelism": (("%d shards of one batch of %d particles (shard_range: "
+                                         "contiguous slices, this rank [%d, %d)), each rank with "
+                                         "its own copy of the mesh, no collective"
+                                         % (world, n_total, shard[0], shard[1])) if args.shard else
+                                        ("%d replicas: every rank locates its own batch of %d "
+                                         "particles against its own copy of the mesh, no "
+                                         "collective" % (world, n))) if world > 1 else "1 GPU",
                        "arithmetic": "walk decisions FP64 (certified FP32 filter); predictor "
                                      "BF16 x BF16 -> FP32 on tcgen05"},
             "mean_path_len": main["mean_path_len"], "max_path_len": main["max_path_len"],

@@ -83,3 +83,21 @@ def test_opt_rates_follow_the_paper_definition():
     assert abs(o["opt_time"] - 0.469) < 5e-4
     assert abs(o["opt_err"] - 0.528) < 5e-4
     assert abs(o["speedup"] - 137.233 / 72.814) < 1e-12
+
+
+def test_shards_cover_the_batch_with_explicit_node_starts():
+    """bench.py --shard: the ranks' slices of one batch cover it exactly once,
+    in order, and node particles carry their node's element as the start."""
+    import bench
+    rng = np.random.default_rng(3)
+    x = rng.random((1001, 2))
+    u = rng.random((1001, 2))
+    node = rng.integers(0, 5000, size=1001).astype(np.int32)
+    parts = [bench.shard_particles(x, u, None, node, r, 4) for r in range(4)]
+    assert [p[3] for p in parts] == [(0, 251), (251, 501), (501, 751), (751, 1001)]
+    assert np.array_equal(np.concatenate([p[0] for p in parts]), x)
+    assert np.array_equal(np.concatenate([p[1] for p in parts]), u)
+    assert np.array_equal(np.concatenate([p[2] for p in parts]), node)
+    start = rng.integers(0, 5000, size=1001).astype(np.int32)
+    p = bench.shard_particles(x, u, start, node, 1, 4)
+    assert np.array_equal(p[2], start[251:501]) and p[2].dtype == np.int32

@@ -309,3 +309,34 @@ def test_host_entry_point_matches_the_device_one(ctx, mode):
     for k in ("host", "path_len", "status"):
         assert np.array_equal(got[k], want[k].cpu().numpy()), (mode, "pairs", k)
     mesh.release()
+
+
+@pytest.mark.parametrize("mode", ["sns", "asg", "cnn"])
+def test_shards_of_one_batch_concatenate_to_the_whole(ctx, mode):
+    """The multi-GPU split of one batch (bench.py --shard): each of 3 shards
+    (shard_range slices, the node particles with their node's element as an
+    explicit start, CNN-SNS predicting from a resident field) is located by a
+    call of its own, one after the other on this GPU; concatenated, the
+    results equal the whole batch's bit for bit. Every shard runs alone: no
+    call waits on another."""
+    import torch
+    from workloads.weights import init_weights
+    from paper_2412_18379_gb300.shard import shard_range
+    c = make_case("tg2d", n_side=301, cfl=8)
+    ctx.load_predictor(2, init_weights(2, 31))
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    mesh.set_predictor_grid(3)
+    f = ctx.upload_field(mesh, c.u)
+    starts = mesh.node_start_elements()
+    whole = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, start=_dev(starts), mode=mode, field=f,
+                      start_out=True)
+    torch.cuda.synchronize()
+    parts = []
+    for r in range(3):
+        lo, hi = shard_range(c.n_particles, r, 3)
+        o = ctx.track(mesh, _dev(c.x[lo:hi]), _dev(c.u[lo:hi]), c.dt, start=_dev(starts[lo:hi]),
+                      mode=mode, field=f, start_out=True)
+        torch.cuda.synchronize()
+        parts.append({k: v.cpu().numpy() for k, v in o.items()})
+    for k in ("host", "path_len", "status", "start"):
+        assert np.array_equal(np.concatenate([p[k] for p in parts]), whole[k].cpu().numpy()), k
