@@ -29,8 +29,9 @@
 // element centroid, given as float hi + lo parts, so the difference is taken
 // in FP32 to about one unit in the last place of the FP64 value; a cell
 // outside the grid or without a centroid holds its centre, (e - W/2) - offset
-// in cell units. x_p's cell and its offset from the cell centre are computed
-// in FP64 (the same formulas as the labels and the start rule).
+// in cell units. x_p's cell is the FP64 formula's (certified in FP32, with the
+// FP64 formula as arbiter: the same cell as the labels and the start rule);
+// its offset from the cell centre is taken in FP32.
 //
 // Warps. Warps 0-3 compute the inputs, run both epilogues and the pooling
 // (warp w reads TMEM lanes 32 w .. 32 w + 31); warp 4 issues the MMAs. A CTA
@@ -117,9 +118,31 @@ __device__ __forceinline__ bool epi_or(bool flag) {
     return r != 0;
 }
 
+// x_p's ASG cell on axis k and its offset from the cell centre (cell units).
+// The cell is the FP64 formula's (floor((x - lo) / s), clamped): taken in
+// FP32 from x's hi + lo parts where the rounding bound cannot move the
+// quotient across an integer, else by the FP64 formula itself (the
+// certification of the walk's cell indices). The offset is the FP32
+// quotient minus (cell + 1/2), within ~1e-7 of the quotient of the FP64 one.
+__device__ __forceinline__ void cell_offset(const DevMesh &m, int k, double x, float xh, float xl,
+                                            int &cell, float &off) {
+    const float df = (xh - m.lo_h[k]) + (xl - m.lo_l[k]);
+    const float ed = delta_bound(df, xh, m.lo_h[k]);
+    const float q = df * m.inv_sa[k];
+    const float bnd = fmaf(2.0f * ed, m.inv_sa[k], fmaf(k8U, fabsf(q), kTiny));
+    const int a = __float2int_rd(q - bnd), b = __float2int_rd(q + bnd);
+    int64_t i;
+    if (a == b && fabsf(q) < 4.0e6f)
+        i = a < 0 ? 0 : (a > m.ga[k] - 1 ? m.ga[k] - 1 : a);
+    else
+        i = cell_axis64(x, m.lo[k], m.sa[k], m.ga[k]);
+    cell = int(i);
+    off = q - (float(i) + 0.5f);
+}
+
 // The inputs of particle b into the operand rows (epilogue warps): thread
-// tid < D first computes axis tid's cell and offset in FP64 and the hi/lo
-// split of x_p; then every window cell is one 16-byte row.
+// tid < D first computes axis tid's cell, offset and the hi/lo split of x_p;
+// then every window cell is one 16-byte row.
 template <int D>
 __device__ __forceinline__ void cls_inputs(const DevMesh &m, const float *__restrict__ pool_f,
                                            const double *__restrict__ xp, int64_t b,
@@ -128,14 +151,16 @@ __device__ __forceinline__ void cls_inputs(const DevMesh &m, const float *__rest
     using G = ClsGeo<D>;
     if (tid < D) {
         const double x = xp[b * D + tid];
-        const int64_t c0 = cell_axis64(x, m.lo[tid], m.sa[tid], m.ga[tid]);
-        const double o = __dsub_rn(__ddiv_rn(__dsub_rn(x, m.lo[tid]), m.sa[tid]), double(c0) + 0.5);
-        sc0[tid] = int(c0);
-        soff[tid] = float(o);
-        off_out[b * D + tid] = float(o);
         const float h = __double2float_rn(x);
+        const float l = __double2float_rn(__dsub_rn(x, double(h)));
+        int c0;
+        float o;
+        cell_offset(m, tid, x, h, l, c0, o);
+        sc0[tid] = c0;
+        soff[tid] = o;
+        off_out[b * D + tid] = o;
         sxh[tid] = h;
-        sxl[tid] = __double2float_rn(__dsub_rn(x, double(h)));
+        sxl[tid] = l;
     }
     epi_sync();
     for (int e = tid; e < G::P; e += kEpiC * 32) {

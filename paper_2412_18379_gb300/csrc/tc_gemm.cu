@@ -86,6 +86,10 @@ template <int ROWS>
 __device__ __forceinline__ void stage_operand(uint8_t *dst, const float *__restrict__ P,
                                               int64_t s_r, int64_t s_k, int64_t r0, int64_t nr,
                                               int64_t k0, int64_t kend, int kn, bool vec, int tid) {
+    // Every path loads a batch of elements per thread before it converts and
+    // stores any of them, so a chunk costs a few load latencies instead of
+    // one per element.
+    constexpr int kB4 = 8, kB1 = 16;
     __nv_bfloat16 *d = reinterpret_cast<__nv_bfloat16 *>(dst);
     const int kv = int(min(kend - k0, int64_t(kn)));            // valid K of the chunk
     const int rv = int(max(min(nr - r0, int64_t(ROWS)), int64_t(0)));   // valid rows
@@ -93,24 +97,47 @@ __device__ __forceinline__ void stage_operand(uint8_t *dst, const float *__restr
         const float *base = P + r0 * s_r + k0;
         if (vec) {
             // groups of 4 consecutive k; kv is a multiple of 4 (K % 4 == 0)
-            const int g4 = kn / 4;
-            for (int e = tid; e < ROWS * g4; e += kThreadsG) {
-                const int r = e / g4, k = 4 * (e % g4);
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < rv && k < kv)
-                    v = __ldg(reinterpret_cast<const float4 *>(base + int64_t(r) * s_r + k));
-                const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-                const __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
-                uint2 w;
-                w.x = *reinterpret_cast<const uint32_t *>(&lo);
-                w.y = *reinterpret_cast<const uint32_t *>(&hi);
-                *reinterpret_cast<uint2 *>(d + ((k >> 3) * ROWS + r) * 8 + (k & 7)) = w;
+            const int g4 = kn / 4, total = ROWS * g4;
+            for (int e0 = tid; e0 < total; e0 += kThreadsG * kB4) {
+                float4 v[kB4];
+                #pragma unroll
+                for (int u = 0; u < kB4; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    const int r = e / g4, k = 4 * (e % g4);
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < total && r < rv && k < kv)
+                        v[u] = __ldg(reinterpret_cast<const float4 *>(base + int64_t(r) * s_r + k));
+                }
+                #pragma unroll
+                for (int u = 0; u < kB4; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    if (e >= total) break;
+                    const int r = e / g4, k = 4 * (e % g4);
+                    const __nv_bfloat162 lo = __floats2bfloat162_rn(v[u].x, v[u].y);
+                    const __nv_bfloat162 hi = __floats2bfloat162_rn(v[u].z, v[u].w);
+                    uint2 w;
+                    w.x = *reinterpret_cast<const uint32_t *>(&lo);
+                    w.y = *reinterpret_cast<const uint32_t *>(&hi);
+                    *reinterpret_cast<uint2 *>(d + ((k >> 3) * ROWS + r) * 8 + (k & 7)) = w;
+                }
             }
         } else {
-            for (int e = tid; e < ROWS * kn; e += kThreadsG) {
-                const int r = e / kn, k = e % kn;
-                const float v = (r < rv && k < kv) ? __ldg(base + int64_t(r) * s_r + k) : 0.f;
-                d[((k >> 3) * ROWS + r) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+            const int total = ROWS * kn;
+            for (int e0 = tid; e0 < total; e0 += kThreadsG * kB1) {
+                float v[kB1];
+                #pragma unroll
+                for (int u = 0; u < kB1; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    const int r = e / kn, k = e % kn;
+                    v[u] = (e < total && r < rv && k < kv) ? __ldg(base + int64_t(r) * s_r + k) : 0.f;
+                }
+                #pragma unroll
+                for (int u = 0; u < kB1; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    if (e >= total) break;
+                    const int r = e / kn, k = e % kn;
+                    d[((k >> 3) * ROWS + r) * 8 + (k & 7)] = __float2bfloat16_rn(v[u]);
+                }
             }
         }
     } else {
@@ -118,23 +145,48 @@ __device__ __forceinline__ void stage_operand(uint8_t *dst, const float *__restr
         if (vec && s_r == 1) {
             // groups of 4 consecutive rows; rv is a multiple of 4 or the tail
             constexpr int g4 = ROWS / 4;
-            for (int e = tid; e < g4 * kn; e += kThreadsG) {
-                const int r = 4 * (e % g4), k = e / g4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r < rv && k < kv)
-                    v = __ldg(reinterpret_cast<const float4 *>(base + int64_t(k) * s_k + r));
-                const int o = ((k >> 3) * ROWS + r) * 8 + (k & 7);
-                d[o] = __float2bfloat16_rn(v.x);
-                d[o + 8] = __float2bfloat16_rn(v.y);
-                d[o + 16] = __float2bfloat16_rn(v.z);
-                d[o + 24] = __float2bfloat16_rn(v.w);
+            const int total = g4 * kn;
+            for (int e0 = tid; e0 < total; e0 += kThreadsG * kB4) {
+                float4 v[kB4];
+                #pragma unroll
+                for (int u = 0; u < kB4; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    const int r = 4 * (e % g4), k = e / g4;
+                    v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < total && r < rv && k < kv)
+                        v[u] = __ldg(reinterpret_cast<const float4 *>(base + int64_t(k) * s_k + r));
+                }
+                #pragma unroll
+                for (int u = 0; u < kB4; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    if (e >= total) break;
+                    const int r = 4 * (e % g4), k = e / g4;
+                    const int o = ((k >> 3) * ROWS + r) * 8 + (k & 7);
+                    d[o] = __float2bfloat16_rn(v[u].x);
+                    d[o + 8] = __float2bfloat16_rn(v[u].y);
+                    d[o + 16] = __float2bfloat16_rn(v[u].z);
+                    d[o + 24] = __float2bfloat16_rn(v[u].w);
+                }
             }
         } else {
-            for (int e = tid; e < ROWS * kn; e += kThreadsG) {
-                const int r = e % ROWS, k = e / ROWS;
-                const float v =
-                    (r < rv && k < kv) ? __ldg(base + int64_t(r) * s_r + int64_t(k) * s_k) : 0.f;
-                d[((k >> 3) * ROWS + r) * 8 + (k & 7)] = __float2bfloat16_rn(v);
+            const int total = ROWS * kn;
+            for (int e0 = tid; e0 < total; e0 += kThreadsG * kB1) {
+                float v[kB1];
+                #pragma unroll
+                for (int u = 0; u < kB1; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    const int r = e % ROWS, k = e / ROWS;
+                    v[u] = (e < total && r < rv && k < kv)
+                               ? __ldg(base + int64_t(r) * s_r + int64_t(k) * s_k)
+                               : 0.f;
+                }
+                #pragma unroll
+                for (int u = 0; u < kB1; ++u) {
+                    const int e = e0 + u * kThreadsG;
+                    if (e >= total) break;
+                    const int r = e % ROWS, k = e / ROWS;
+                    d[((k >> 3) * ROWS + r) * 8 + (k & 7)] = __float2bfloat16_rn(v[u]);
+                }
             }
         }
     }
