@@ -344,11 +344,14 @@ def classifier_bench(ctx, mesh, case, flush, n_fields, steps, batch, timed, seed
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(timed)]
     l0 = ctx.launches
+    marked = nvtx_push("timed_classifier")     # selects these steps for a profiler
     for i in range(timed):
         flush.fill_(i & 0xff)
         ev[i][0].record(stream)
         ctx.track_classifier(mesh, x, u, case.dt, out=out)
         ev[i][1].record(stream)
+    if marked:
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = (ctx.launches - l0) // max(1, timed)
     ms = sum(a.elapsed_time(b) for a, b in ev) / timed

@@ -192,7 +192,14 @@ cs_status cs_track(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n, co
                    int32_t *start_out, void *stream);
 
 /* cs_track with HOST pointers: copies inputs to the device, runs, copies the
- * results back and synchronises. Same arguments and errors. */
+ * results back and synchronises. Same arguments, results and errors.
+ * The particle range is processed in up to 4 chunks on three streams of the
+ * context (copy in, compute, copy out), so that the copies of one chunk
+ * overlap the walk of another; CNN-SNS without a field first copies the whole
+ * nodal velocity its predictor reads. Page-locked host buffers overlap best;
+ * pageable ones give the same results. The call orders itself after work
+ * already queued on the legacy default stream; calls on one context must not
+ * overlap (they share the streams and the device staging buffer). */
 cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
                         const double *x, const double *u, double dt, const int32_t *start,
                         int mode, int32_t *host_out, int32_t *path_len_out,

@@ -72,6 +72,18 @@ cs::Mesh *find_mesh(cs_ctx *ctx, int32_t id) {
     return it == ctx->meshes.end() ? nullptr : it->second;
 }
 
+// the three non-blocking streams and the events of cs_track_host (created once)
+cs_status ensure_host_streams(cs_ctx *ctx) {
+    if (ctx->hstream[0]) return CS_OK;
+    for (auto &st : ctx->hstream)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, CS_ECUDA, "cs_track_host: stream creation failed");
+    for (auto &ev : ctx->hevent)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, CS_ECUDA, "cs_track_host: event creation failed");
+    return CS_OK;
+}
+
 cs_status ensure_scratch(cs_ctx *ctx) {
     cs::Scratch &s = ctx->scratch;
     if (!s.counters) {
@@ -164,6 +176,10 @@ void cs_destroy(cs_ctx *ctx) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : ctx->prof.pool) cudaEventDestroy(e);
+    for (cudaStream_t st : ctx->hstream)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ctx->hevent)
+        if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -519,11 +535,36 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
     if (!ctx) return CS_EINVAL;
     cs::Mesh *m = find_mesh(ctx, mesh_id);
     if (!m) return fail(ctx, CS_ENOMESH, "cs_track_host: unknown mesh id");
-    if (n < 0) return fail(ctx, CS_EINVAL, "cs_track_host: n < 0");
+    if (n < 0 || n >= (int64_t(1) << 31) - 1)
+        return fail(ctx, CS_EINVAL, "cs_track_host: n is outside [0, 2^31 - 2]");
+    if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS)
+        return fail(ctx, CS_EINVAL, "cs_track_host: bad mode");
+    cs::Field *f = nullptr;
+    if (mode == CS_CNN_SNS) {
+        if (!ctx->pred[m->d.dim - 2].loaded)
+            return fail(ctx, CS_ENOPRED, "cs_track_host: no predictor loaded");
+        if (field_id != CS_NO_FIELD) {
+            auto it = ctx->fields.find(field_id);
+            if (it == ctx->fields.end() || it->second->mesh_id != mesh_id)
+                return fail(ctx, CS_EINVAL, "cs_track_host: field id is not a field of this mesh");
+            f = it->second;
+        }
+    }
     if (n == 0) return CS_OK;
     if (!x || !u || !host_out || !path_len_out || !status_out)
         return fail(ctx, CS_EINVAL, "cs_track_host: null pointer");
+    if (!start && n != m->d.n_v)
+        return fail(ctx, CS_EINVAL, "cs_track_host: start == NULL needs n == n_vertices");
+    // CNN-SNS without a field predicts from the call's own nodal velocity:
+    // all of u has to be on the device before the predictor runs
+    const bool whole_u = mode == CS_CNN_SNS && !f;
+    if (whole_u && start)
+        return fail(ctx, CS_EINVAL,
+                    "cs_track_host: CNN-SNS needs a field id (cs_field_upload) unless the "
+                    "particles are the mesh nodes");
     CS_CUDA(ctx, cudaSetDevice(ctx->device));
+    cs_status rc = ensure_scratch(ctx);
+    if (rc) return rc;
     const int dim = m->d.dim;
     const size_t in_b = size_t(n) * dim * sizeof(double);
     const size_t total = 2 * in_b + size_t(n) * (4 + 4 + 4 + 4 + 1) + 256;
@@ -532,37 +573,87 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
         cs::dfree(ctx, S.stage);
         S.stage = nullptr;
         S.stage_cap = 0;
-        cs_status rc = cs::dmalloc_n(ctx, &S.stage, total);
+        rc = cs::dmalloc_n(ctx, &S.stage, total);
         if (rc) return rc;
         S.stage_cap = total;
     }
+    // node particles walk from their node's element, given explicitly per chunk
+    if (!start && !m->node_start_user) {
+        rc = dev_copy(ctx, m, m->node_elem_user.data(), m->node_elem_user.size(),
+                      &m->node_start_user);
+        if (rc) return rc;
+    }
+    if ((rc = ensure_host_streams(ctx))) return rc;
     char *buf = S.stage;
     double *dx = reinterpret_cast<double *>(buf);
     double *du = reinterpret_cast<double *>(buf + in_b);
     int32_t *ds = reinterpret_cast<int32_t *>(buf + 2 * in_b);
     int32_t *dh = ds + n, *dp = dh + n, *dso = dp + n;
     uint8_t *dst = reinterpret_cast<uint8_t *>(dso + n);
-    cudaStream_t st = nullptr;
-    cs_status rc = CS_OK;
-    cudaError_t e = cudaMemcpyAsync(dx, x, in_b, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(du, u, in_b, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && start)
-        e = cudaMemcpyAsync(ds, start, size_t(n) * 4, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host: copy in");
-    rc = cs_track(ctx, mesh_id, field_id, n, dx, du, dt, start ? ds : nullptr, mode, dh, dp, dst,
-                  start_out ? dso : nullptr, st);
-    if (rc == CS_OK) {
-        e = cudaMemcpyAsync(host_out, dh, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(path_len_out, dp, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(status_out, dst, size_t(n), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && start_out)
-            e = cudaMemcpyAsync(start_out, dso, size_t(n) * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cs_track_host: copy out");
+    cudaStream_t s_in = ctx->hstream[0], s_cmp = ctx->hstream[1], s_out = ctx->hstream[2];
+    cudaEvent_t *ev = ctx->hevent;
+    // Chunks of the particle range, pipelined over three streams: the copies
+    // in of chunk i + 1 and the copies out of chunk i - 1 overlap the walk of
+    // chunk i (the two copy directions run at once).
+    const int K = int(std::min<int64_t>(cs::kHostChunks, std::max<int64_t>(1, n / (int64_t(1) << 18))));
+    cudaError_t e = cudaEventRecord(ev[0], nullptr);   // after the caller's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev[0], 0);
+    if (e == cudaSuccess && whole_u) {
+        e = cudaMemcpyAsync(du, u, in_b, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev[1], 0);
     }
-    return rc;
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+        const int64_t lo = n * i / K, hi = n * (i + 1) / K, c = hi - lo;
+        e = cudaMemcpyAsync(dx + lo * dim, x + lo * dim, size_t(c) * dim * 8, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess && !whole_u)
+            e = cudaMemcpyAsync(du + lo * dim, u + lo * dim, size_t(c) * dim * 8, cudaMemcpyHostToDevice,
+                                s_in);
+        if (e == cudaSuccess && start)
+            e = cudaMemcpyAsync(ds + lo, start + lo, size_t(c) * 4, cudaMemcpyHostToDevice, s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + i], s_in);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host: copy in");
+    const float *dhat = nullptr;
+    if (mode == CS_CNN_SNS) {
+        const float *grid = nullptr;
+        if (f && (rc = cs::field_grid(ctx, m, f, s_cmp, &grid))) return rc;
+        if ((rc = cs::cnn_prepare(ctx, m, grid, f ? nullptr : du, dt, s_cmp, &dhat))) return rc;
+    }
+    for (int i = 0; i < K && rc == CS_OK; ++i) {
+        const int64_t lo = n * i / K, hi = n * (i + 1) / K, c = hi - lo;
+        e = cudaStreamWaitEvent(s_cmp, ev[2 + i], 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(ctx, e, "cs_track_host: event wait");
+            break;
+        }
+        const int32_t *st0 = start ? ds + lo : m->node_start_user + lo;
+        rc = cs::cs_track_impl(ctx, m, c, dx + lo * dim, du + lo * dim, dt, st0, mode, dhat,
+                               dh + lo, dp + lo, dst + lo, start_out ? dso + lo : nullptr, s_cmp);
+        if (rc == CS_OK) {
+            e = cudaEventRecord(ev[2 + K + i], s_cmp);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev[2 + K + i], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(host_out + lo, dh + lo, size_t(c) * 4, cudaMemcpyDeviceToHost, s_out);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(path_len_out + lo, dp + lo, size_t(c) * 4, cudaMemcpyDeviceToHost,
+                                    s_out);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(status_out + lo, dst + lo, size_t(c), cudaMemcpyDeviceToHost, s_out);
+            if (e == cudaSuccess && start_out)
+                e = cudaMemcpyAsync(start_out + lo, dso + lo, size_t(c) * 4, cudaMemcpyDeviceToHost,
+                                    s_out);
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cs_track_host: copy out");
+        }
+    }
+    // every stream drained before return (also after a failed launch)
+    const cudaError_t e1 = cudaStreamSynchronize(s_in), e2 = cudaStreamSynchronize(s_cmp),
+                      e3 = cudaStreamSynchronize(s_out);
+    if (rc) return rc;
+    e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host");
+    return CS_OK;
 }
 
 cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len, const uint8_t *status,

@@ -117,6 +117,7 @@ struct Mesh {
     float *interp_w = nullptr;            //   host vertices and weights (static per mesh)
     bool grid_u_valid = false;
     int32_t pgrid_version = 0;            // bumped by every cs_predictor_grid
+    int32_t *node_start_user = nullptr;   // [n_v] plain starts as user ids (cs_track_host)
 };
 
 // A velocity field of a mesh (cs_field_upload): the nodal velocity, kept for
@@ -156,6 +157,9 @@ struct Predictor {
 
 // The classifier start predictor of one dimension (classifier.cpp).
 struct Classifier;
+
+// chunks of the particle range that cs_track_host pipelines (at most)
+constexpr int kHostChunks = 4;
 
 // Device scratch owned by a context.
 struct Scratch {
@@ -271,6 +275,10 @@ struct cs_ctx {
     int *dev_err = nullptr;  // device error flag of bounded waits
     int *hold_flag = nullptr;  // test hook: a device flag nothing sets (cs_debug_hold_predictor)
     cs::Server *server = nullptr;   // serving loop (serve.cpp), if started
+    // cs_track_host: copy-in, compute and copy-out streams, and its events
+    // ([0] caller, [1] velocity in, [2, 2 + chunks) chunk in, then chunk walked)
+    cudaStream_t hstream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t hevent[2 + 2 * cs::kHostChunks] = {};
     std::atomic<int64_t> launches{0};
 };
 
