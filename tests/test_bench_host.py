@@ -60,7 +60,12 @@ def test_committed_summaries_name_their_sources():
         assert len(vals["source_sha256_16"]) == 16, f
         for s in vals["sources"].split(","):
             assert os.path.exists(os.path.join(bench.ROOT, "paper_2412_18379_gb300", "csrc", s)), f
-        assert float(vals["dram_bytes_per_full_launch"]) > 0, f
+        # a summary of one kernel's launch gives its traffic; one of several
+        # launches of a general kernel (the training GEMM) gives each table
+        if "dram_bytes_per_full_launch" in vals:
+            assert float(vals["dram_bytes_per_full_launch"]) > 0, f
+        else:
+            assert open(os.path.join(prof, f)).read().count("dram__bytes_read.sum") >= 2, f
 
 
 @pytest.mark.parametrize("particles", ["nodes", "element-nodes"])
