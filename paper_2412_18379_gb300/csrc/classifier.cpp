@@ -260,27 +260,27 @@ int backward(cs_ctx *ctx, Classifier &C, int64_t B, const int32_t *labels, const
     n += 1;
     // logits and fusion
     n += gemm(ctx, C, C.gH, C.ru, g + S.w_off[5], nullptr, S.n_cls, kClsH2, B, true, false, st);
-    n += launch_colsum(C.gH, B, S.n_cls, g + S.b_off[5], st);
+    n += launch_colsum(C.gH, B, S.n_cls, g + S.b_off[5], st, C.splitk, C.splitk_n, sm);
     n += gemm(ctx, C, C.gH, w + S.w_off[5], C.gu, nullptr, B, kClsH2, S.n_cls, false, false, st);
     n += launch_relu_back(C.u, C.gu, B * kClsH2, sm, st);
     n += gemm(ctx, C, C.gu, C.cat, g + S.w_off[4], nullptr, kClsH2, S.ldc, B, true, false, st);
-    n += launch_colsum(C.gu, B, kClsH2, g + S.b_off[4], st);
+    n += launch_colsum(C.gu, B, kClsH2, g + S.b_off[4], st, C.splitk, C.splitk_n, sm);
     n += gemm(ctx, C, C.gu, w + S.w_off[4], C.gcat, nullptr, B, S.ldc, kClsH2, false, false, st);
     // module 2
     launch_cls_uncat_relu_back(C.gcat, S.ldc, S.n_pool, C.h2, B, kClsH1, C.gh2, sm, st);
     n += 1;
     n += gemm(ctx, C, C.gh2, C.r1, g + S.w_off[3], nullptr, kClsH1, kClsH1, B, true, false, st);
-    n += launch_colsum(C.gh2, B, kClsH1, g + S.b_off[3], st);
+    n += launch_colsum(C.gh2, B, kClsH1, g + S.b_off[3], st, C.splitk, C.splitk_n, sm);
     n += gemm(ctx, C, C.gh2, w + S.w_off[3], C.gh1, nullptr, B, kClsH1, kClsH1, false, false, st);
     n += launch_relu_back(C.h1, C.gh1, B * kClsH1, sm, st);
     n += gemm(ctx, C, C.gh1, C.off, g + S.w_off[2], nullptr, kClsH1, d, B, true, false, st);
-    n += launch_colsum(C.gh1, B, kClsH1, g + S.b_off[2], st);
+    n += launch_colsum(C.gh1, B, kClsH1, g + S.b_off[2], st, C.splitk, C.splitk_n, sm);
     // module 1: pooling, second and first convolution
     launch_cls_pool_back(d, C.gcat, S.ldc, C.z2, B, C.gz2, sm, st);
     n += 1;
     const int64_t K2 = int64_t(kClsCh) * S.taps;
     n += gemm(ctx, C, C.gz2, C.col2, g + S.w_off[1], nullptr, kClsCh, K2, BP, true, false, st);
-    n += launch_colsum(C.gz2, BP, kClsCh, g + S.b_off[1], st);
+    n += launch_colsum(C.gz2, BP, kClsCh, g + S.b_off[1], st, C.splitk, C.splitk_n, sm);
     float *dcol2 = C.col2, *dpad = C.a1, *gz1 = C.y1;
     n += gemm(ctx, C, C.gz2, w + S.w_off[1], dcol2, nullptr, BP, K2, kClsCh, false, false, st);
     n += launch_col2im(d, dcol2, B, kClsCh, S.W + 2, dpad, sm, st);
@@ -288,7 +288,7 @@ int backward(cs_ctx *ctx, Classifier &C, int64_t B, const int32_t *labels, const
     n += 1;
     n += gemm(ctx, C, gz1, C.col1, g + S.w_off[0], nullptr, kClsCh, int64_t(d) * S.taps, BP, true,
               false, st);
-    n += launch_colsum(gz1, BP, kClsCh, g + S.b_off[0], st);
+    n += launch_colsum(gz1, BP, kClsCh, g + S.b_off[0], st, C.splitk, C.splitk_n, sm);
     return n;
 }
 

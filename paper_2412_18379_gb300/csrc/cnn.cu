@@ -225,9 +225,10 @@ __global__ void __launch_bounds__(kThreads) tile_scatter_kernel(const DevMesh m,
 
 // im2col of one valid 3^D convolution: col[(b*Po + p)][i*taps + t] =
 // x(b, i, p + offset(t)); x is channels-first [B][C][Si^D] (first layer) or
-// channels-last [B][Si^D][C].
-template <int D>
-__global__ void __launch_bounds__(kThreads) im2col_kernel(const float *__restrict__ x, int64_t B,
+// channels-last [B][Si^D][C]. I: the index type (32-bit when the sizes allow:
+// its divisions are far cheaper than 64-bit ones).
+template <int D, class I>
+__global__ void __launch_bounds__(kThreads) im2col_kernel(const float *__restrict__ x, I B,
                                                           int C, int Si, bool chfirst,
                                                           float *__restrict__ col) {
     const int So = Si - 2;
@@ -237,13 +238,12 @@ __global__ void __launch_bounds__(kThreads) im2col_kernel(const float *__restric
         Po *= So;
         Pi *= Si;
     }
-    const int64_t K = int64_t(C) * taps;
-    const int64_t total = B * Po * K;
-    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
-         q += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t row = q / K;
+    const I K = I(C) * taps;
+    const I total = B * Po * K;
+    for (I q = I(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += I(gridDim.x) * blockDim.x) {
+        const I row = q / K;
         const int kk = int(q % K);
-        const int64_t b = row / Po;
+        const I b = row / Po;
         const int p = int(row % Po);
         const int i = kk / taps, t = kk % taps;
         int px = p % So, py = (p / So) % So, pz = D == 3 ? p / (So * So) : 0;
@@ -251,14 +251,14 @@ __global__ void __launch_bounds__(kThreads) im2col_kernel(const float *__restric
         py += (t / 3) % 3;
         pz += D == 3 ? t / 9 : 0;
         const int pin = D == 2 ? py * Si + px : (pz * Si + py) * Si + px;
-        col[q] = chfirst ? x[(b * C + i) * Pi + pin] : x[(b * Pi + pin) * C + i];
+        col[q] = chfirst ? x[(int64_t(b) * C + i) * Pi + pin] : x[(int64_t(b) * Pi + pin) * C + i];
     }
 }
 
 // col2im (gather form): dx[b][pin][i] = sum over taps t with a valid output
 // position p = pin - offset(t) of dcol[(b*Po + p)][i*taps + t]. Channels-last.
-template <int D>
-__global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restrict__ dcol, int64_t B,
+template <int D, class I>
+__global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restrict__ dcol, I B,
                                                           int C, int Si, float *__restrict__ dx) {
     const int So = Si - 2;
     const int taps = D == 2 ? 9 : 27;
@@ -267,13 +267,12 @@ __global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restric
         Po *= So;
         Pi *= Si;
     }
-    const int64_t total = B * Pi * C;
-    for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < total;
-         q += int64_t(gridDim.x) * blockDim.x) {
+    const I total = B * Pi * C;
+    for (I q = I(blockIdx.x) * blockDim.x + threadIdx.x; q < total; q += I(gridDim.x) * blockDim.x) {
         const int i = int(q % C);
-        const int64_t bp = q / C;
+        const I bp = q / C;
         const int pin = int(bp % Pi);
-        const int64_t b = bp / Pi;
+        const I b = bp / Pi;
         const int ix = pin % Si, iy = (pin / Si) % Si, iz = D == 3 ? pin / (Si * Si) : 0;
         float s = 0.f;
         for (int t = 0; t < taps; ++t) {
@@ -281,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) col2im_kernel(const float *__restric
             if (ox < 0 || oy < 0 || oz < 0 || ox >= So || oy >= So || (D == 3 && oz >= So))
                 continue;
             const int p = D == 2 ? oy * So + ox : (oz * So + oy) * So + ox;
-            s += dcol[(b * Po + p) * (int64_t(C) * taps) + int64_t(i) * taps + t];
+            s += dcol[(int64_t(b) * Po + p) * (int64_t(C) * taps) + int64_t(i) * taps + t];
         }
         dx[q] = s;
     }
@@ -364,6 +363,61 @@ __global__ void relu_back_kernel(const float *__restrict__ z, float *__restrict_
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += int64_t(gridDim.x) * blockDim.x)
         dy[i] = z[i] > 0.f ? dy[i] : 0.f;
+}
+
+// Column sums in two passes (bias gradients): block b sums its range of rows
+// for every column (consecutive threads on consecutive columns: coalesced)
+// into part[b][n]; then out[n] = sum over b, in order, of part[b][n]. The
+// order of every sum is fixed, so the result has the same bits on every run.
+__global__ void __launch_bounds__(kThreads) colsum_part_kernel(const float *__restrict__ x,
+                                                               int64_t M, int64_t N, int64_t rows,
+                                                               float *__restrict__ part) {
+    const int64_t m0 = int64_t(blockIdx.x) * rows, m1 = min(M, m0 + rows);
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+        float s = 0.f;
+        for (int64_t m = m0; m < m1; ++m) s += x[m * N + n];
+        part[int64_t(blockIdx.x) * N + n] = s;
+    }
+}
+// Thin products with a long K (weight gradients of narrow layers):
+// part[b][i N + j] = sum over k of block b's range of op(A)(i, k) B(k, j),
+// A stored [K][M] (op(A) = A^T), B [K][N], operands rounded to BF16 as in the
+// other training GEMMs; colsum_final_kernel then sums the blocks in order.
+__global__ void __launch_bounds__(kThreads) thin_part_kernel(const float *__restrict__ A,
+                                                             const float *__restrict__ B,
+                                                             int64_t M, int64_t N, int64_t K,
+                                                             int64_t rows, bool round_bf16,
+                                                             float *__restrict__ part) {
+    const int64_t k0 = int64_t(blockIdx.x) * rows, k1 = min(K, k0 + rows);
+    for (int64_t q = threadIdx.x; q < M * N; q += blockDim.x) {
+        const int64_t i = q / N, j = q % N;
+        float s = 0.f;
+        for (int64_t k = k0; k < k1; ++k) {
+            float a = A[k * M + i], b = B[k * N + j];
+            if (round_bf16) {
+                a = __bfloat162float(__float2bfloat16_rn(a));
+                b = __bfloat162float(__float2bfloat16_rn(b));
+            }
+            s = fmaf(a, b, s);
+        }
+        part[int64_t(blockIdx.x) * M * N + q] = s;
+    }
+}
+
+// one warp per column: lane l sums partials l, l + 32, ... in order, then a
+// butterfly over the lanes (a fixed order as well)
+__global__ void __launch_bounds__(kThreads) colsum_final_kernel(const float *__restrict__ part,
+                                                                int64_t G, int64_t N,
+                                                                float *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t n = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; n < N; n += warps) {
+        float s = 0.f;
+        for (int64_t b = lane; b < G; b += 32) s += part[b * N + n];
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[n] = s;
+    }
 }
 
 // column sums: out[n] = sum_m x[m][n]  (bias gradients); one block per column
@@ -539,22 +593,37 @@ int launch_im2col(int dim, const float *x, int64_t B, int C, int Si, bool chfirs
                   int sm_count, cudaStream_t st) {
     const int So = Si - 2, taps = dim == 2 ? 9 : 27;
     const int64_t Po = dim == 2 ? So * So : int64_t(So) * So * So;
-    const int g = grid_for(B * Po * C * taps, sm_count, 32);
-    if (dim == 2)
-        im2col_kernel<2><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
-    else
-        im2col_kernel<3><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
+    const int64_t total = B * Po * C * taps;
+    const int g = grid_for(total, sm_count, 32);
+    // unsigned 32-bit indices while q + the grid's stride cannot wrap
+    if (total < (int64_t(1) << 31)) {
+        if (dim == 2)
+            im2col_kernel<2, uint32_t><<<g, kThreads, 0, st>>>(x, uint32_t(B), C, Si, chfirst, col);
+        else
+            im2col_kernel<3, uint32_t><<<g, kThreads, 0, st>>>(x, uint32_t(B), C, Si, chfirst, col);
+    } else if (dim == 2) {
+        im2col_kernel<2, int64_t><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
+    } else {
+        im2col_kernel<3, int64_t><<<g, kThreads, 0, st>>>(x, B, C, Si, chfirst, col);
+    }
     return 1;
 }
 
 int launch_col2im(int dim, const float *dcol, int64_t B, int C, int Si, float *dx, int sm_count,
                   cudaStream_t st) {
     const int64_t Pi = dim == 2 ? Si * Si : int64_t(Si) * Si * Si;
-    const int g = grid_for(B * Pi * C, sm_count, 32);
-    if (dim == 2)
-        col2im_kernel<2><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
-    else
-        col2im_kernel<3><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
+    const int64_t total = B * Pi * C;
+    const int g = grid_for(total, sm_count, 32);
+    if (total < (int64_t(1) << 31)) {
+        if (dim == 2)
+            col2im_kernel<2, uint32_t><<<g, kThreads, 0, st>>>(dcol, uint32_t(B), C, Si, dx);
+        else
+            col2im_kernel<3, uint32_t><<<g, kThreads, 0, st>>>(dcol, uint32_t(B), C, Si, dx);
+    } else if (dim == 2) {
+        col2im_kernel<2, int64_t><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
+    } else {
+        col2im_kernel<3, int64_t><<<g, kThreads, 0, st>>>(dcol, B, C, Si, dx);
+    }
     return 1;
 }
 
@@ -826,6 +895,22 @@ int launch_gemm(const float *A, const float *Bm, float *C, const float *bias, in
     if (g_gemm_bf16 && err && !accumulate && tc_gemm_fits(M, N, K))
         return launch_tc_gemm(A, Bm, C, bias, M, N, K, transA, transB, err, sm_count, work,
                                work_floats, st);
+    if (transA && !transB && !accumulate && !bias && work && M * N <= 4096 && K >= 2048) {
+        // thin product with a long K: blocks of K rows, then a fixed-order sum
+        int64_t G = std::min<int64_t>((K + 63) / 64, int64_t(sm_count) * 4);
+        G = std::min<int64_t>(G, work_floats / (M * N));
+        if (G >= 2) {
+            const int64_t rows = (K + G - 1) / G;
+            G = (K + rows - 1) / rows;
+            thin_part_kernel<<<unsigned(G), kThreads, 0, st>>>(A, Bm, M, N, K, rows, g_gemm_bf16,
+                                                              work);
+            const int64_t per_block = kThreads / 32;
+            colsum_final_kernel<<<unsigned(std::min<int64_t>((M * N + per_block - 1) / per_block,
+                                                             4096)),
+                                  kThreads, 0, st>>>(work, G, M * N, C);
+            return 2;
+        }
+    }
     if (!transA && transB && !accumulate && N <= 32) {
         gemm_nt32_kernel<<<unsigned((M + 31) / 32), 64, 0, st>>>(A, Bm, C, bias, M, int(N), K,
                                                                  g_gemm_bf16);
@@ -887,9 +972,23 @@ int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStr
     return 1;
 }
 
-int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st) {
-    colsum_kernel<<<unsigned(std::min<int64_t>(N, 1024)), kThreads, 0, st>>>(x, M, N, out);
-    return 1;
+int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st,
+                  float *work, int64_t work_floats, int sm_count) {
+    // blocks of at least 64 rows, about 4 per SM, as the workspace allows
+    int64_t G = std::min<int64_t>((M + 63) / 64, int64_t(sm_count) * 4);
+    if (work && N > 0) G = std::min<int64_t>(G, work_floats / N);
+    if (!work || G < 2) {
+        colsum_kernel<<<unsigned(std::min<int64_t>(N, 1024)), kThreads, 0, st>>>(x, M, N, out);
+        return 1;
+    }
+    const int64_t rows = (M + G - 1) / G;
+    G = (M + rows - 1) / rows;
+    colsum_part_kernel<<<unsigned(G), kThreads, 0, st>>>(x, M, N, rows, work);
+    const int64_t per_block = kThreads / 32;
+    colsum_final_kernel<<<unsigned(std::max<int64_t>(1, std::min<int64_t>((N + per_block - 1) / per_block,
+                                                                            4096))),
+                          kThreads, 0, st>>>(work, G, N, out);
+    return 2;
 }
 
 int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,

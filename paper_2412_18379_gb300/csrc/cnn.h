@@ -71,7 +71,10 @@ int launch_head(int dim, const float *y, const float *W1, const float *b1, const
 int launch_conv_relu(int dim, const float *x, bool chfirst, int64_t B, int C, int Si,
                      const float *W, const float *bias, float *y, cudaStream_t st);
 int launch_relu_back(const float *z, float *dy, int64_t n, int sm_count, cudaStream_t st);
-int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st);
+// out[n] = sum_m x[m][n] in a fixed order; with a workspace (work,
+// work_floats) in two coalesced passes, else one block per column
+int launch_colsum(const float *x, int64_t M, int64_t N, float *out, cudaStream_t st,
+                  float *work = nullptr, int64_t work_floats = 0, int sm_count = 0);
 int launch_mse_grad(const float *out, const float *tgt, int64_t n, float *g, float *loss,
                     int sm_count, cudaStream_t st);
 int launch_adam(float *w, const float *g, float *m, float *v, int64_t n, float lr, int64_t t,

@@ -178,13 +178,13 @@ int backward(cs_ctx *ctx, Predictor &P, int64_t B, const float *tgt, float *loss
     n += launch_mse_grad(P.out, tgt, B * S.dim, P.gout, loss, sm, st);
     n += gemm(ctx, P, P.gout, P.a5, P.g + S.w_off[f2], nullptr,
               S.dim, S.hidden, B, true, false, st);
-    n += launch_colsum(P.gout, B, S.dim, P.g + S.b_off[f2], st);
+    n += launch_colsum(P.gout, B, S.dim, P.g + S.b_off[f2], st, P.splitk, P.splitk_n, sm);
     n += gemm(ctx, P, P.gout, P.w + S.w_off[f2], P.da5, nullptr,
               B, S.hidden, S.dim, false, false, st);
     n += launch_relu_back(P.z5, P.da5, B * S.hidden, sm, st);
     const float *h4 = P.y[S.n_conv - 1];
     n += gemm(ctx, P, P.da5, h4, P.g + S.w_off[f1], nullptr, S.hidden, S.ch, B, true, false, st);
-    n += launch_colsum(P.da5, B, S.hidden, P.g + S.b_off[f1], st);
+    n += launch_colsum(P.da5, B, S.hidden, P.g + S.b_off[f1], st, P.splitk, P.splitk_n, sm);
     float *dy = P.dy0, *dnext = P.dy1;
     n += gemm(ctx, P, P.da5, P.w + S.w_off[f1], dy, nullptr, B, S.ch, S.hidden, false, false, st);
     // conv layers, last to first; edge of layer l's input
@@ -201,7 +201,7 @@ int backward(cs_ctx *ctx, Predictor &P, int64_t B, const float *tgt, float *loss
         n += launch_relu_back(P.z[l], dy, B * Po * S.ch, sm, st);
         n += gemm(ctx, P, dy, P.col[l], P.g + S.w_off[l], nullptr,
                   S.ch, K, B * Po, true, false, st);
-        n += launch_colsum(dy, B * Po, S.ch, P.g + S.b_off[l], st);
+        n += launch_colsum(dy, B * Po, S.ch, P.g + S.b_off[l], st, P.splitk, P.splitk_n, sm);
         if (l > 0) {
             n += gemm(ctx, P, dy, P.w + S.w_off[l], P.dcol, nullptr,
                       B * Po, K, S.ch, false, false, st);

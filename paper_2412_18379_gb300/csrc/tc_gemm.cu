@@ -324,8 +324,7 @@ void launch_bn(const TcGemm &g, int64_t splits, int *err, cudaStream_t st) {
 }  // namespace
 
 bool tc_gemm_fits(int64_t M, int64_t N, int64_t K) {
-    const int64_t n = std::min(M, N), m = std::max(M, N);
-    return n >= 16 && m >= 64 && K >= 16;
+    return std::min(M, N) >= 16 && K >= 16;
 }
 
 int64_t tc_gemm_work_floats(int sm_count) { return int64_t(2) * sm_count * kBM * 256; }
