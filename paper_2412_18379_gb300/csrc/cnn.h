@@ -87,11 +87,26 @@ struct TcHold {
     const int *flag = nullptr;
     uint32_t polls = 0;
 };
+// Where a tensor-core grid predictor kernel takes its input velocities: the
+// grid velocity U (node null), or the P1 interpolation of the nodal velocity
+// un at each predictor cell centre through the mesh's static table (node, w),
+// computed as the tile's input is loaded (the resample kernel's arithmetic,
+// in its order, so the same bits) and written to U_out for the tile's own
+// cells. The 2-D kernel takes either; the 3-D kernel takes the grid
+// velocity only (a tile's (T + 6)^3 input cells are many times its T^3 own
+// cells, so interpolating them costs more than the separate resample).
+struct TcSource {
+    const float *U = nullptr;
+    const int32_t *node = nullptr;
+    const float *w = nullptr;
+    const double *un = nullptr;
+    float *U_out = nullptr;
+};
 // tensor-core grid inference of the 2-D predictor (cnn_tc.cu)
 int64_t tc_packed_bytes();
 int launch_pack_tc(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
 // tile_rows: output rows per tile (24, 13 or 8), 0 = tc_pick_tile_rows
-int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+int launch_cnn2d_tc(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed,
                     float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st,
                     TcHold hold = TcHold());
 // the tile height with the least estimated cost on a grid (24, 13 or 8)
@@ -100,7 +115,7 @@ int tc_pick_tile_rows(const DevMesh &m, int sm_count);
 // the cubic output tiles (4, 3 or 2), 0 = tc3_pick_tile
 int64_t tc3_packed_bytes();
 int launch_pack_tc3(const float *w, const NetShape &S, uint8_t *packed, cudaStream_t st);
-int launch_cnn3d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+int launch_cnn3d_tc(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed,
                     float *dhat, int *err, int sm_count, int tile, cudaStream_t st,
                     TcHold hold = TcHold());
 int tc3_pick_tile(const DevMesh &m, int sm_count);

@@ -144,7 +144,7 @@ __device__ __forceinline__ bool epi3_or(bool flag) {
 
 template <int T>
 __global__ void __launch_bounds__(kThreads3, 1) cnn3d_tc_kernel(
-    const DevMesh m, const float *__restrict__ U, float s0, float s1, float s2,
+    const DevMesh m, const TcSource src, float s0, float s1, float s2,
     const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err, TcHold hold) {
     using G = Geo3<T>;
     constexpr int D = G::D;
@@ -200,18 +200,36 @@ __global__ void __launch_bounds__(kThreads3, 1) cnn3d_tc_kernel(
         fence_after();
         if (*abort_flag) break;
         const int cx0 = (tile % tx) * T, cy0 = ((tile / tx) % ty) * T, cz0 = (tile / (tx * ty)) * T;
-        // ---- input: (T + 6)^3 cells around the tile, zero outside the grid ----
-        for (int i = tid; i < D * D * D; i += kThreads3) {
-            const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
-            const int cx = cx0 + ix - 3, cy = cy0 + iy - 3, cz = cz0 + iz - 3;
-            float v[3] = {0.f, 0.f, 0.f};
-            if (cx >= 0 && cx < gx && cy >= 0 && cy < gy && cz >= 0 && cz < gz) {
-                const int64_t c = (int64_t(cz) * gy + cy) * gx + cx;
-                #pragma unroll
-                for (int q = 0; q < 3; ++q) v[q] = __ldg(U + c * 3 + q) * scale[q];
+        // ---- input: (T + 6)^3 cells around the tile, zero outside the grid;
+        //      kB cells per thread at a time, their loads in flight together
+        //      (the grid velocity src.U; this kernel does not take the nodal
+        //      source: a tile's input cells are many times its own) ----
+        constexpr int kB = 3, kCells3 = D * D * D;
+        for (int i0 = tid; i0 < kCells3; i0 += kB * kThreads3) {
+            int64_t cc[kB];
+            #pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int i = i0 + j * kThreads3;
+                const int ix = i % D, iy = (i / D) % D, iz = i / (D * D);
+                const int cx = cx0 + ix - 3, cy = cy0 + iy - 3, cz = cz0 + iz - 3;
+                cc[j] = i < kCells3 && cx >= 0 && cx < gx && cy >= 0 && cy < gy && cz >= 0 && cz < gz
+                            ? (int64_t(cz) * gy + cy) * gx + cx
+                            : -1;
             }
-            *reinterpret_cast<uint4 *>(in + 16 * i) =
-                make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], 0.f), 0u, 0u);
+            float v[kB][3];
+            #pragma unroll
+            for (int j = 0; j < kB; ++j)
+                #pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2)
+                    v[j][k2] = cc[j] >= 0 ? __ldg(src.U + cc[j] * 3 + k2) : 0.f;
+            #pragma unroll
+            for (int j = 0; j < kB; ++j) {
+                const int i = i0 + j * kThreads3;
+                if (i >= kCells3) break;
+                *reinterpret_cast<uint4 *>(in + 16 * i) =
+                    make_uint4(pack_bf16x2(v[j][0] * scale[0], v[j][1] * scale[1]),
+                               pack_bf16x2(v[j][2] * scale[2], 0.f), 0u, 0u);
+            }
         }
         fence_async_smem();
         fence_before();
@@ -412,7 +430,7 @@ int64_t cost3(const DevMesh &m, int sm_count) {
 }
 
 template <int T>
-int launch3(const DevMesh &m, const float *U, double dt, const uint8_t *packed, float *dhat,
+int launch3(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed, float *dhat,
             int *err, int sm_count, cudaStream_t st, TcHold hold) {
     static bool attr = false;
     if (!attr) {
@@ -422,7 +440,7 @@ int launch3(const DevMesh &m, const float *U, double dt, const uint8_t *packed, 
     }
     const int grid = int(std::min<int64_t>(tiles3<T>(m), sm_count));
     launch_pdl(cnn3d_tc_kernel<T>, dim3(grid), dim3(kThreads3), size_t(Geo3<T>::kSmTotal), st, m,
-               U, float(dt / m.sa[0]), float(dt / m.sa[1]), float(dt / m.sa[2]), packed, dhat, err,
+               src, float(dt / m.sa[0]), float(dt / m.sa[1]), float(dt / m.sa[2]), packed, dhat, err,
                hold);
     return 1;
 }
@@ -443,12 +461,12 @@ int tc3_pick_tile(const DevMesh &m, int sm_count) {
     return c4 <= c3 ? 4 : 3;
 }
 
-int launch_cnn3d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+int launch_cnn3d_tc(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed,
                     float *dhat, int *err, int sm_count, int tile, cudaStream_t st, TcHold hold) {
     const int t = tile ? tile : tc3_pick_tile(m, sm_count);
-    if (t == 4) return launch3<4>(m, U, dt, packed, dhat, err, sm_count, st, hold);
-    if (t == 3) return launch3<3>(m, U, dt, packed, dhat, err, sm_count, st, hold);
-    return launch3<2>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    if (t == 4) return launch3<4>(m, src, dt, packed, dhat, err, sm_count, st, hold);
+    if (t == 3) return launch3<3>(m, src, dt, packed, dhat, err, sm_count, st, hold);
+    return launch3<2>(m, src, dt, packed, dhat, err, sm_count, st, hold);
 }
 
 }  // namespace cs

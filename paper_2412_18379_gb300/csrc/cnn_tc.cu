@@ -240,7 +240,7 @@ __device__ __forceinline__ void issue_fc1(uint32_t dcol, uint64_t adesc, uint64_
 
 template <int TH>
 __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
-    const DevMesh m, const float *__restrict__ U, float scale0, float scale1,
+    const DevMesh m, const TcSource src, float scale0, float scale1,
     const uint8_t *__restrict__ packed, float *__restrict__ dhat, int *err, TcHold hold) {
     using G = Geo<TH>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -289,13 +289,62 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
     pdl_wait();
     float2 *stage = reinterpret_cast<float2 *>(x0);   // staging, until tap-packed
     static_assert(G::kInRows * kW * 8 <= G::kX0Bytes, "staging fits the input buffer");
-    const float2 *U2 = reinterpret_cast<const float2 *>(U);
+    const float2 *U2 = reinterpret_cast<const float2 *>(src.U);
     if (warp < kEpiWarps) {
         const int cx0 = (blockIdx.x % tiles_x) * kTileW - 4, cy0 = (blockIdx.x / tiles_x) * TH - 4;
-        for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
-            const int cx = cx0 + i % kW, cy = cy0 + i / kW;
-            const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
-            cp_async8_zfill(stage + i, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+        if (src.node) {
+            // the resample fused: every cell of this thread first loads its
+            // table entries, then its nodal velocities, then interpolates (two
+            // rounds of loads in flight, not two per cell); the tile's own
+            // cells are kept as the mesh's grid velocity
+            constexpr int kCells = G::kInRows * kW, kPer = (kCells + kEpiWarps * 32 - 1) / (kEpiWarps * 32);
+            int32_t nd[kPer][3];
+            float wt[kPer][3];
+            int64_t cc[kPer];
+            #pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int i = tid + j * kEpiWarps * 32;
+                const int cx = cx0 + i % kW, cy = cy0 + i / kW;
+                const bool in = i < kCells && cx >= 0 && cx < gx && cy >= 0 && cy < gy;
+                cc[j] = in ? int64_t(cy) * gx + cx : -1;
+                #pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    nd[j][q] = in ? __ldg(src.node + cc[j] * 3 + q) : -1;
+                    wt[j][q] = in ? __ldg(src.w + cc[j] * 3 + q) : 0.f;
+                }
+            }
+            double un[kPer][3][2];
+            #pragma unroll
+            for (int j = 0; j < kPer; ++j)
+                #pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    #pragma unroll
+                    for (int k = 0; k < 2; ++k)
+                        un[j][q][k] = nd[j][0] >= 0 ? __ldg(src.un + int64_t(nd[j][q]) * 2 + k) : 0.0;
+            #pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+                const int i = tid + j * kEpiWarps * 32;
+                if (i >= kCells) break;
+                // the resample kernel's arithmetic, in its order
+                float v0 = 0.f, v1 = 0.f;
+                if (nd[j][0] >= 0) {
+                    #pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        v0 = fmaf(wt[j][q], trunc_to_float(un[j][q][0]), v0);
+                        v1 = fmaf(wt[j][q], trunc_to_float(un[j][q][1]), v1);
+                    }
+                }
+                stage[i] = make_float2(v0, v1);
+                const int ix = i % kW, iy = i / kW;
+                if (cc[j] >= 0 && ix >= 4 && ix < 4 + kTileW && iy >= 4 && iy < 4 + TH)
+                    reinterpret_cast<float2 *>(src.U_out)[cc[j]] = make_float2(v0, v1);
+            }
+        } else {
+            for (int i = tid; i < G::kInRows * kW; i += kEpiWarps * 32) {
+                const int cx = cx0 + i % kW, cy = cy0 + i / kW;
+                const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
+                cp_async8_zfill(stage + i, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+            }
         }
     }
     for (int i = tid; i < TcLayout::total / 16; i += kThreadsTC)
@@ -327,7 +376,16 @@ __global__ void __launch_bounds__(kThreadsTC, 1) cnn2d_tc_kernel(
             for (int y = 0; y < G::kInRows; ++y) {
                 const int cx = cx0 + lane, cy = cy0 + y;
                 const bool in = cx >= 0 && cx < gx && cy >= 0 && cy < gy;
-                cp_async8_zfill(stage + y * kW + lane, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+                if (src.node) {
+                    float v[2] = {0.f, 0.f};
+                    if (in) interp_cell<2>(src.node, src.w, src.un, int64_t(cy) * gx + cx, v);
+                    stage[y * kW + lane] = make_float2(v[0], v[1]);
+                    if (in && lane >= 4 && lane < 4 + kTileW && y >= 4 && y < 4 + TH)
+                        reinterpret_cast<float2 *>(src.U_out)[int64_t(cy) * gx + cx] =
+                            make_float2(v[0], v[1]);
+                } else {
+                    cp_async8_zfill(stage + y * kW + lane, in ? U2 + int64_t(cy) * gx + cx : U2, in);
+                }
             }
             cp_async_wait_all();
             uint32_t *win = reinterpret_cast<uint32_t *>(smem + G::kSmWin);
@@ -677,8 +735,8 @@ int64_t tile_cost(const DevMesh &m, int sm_count) {
 }
 
 template <int TH>
-int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *packed, float *dhat,
-                int *err, int sm_count, cudaStream_t st, TcHold hold) {
+int launch_rows(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed,
+                float *dhat, int *err, int sm_count, cudaStream_t st, TcHold hold) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(cnn2d_tc_kernel<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -687,7 +745,7 @@ int launch_rows(const DevMesh &m, const float *U, double dt, const uint8_t *pack
     }
     const int grid = std::min(tiles_of<TH>(m), sm_count);
     launch_pdl(cnn2d_tc_kernel<TH>, dim3(grid), dim3(kThreadsTC), size_t(Geo<TH>::kSmTotal), st, m,
-               U, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err, hold);
+               src, float(dt / m.sa[0]), float(dt / m.sa[1]), packed, dhat, err, hold);
     return 1;
 }
 
@@ -700,13 +758,13 @@ int tc_pick_tile_rows(const DevMesh &m, int sm_count) {
     return c13 <= c8 ? 13 : 8;
 }
 
-int launch_cnn2d_tc(const DevMesh &m, const float *U, double dt, const uint8_t *packed,
+int launch_cnn2d_tc(const DevMesh &m, const TcSource &src, double dt, const uint8_t *packed,
                     float *dhat, int *err, int sm_count, int tile_rows, cudaStream_t st,
                     TcHold hold) {
     const int th = tile_rows ? tile_rows : tc_pick_tile_rows(m, sm_count);
-    if (th == 24) return launch_rows<24>(m, U, dt, packed, dhat, err, sm_count, st, hold);
-    if (th == 13) return launch_rows<13>(m, U, dt, packed, dhat, err, sm_count, st, hold);
-    return launch_rows<8>(m, U, dt, packed, dhat, err, sm_count, st, hold);
+    if (th == 24) return launch_rows<24>(m, src, dt, packed, dhat, err, sm_count, st, hold);
+    if (th == 13) return launch_rows<13>(m, src, dt, packed, dhat, err, sm_count, st, hold);
+    return launch_rows<8>(m, src, dt, packed, dhat, err, sm_count, st, hold);
 }
 
 }  // namespace cs

@@ -389,11 +389,16 @@ cs_status predict_tiles(cs_ctx *ctx, Predictor &P, cs::Mesh *m, const float *gri
 }
 
 // prediction at every predictor cell of mesh m from the grid velocity `grid`
-cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, float *dhat,
-                       cudaStream_t st) {
+// Prediction at every predictor cell from `src`: the grid velocity, or (the
+// tensor-core engine only) the nodal velocity, resampled as the kernel loads
+// its tiles
+cs_status predict_grid_src(cs_ctx *ctx, cs::Mesh *m, const TcSource &src, double dt, float *dhat,
+                           cudaStream_t st) {
     Predictor *P = get_pred(ctx, m->d.dim);
     if (!P || !P->loaded) return fail(ctx, CS_ENOPRED, "no predictor loaded for this dimension");
-    if (!grid) return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
+    const float *grid = src.U;
+    if (!grid && !(src.node && ctx->engine == 1))
+        return fail(ctx, CS_EINVAL, "the mesh has no grid velocity yet");
     if (ctx->engine == 1) {
         // tensor-core grid kernels: weights repacked after every load / training
         const int64_t bytes = m->d.dim == 2 ? tc_packed_bytes() : tc3_packed_bytes();
@@ -417,11 +422,11 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
             hold.polls = 1u << 16;
         }
         if (m->d.dim == 2)
-            ctx->launches += launch_cnn2d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
+            ctx->launches += launch_cnn2d_tc(pred_view(m->d), src, dt, P->packed, dhat,
                                              ctx->dev_err, ctx->sm_count, ctx->tc_tile_rows, st,
                                              hold);
         else
-            ctx->launches += launch_cnn3d_tc(pred_view(m->d), grid, dt, P->packed, dhat,
+            ctx->launches += launch_cnn3d_tc(pred_view(m->d), src, dt, P->packed, dhat,
                                              ctx->dev_err, ctx->sm_count, ctx->tc3_tile, st, hold);
         return CS_OK;
     }
@@ -441,6 +446,13 @@ cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, f
                              cudaMemcpyDeviceToDevice, st));
     }
     return CS_OK;
+}
+
+cs_status predict_grid(cs_ctx *ctx, cs::Mesh *m, const float *grid, double dt, float *dhat,
+                       cudaStream_t st) {
+    TcSource src;
+    src.U = grid;
+    return predict_grid_src(ctx, m, src, dt, dhat, st);
 }
 
 cs_status reserve_tiles(cs_ctx *ctx, cs::Mesh *m) {
@@ -523,6 +535,25 @@ cs_status cnn_prepare(cs_ctx *ctx, cs::Mesh *m, const float *grid, const double 
         if (!u_nodal) return fail(ctx, CS_EINVAL, "no velocity for the start predictor");
         rc = ensure_interp(ctx, m, st);
         if (rc) return rc;
+        if (ctx->engine == 1 && m->d.dim == 2) {
+            // the 2-D tensor-core kernel resamples as it loads its tiles and
+            // stores the grid velocity in the mesh (the same bits as the
+            // resample kernel). In 3-D a tile's (T + 6)^3 input cells are
+            // many times its T^3 own cells, so the separate resample is
+            // cheaper there.
+            TcSource src;
+            src.node = m->interp_node;
+            src.w = m->interp_w;
+            src.un = u_nodal;
+            src.U_out = m->grid_u;
+            const int ev = ctx->prof.begin(CS_STAGE_CNN, st);
+            rc = predict_grid_src(ctx, m, src, dt, m->grid_dhat, st);
+            ctx->prof.end(ev, st);
+            if (rc) return rc;
+            m->grid_u_valid = true;
+            *dhat_out = m->grid_dhat;
+            return CS_OK;
+        }
         const int ev = ctx->prof.begin(CS_STAGE_RESAMPLE, st);
         ctx->launches += launch_resample(pred_view(m->d), m->interp_node, m->interp_w, u_nodal, m->grid_u,
                                          ctx->sm_count, st);

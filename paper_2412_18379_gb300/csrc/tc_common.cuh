@@ -223,5 +223,27 @@ __device__ __forceinline__ bool wait_flag(const int *flag, uint32_t polls, volat
     return false;
 }
 
+// The P1 interpolation of the nodal velocity at predictor cell c through the
+// static table (node, w), with the resample kernel's arithmetic in its order
+// (FP32 fused multiply-adds of the truncated nodal components, vertex by
+// vertex); 0 where the cell centre has no host.
+template <int D>
+__device__ __forceinline__ void interp_cell(const int32_t *__restrict__ node,
+                                            const float *__restrict__ w,
+                                            const double *__restrict__ un, int64_t c, float *out) {
+    #pragma unroll
+    for (int k = 0; k < D; ++k) out[k] = 0.f;
+    if (__ldg(node + c * (D + 1)) >= 0) {
+        #pragma unroll
+        for (int i = 0; i <= D; ++i) {
+            const int32_t v = __ldg(node + c * (D + 1) + i);
+            const float wi = __ldg(w + c * (D + 1) + i);
+            #pragma unroll
+            for (int k = 0; k < D; ++k)
+                out[k] = fmaf(wi, trunc_to_float(__ldg(un + int64_t(v) * D + k)), out[k]);
+        }
+    }
+}
+
 }  // namespace
 }  // namespace cs

@@ -878,3 +878,34 @@ def test_a_wait_that_runs_out_ends_the_kernel_with_cs_edevice(ctx, name, kw, str
     ctx.device_status()
     assert np.array_equal(before.cpu().numpy().view(np.uint32), after.cpu().numpy().view(np.uint32))
     mesh.release()
+
+
+@pytest.mark.parametrize("rows", [24, 13, 8])
+def test_fused_resample_gives_the_resample_kernels_bits(ctx, rows):
+    """CNN-SNS on the mesh nodes in 2-D resamples the nodal velocity inside
+    the tensor-core predictor as it loads its tiles. On a 400^2 predictor
+    grid (289 to 850 tiles: CTAs take several, so both the first-tile and the
+    loader warp's path run), the grid velocity it stores and the predictions
+    it starts the walks from must equal, bit for bit, those of the separate
+    resample kernel followed by the prediction."""
+    import torch
+    c = make_case("tg2d", n_side=401, cfl=8)
+    mesh = ctx.upload_mesh(c.xyz, c.conn)
+    ctx.load_predictor(2, init_weights(2, 41))
+    ctx.predictor_tile_rows(rows)
+    try:
+        cells = int(np.prod(mesh.info()["pred_grid"]))
+        fused = ctx.track(mesh, _dev(c.x), _dev(c.u), c.dt, mode="cnn", start_out=True)
+        a = torch.empty((cells, 2), dtype=torch.float32, device="cuda")
+        ctx.predict(mesh, c.dt, out=a)            # from the grid velocity the track stored
+        ctx.grid_velocity(mesh, _dev(c.u))         # the resample kernel
+        b = torch.empty((cells, 2), dtype=torch.float32, device="cuda")
+        ctx.predict(mesh, c.dt, out=b)
+        ref = ctx.track_dhat(mesh, _dev(c.x), _dev(c.u), c.dt, dhat=b, start_out=True)
+        torch.cuda.synchronize()
+        ctx.device_status()
+        assert torch.equal(a, b)
+        for k in ("start", "host", "path_len", "status"):
+            assert torch.equal(fused[k], ref[k]), k
+    finally:
+        ctx.predictor_tile_rows(0)
