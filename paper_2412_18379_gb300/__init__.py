@@ -35,8 +35,20 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+_DTYPE_NAMES = {}
+
+
 def _dtype_name(a):
-    return str(a.dtype).replace("torch.", "")
+    d = a.dtype
+    name = _DTYPE_NAMES.get(d)
+    if name is None:
+        name = _DTYPE_NAMES[d] = str(d).replace("torch.", "")
+    return name
+
+
+def _numel(a):
+    """Element count of a numpy array or a torch tensor."""
+    return int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
 
 
 def _contiguous(a):
@@ -73,9 +85,8 @@ def check_track_args(dim, x, u, start=None, out=None, on_device=True):
             raise ValueError("%s must be contiguous" % name)
         if shape is not None and tuple(a.shape) != shape:
             raise ValueError("%s must have shape %s, not %s" % (name, shape, tuple(a.shape)))
-        if shape is None and int(np.prod(a.shape)) < n:
-            raise ValueError("%s holds %d elements, fewer than n = %d"
-                             % (name, int(np.prod(a.shape)), n))
+        if shape is None and _numel(a) < n:
+            raise ValueError("%s holds %d elements, fewer than n = %d" % (name, _numel(a), n))
         cuda = bool(getattr(a, "is_cuda", False))
         if on_device and (not cuda or a.device != dev):
             raise ValueError("%s must be a CUDA tensor on %s" % (name, dev))
@@ -261,7 +272,6 @@ class Context:
         import torch
         n = check_track_args(mesh.dim, x, u, start, out)
         out = self._device_out(n, x.device, out, start_out)
-        check_track_args(mesh.dim, x, u, start, out)
         st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track(
             self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
@@ -278,7 +288,6 @@ class Context:
         import torch
         n = check_track_args(mesh.dim, x, u, start, out)
         out = self._device_out(n, x.device, out, start_out)
-        check_track_args(mesh.dim, x, u, start, out)
         st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track_noalloc(
             self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
@@ -296,13 +305,13 @@ class Context:
             u = np.ascontiguousarray(u, dtype=np.float64)
             if start is not None:
                 start = np.ascontiguousarray(start, dtype=np.int32)
+        # one check of every array; outputs made here need none
         n = check_track_args(mesh.dim, x, u, start, out, on_device=False)
         if out is None:
             out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
                        status=np.empty(n, dtype=np.uint8))
             if start_out:
                 out["start"] = np.empty(n, dtype=np.int32)
-        check_track_args(mesh.dim, x, u, start, out, on_device=False)
         self._check(self.lib.cs_track_host(
             self.h, mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt), _ptr(start),
             MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
@@ -451,7 +460,6 @@ class Context:
                 raise ValueError("dhat must be a contiguous float32 CUDA tensor [%d, %d]"
                                  % (cells, mesh.dim))
         out = self._device_out(n, x.device, out, start_out)
-        check_track_args(mesh.dim, x, u, start, out)
         st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track_dhat(
             self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(dhat),
@@ -582,7 +590,6 @@ class Context:
         import torch
         n = check_track_args(mesh.dim, x, u, start, out)
         out = self._device_out(n, x.device, out, start_out)
-        check_track_args(mesh.dim, x, u, start, out)
         st = stream if stream is not None else torch.cuda.current_stream(x.device)
         self._check(self.lib.cs_track_classifier(
             self.h, mesh.id, n, _ptr(x), _ptr(u), float(dt), _ptr(start), _ptr(out["host"]),
