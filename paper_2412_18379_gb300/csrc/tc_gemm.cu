@@ -57,6 +57,7 @@ struct GemmGeo {
     static constexpr int kSmBar = 2 * kStage;
     static constexpr int kSmSlot = kSmBar + 3 * 8;
     static constexpr int kSmTotal = kSmSlot + 16;
+    static_assert(8 * 32 * 17 * 4 <= kSmBar, "the epilogue's per-warp tiles fit the operand stages");
     static constexpr uint32_t kCols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
 };
 
@@ -193,7 +194,7 @@ __device__ __forceinline__ void stage_operand(uint8_t *dst, const float *__restr
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kThreadsG) tc_gemm_kernel(const TcGemm g, int *err) {
+__global__ void __launch_bounds__(kThreadsG, 2) tc_gemm_kernel(const TcGemm g, int *err) {
     using G = GemmGeo<BN>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + G::kSmBar);
@@ -253,26 +254,50 @@ __global__ void __launch_bounds__(kThreadsG) tc_gemm_kernel(const TcGemm g, int 
     if (ok && nch > 0) {
         fence_after();
         // warp w reads TMEM lanes 32 (w % 4) ..; warps w and w + 4 take
-        // alternate 16-column pieces
+        // alternate 16-column pieces. A row-major output (a split's partial
+        // tile, or C with c_j == 1) goes through a per-warp tile in the now
+        // idle operand stages, so that a store instruction writes 16
+        // consecutive floats of two rows instead of one float of 32 rows.
         const int64_t i = i0 + 32 * (warp & 3) + lane;
         const uint32_t tq = tmem + (uint32_t(32 * (warp & 3)) << 16);
-        #pragma unroll 1
-        for (int jc = 16 * (warp >> 2); jc < BN; jc += 32) {
-            float v[16];
-            tmem_ld16(tq + uint32_t(jc), v);
-            if (i < g.M) {
-                #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int64_t j = j0 + jc + e;
-                    if (j >= g.N) break;
-                    if (g.split) {
-                        g.part[(int64_t(blockIdx.z) * g.M + i) * g.N + j] = v[e];
-                    } else {
+        if (!(g.split || g.c_j == 1)) {
+            // C with c_i == 1 (a swapped product): consecutive lanes write
+            // consecutive addresses already
+            #pragma unroll 1
+            for (int jc = 16 * (warp >> 2); jc < BN; jc += 32) {
+                float v[16];
+                tmem_ld16(tq + uint32_t(jc), v);
+                if (i < g.M) {
+                    #pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int64_t j = j0 + jc + e;
+                        if (j >= g.N) break;
                         float x = v[e];
                         if (g.bias) x += __ldg(g.bias + j);
                         g.C[i * g.c_i + j * g.c_j] = x;
                     }
                 }
+            }
+        } else {
+            float *tile = reinterpret_cast<float *>(smem) + warp * (32 * 17);
+            float *dst = g.split ? g.part + int64_t(blockIdx.z) * g.M * g.N : g.C;
+            const int64_t ld = g.split ? g.N : g.c_i;
+            const int e = lane & 15;
+            #pragma unroll 1
+            for (int jc = 16 * (warp >> 2); jc < BN; jc += 32) {
+                float v[16];
+                tmem_ld16(tq + uint32_t(jc), v);
+                #pragma unroll
+                for (int q = 0; q < 16; ++q) tile[lane * 17 + q] = v[q];
+                __syncwarp();
+                const int64_t j = j0 + jc + e;
+                const float bj = (!g.split && g.bias && j < g.N) ? __ldg(g.bias + j) : 0.f;
+                #pragma unroll 1
+                for (int r = lane >> 4; r < 32; r += 2) {
+                    const int64_t ii = i0 + 32 * (warp & 3) + r;
+                    if (ii < g.M && j < g.N) dst[ii * ld + j] = tile[r * 17 + e] + bj;
+                }
+                __syncwarp();
             }
         }
     }
