@@ -89,6 +89,30 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
     double xp[D];
     float xh[D], xl[D];
     if (valid) {
+        // CNN-SNS: Algorithm 2's origin, in FP32 (reading R23: it selects the
+        // start element only, never the host, and FP64 costs GB300 1/64 of
+        // the FP32 rate): x truncated to float and its predictor cell. The
+        // gather of the cell's predicted displacement depends on x alone, so
+        // it is issued before the departure point's FP64 arithmetic, which
+        // then runs under its latency (any x gives an in-range cell; the
+        // value is used only when x_p is finite).
+        float xt[D], dh[D];
+        if (a.mode == CS_CNN_SNS) {
+            int64_t c0 = 0;
+            #pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+                xt[k] = trunc_to_float(kPrefetch<D> ? f.x[lane * D + k] : __ldg(a.x + pp * D + k));
+                c0 = c0 * m.pga[k] + cell_f32(xt[k], m.lo_h[k], m.pinv_sa[k], m.pga[k]);
+            }
+            if constexpr (D == 2) {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(a.dhat) + c0);
+                dh[0] = v.x;
+                dh[D - 1] = v.y;
+            } else {
+                #pragma unroll
+                for (int k = 0; k < D; ++k) dh[k] = __ldg(a.dhat + c0 * D + k);
+            }
+        }
         bool finite = true;
         #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -110,27 +134,7 @@ __device__ __forceinline__ void prepare(const DevMesh &m, const TrackArgs &a, in
         if (finite && a.mode == CS_ASG_DIRECT) {
             c1 = grid_cell_f<D>(xp, xh, xl, m);
         } else if (finite && a.mode == CS_CNN_SNS) {
-            // Algorithm 2's origin, in FP32 (reading R23: it selects the start
-            // element only, never the host, and FP64 costs GB300 1/64 of the
-            // FP32 rate): x truncated to float, its predictor cell, then the
-            // ASG seed of y = x + dhat * (predictor cell size)
-            float xt[D];
-            #pragma unroll
-            for (int k = 0; k < D; ++k)
-                xt[k] = trunc_to_float(kPrefetch<D> ? f.x[lane * D + k] : __ldg(a.x + pp * D + k));
-            int64_t c0 = 0;
-            #pragma unroll
-            for (int k = D - 1; k >= 0; --k)
-                c0 = c0 * m.pga[k] + cell_f32(xt[k], m.lo_h[k], m.pinv_sa[k], m.pga[k]);
-            float dh[D];
-            if constexpr (D == 2) {
-                const float2 v = __ldg(reinterpret_cast<const float2 *>(a.dhat) + c0);
-                dh[0] = v.x;
-                dh[D - 1] = v.y;
-            } else {
-                #pragma unroll
-                for (int k = 0; k < D; ++k) dh[k] = __ldg(a.dhat + c0 * D + k);
-            }
+            // the ASG seed of y = x + dhat * (predictor cell size)
             c1 = 0;
             #pragma unroll
             for (int k = D - 1; k >= 0; --k) {
