@@ -393,9 +393,9 @@ def serve_bench(ctx, n_requests, rate, slots, seed, pred_stride, repeats):
     velocity field; requests of 1e4-2e6 particles (log-uniform, at most the
     mesh's nodes: a contiguous range of its nodes with their elements as the
     plain starts), CFL U(1, 16), CNN-SNS on the request's mesh and field (the
-    2-D and 3-D tensor-core predictors), inputs in pinned host memory, every
-    request copying its inputs in and its results out. p50/p99 are the
-    medians over `repeats` streams of n_requests each."""
+    2-D and 3-D tensor-core predictors), inputs and result buffers in pinned
+    host memory, every request copying its inputs in and its results out.
+    p50/p99 are the medians over `repeats` streams of n_requests each."""
     import torch
     from workloads.meshes import lattice_tris_2d, kuhn_3d, serving_mesh_sizes
     from workloads.fields import fourier_modes_2d, fourier_modes_3d
@@ -421,6 +421,7 @@ def serve_bench(ctx, n_requests, rate, slots, seed, pred_stride, repeats):
                             umax=float(np.sqrt((u * u).sum(axis=1)).max())))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
+    dims = {e["mesh"].id: e["mesh"].dim for e in entries}
     used, _ = ctx.memory_usage()
     # warm-up: one small request per mesh, so that no timed request pays a
     # kernel's first launch
@@ -433,36 +434,76 @@ def serve_bench(ctx, n_requests, rate, slots, seed, pred_stride, repeats):
             ctx.wait(t, timeout_ms=120000)
     finally:
         ctx.serve_stop()
-    reps = []
+    # every stream's requests are drawn before it starts, and their results go
+    # to slices of one pinned block, as a server reuses its response buffers:
+    # the arrival loop does nothing but submit
+    plans = []
     for rep in range(repeats):
+        plan = []
+        for _ in range(n_requests):
+            e = entries[rng.integers(len(entries))]
+            n = int(np.exp(rng.uniform(np.log(1e4), np.log(min(2e6, e["n"])))))
+            off = int(rng.integers(0, e["n"] - n + 1))
+            dt = rng.uniform(1.0, 16.0) * e["h"] / e["umax"]
+            plan.append((e, n, off, dt, rng.exponential(1.0 / rate)))
+        plans.append(plan)
+    cap = max(sum(p[1] for p in plan) for plan in plans)
+    res = dict(host=torch.empty(cap, dtype=torch.int32, pin_memory=True),
+               path_len=torch.empty(cap, dtype=torch.int32, pin_memory=True),
+               status=torch.empty(cap, dtype=torch.uint8, pin_memory=True))
+    # A server's staging buffers have carried requests before: one DMA pass
+    # over every pinned input and result buffer (the first transfer through
+    # a page of pinned memory runs far below the link's rate)
+    for e in entries:
+        for k in ("x", "u", "start"):
+            torch.empty(e[k].shape, dtype=e[k].dtype, device="cuda").copy_(e[k], non_blocking=True)
+    for v in res.values():
+        v.copy_(torch.zeros(v.shape, dtype=v.dtype, device="cuda"), non_blocking=True)
+    torch.cuda.synchronize()
+    reps = []
+    for plan in plans:
         ctx.serve_start(slots=slots, arena_bytes=4 << 30)
         tickets = []
+        o = 0
         t_next = time.perf_counter()
         try:
-            for _ in range(n_requests):
-                e = entries[rng.integers(len(entries))]
-                n = int(np.exp(rng.uniform(np.log(1e4), np.log(min(2e6, e["n"])))))
-                off = int(rng.integers(0, e["n"] - n + 1))
-                dt = rng.uniform(1.0, 16.0) * e["h"] / e["umax"]
-                t_next += rng.exponential(1.0 / rate)
+            for e, n, off, dt, gap in plan:
+                out = {k: v[o:o + n] for k, v in res.items()}
+                o += n
+                t_next += gap
                 while time.perf_counter() < t_next:
                     pass
                 sl = slice(off, off + n)
                 t, _ = ctx.submit(e["mesh"], e["x"][sl], e["u"][sl], dt, start=e["start"][sl],
-                                  mode="cnn", field=e["field"])
+                                  mode="cnn", field=e["field"], out=out)
                 tickets.append(t)
             modes = [ctx.wait(t, timeout_ms=120000) for t in tickets]
             r = ctx.serve_report()
+            trace = ctx.serve_trace()
         finally:
             ctx.serve_stop()
         r["cnn_sns_share"] = float(np.mean(np.array(modes) == 1))
+        # where the time of the slowest requests went: waiting for a slot or
+        # arena memory (admit - submit), or running (done - admit)
+        wait = np.array([t["admit_ms"] - t["submit_ms"] for t in trace])
+        run = np.array([t["done_ms"] - t["admit_ms"] for t in trace])
+        r["queue_p99_ms"] = float(np.percentile(wait, 99))
+        r["service_p99_ms"] = float(np.percentile(run, 99))
+        slow = sorted(trace, key=lambda t: t["done_ms"] - t["submit_ms"])[-4:]
+        r["slowest"] = [{"n": t["n"], "dim": dims[t["mesh_id"]], "in_flight": t["in_flight"],
+                         "queue_ms": round(t["admit_ms"] - t["submit_ms"], 4),
+                         "service_ms": round(t["done_ms"] - t["admit_ms"], 4),
+                         "device_ms": {k: round(t[k + "_ms"], 4)
+                                       for k in ("h2d", "predict", "walk", "d2h")}}
+                        for t in reversed(slow)]
         reps.append(r)
     med = lambda k: float(np.median([r[k] for r in reps]))
     out = {"p50_ms": med("p50_ms"), "p99_ms": med("p99_ms"), "mean_ms": med("mean_ms"),
            "max_ms": med("max_ms"), "particles_per_s": med("particles_per_s"),
            "repeats": [{k: r[k] for k in ("p50_ms", "p99_ms", "max_ms", "particles_per_s",
                                           "completed", "rejected", "max_concurrent", "peak_bytes",
-                                          "cnn_sns_share")} for r in reps],
+                                          "cnn_sns_share", "queue_p99_ms", "service_p99_ms",
+                                          "slowest")} for r in reps],
            "requests_per_repeat": n_requests, "arrival_rate_per_s": rate, "slots": slots,
            "meshes": "16 triangle meshes (%.1fM triangles) + 16 tetrahedral meshes (%.1fM tets), "
                      "each with its own resident 8-mode field" % (n_elems[2] / 1e6, n_elems[3] / 1e6),

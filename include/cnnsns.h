@@ -568,6 +568,36 @@ cs_status cs_serve_wait(cs_ctx *ctx, int64_t ticket, int32_t timeout_ms, cs_stat
 /* Latency percentiles and throughput of the requests finished so far. */
 cs_status cs_serve_report(cs_ctx *ctx, cs_serve_stats *out);
 
+/* One finished request of the running server. Times are milliseconds since
+ * the server's first submit: submitted (cs_serve_submit returned), admitted
+ * (slot and arena memory taken, inputs about to be copied in) and done (its
+ * end event seen by the worker). The latency of cs_serve_report is
+ * done - submit; admit - submit is its wait in the queue. */
+typedef struct cs_serve_record {
+    int64_t ticket;
+    int64_t n;              /* particles                                     */
+    int32_t mesh_id;
+    int32_t mode_used;      /* start rule it ran with                        */
+    int32_t slot;           /* the slot (stream) it ran on                   */
+    int32_t in_flight;      /* requests on the GPU after it was admitted     */
+    int32_t result;         /* its cs_status                                 */
+    int32_t reserved;
+    double  dt;             /* its time step                                 */
+    double  submit_ms, admit_ms, done_ms;
+    /* device time of its stages on its stream (CUDA events): the input
+     * copies, the start predictor (0 without CNN-SNS), the walk, the output
+     * copies; the gaps between admit_ms and done_ms beyond their sum are
+     * host-side (launch, event polling) or waits for the GPU held by others */
+    double  h2d_ms, predict_ms, walk_ms, d2h_ms;
+} cs_serve_record;
+
+/* Copy the records of the requests finished so far, in the order they
+ * finished, into out[0, cap) (HOST memory the caller owns); *count = records
+ * copied. With out = NULL, *count = the number of records held. The server
+ * keeps every record until cs_serve_stop. CS_EINVAL when not serving, when
+ * count is NULL or when cap < 0. */
+cs_status cs_serve_trace(cs_ctx *ctx, int64_t cap, cs_serve_record *out, int64_t *count);
+
 /* Drain the queue, stop the worker and free the serving resources. */
 cs_status cs_serve_stop(cs_ctx *ctx);
 

@@ -603,14 +603,20 @@ class Context:
         self._check(self.lib.cs_serve_start(self.h, ctypes.byref(cfg)))
         self._requests = {}
 
-    def submit(self, mesh, x, u, dt, start=None, mode="sns", field=None):
+    def submit(self, mesh, x, u, dt, start=None, mode="sns", field=None, out=None):
         """Queue a request (host arrays, pinned torch tensors overlap best).
-        Returns (ticket, outputs); outputs are valid after wait(ticket)."""
+        out: the caller's host arrays host, path_len (int32) and status
+        (uint8) of at least n elements (a server reuses its pinned result
+        buffers), else new pinned ones. Returns (ticket, outputs); outputs are
+        valid after wait(ticket)."""
         import torch
-        n = check_track_args(mesh.dim, x, u, start, on_device=False)
-        out = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
-                   path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
-                   status=torch.empty(n, dtype=torch.uint8).pin_memory())
+        if out is not None and any(out.get(k) is None for k in ("host", "path_len", "status")):
+            raise ValueError("out needs host, path_len and status")
+        n = check_track_args(mesh.dim, x, u, start, out=out, on_device=False)
+        if out is None:
+            out = dict(host=torch.empty(n, dtype=torch.int32, pin_memory=True),
+                       path_len=torch.empty(n, dtype=torch.int32, pin_memory=True),
+                       status=torch.empty(n, dtype=torch.uint8, pin_memory=True))
         req = _capi.Request(mesh.id, _field_id(field), n, _ptr(x), _ptr(u), float(dt),
                             _ptr(start),
                             MODES[mode] if isinstance(mode, str) else int(mode),
@@ -636,6 +642,19 @@ class Context:
         s = _capi.ServeStats()
         self._check(self.lib.cs_serve_report(self.h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in _capi.ServeStats._fields_}
+
+    def serve_trace(self):
+        """Records of the requests finished so far, in finishing order: dicts
+        of ticket, n, mesh_id, mode_used, slot, in_flight, result, dt, the
+        submit, admit and done times in ms since the first submit, and the
+        device times of the request's stages (h2d_ms, predict_ms, walk_ms,
+        d2h_ms)."""
+        count = ctypes.c_int64()
+        self._check(self.lib.cs_serve_trace(self.h, 0, None, ctypes.byref(count)))
+        recs = (_capi.ServeRecord * max(count.value, 1))()
+        self._check(self.lib.cs_serve_trace(self.h, count.value, recs, ctypes.byref(count)))
+        return [{k: getattr(recs[i], k) for k, _ in _capi.ServeRecord._fields_ if k != "reserved"}
+                for i in range(count.value)]
 
     def serve_stop(self):
         self._check(self.lib.cs_serve_stop(self.h))

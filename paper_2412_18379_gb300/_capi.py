@@ -130,11 +130,19 @@ class ServeStats(ctypes.Structure):
                 ("max_concurrent", _i32)]
 
 
+class ServeRecord(ctypes.Structure):
+    _fields_ = [("ticket", _i64), ("n", _i64), ("mesh_id", _i32), ("mode_used", _i32),
+                ("slot", _i32), ("in_flight", _i32), ("result", _i32), ("reserved", _i32),
+                ("dt", _dbl), ("submit_ms", _dbl), ("admit_ms", _dbl), ("done_ms", _dbl),
+                ("h2d_ms", _dbl), ("predict_ms", _dbl), ("walk_ms", _dbl), ("d2h_ms", _dbl)]
+
+
 SIGNATURES.update({
     "cs_serve_start": (_i32, [_vp, ctypes.POINTER(ServeCfg)]),
     "cs_serve_submit": (_i32, [_vp, ctypes.POINTER(Request), ctypes.POINTER(_i64)]),
     "cs_serve_wait": (_i32, [_vp, _i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "cs_serve_report": (_i32, [_vp, ctypes.POINTER(ServeStats)]),
+    "cs_serve_trace": (_i32, [_vp, _i64, ctypes.POINTER(ServeRecord), ctypes.POINTER(_i64)]),
     "cs_serve_stop": (_i32, [_vp]),
 })
 

@@ -80,11 +80,13 @@ struct Request {
     cs_status result = CS_OK;
     bool done = false;
     int used_mode = 0;
+    int in_flight = 0;             // requests on the GPU once it was admitted
 };
 
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t stage[5] = {};     // timed: admit, inputs in, predicted, walked, outputs out
     int32_t *counters = nullptr;   // walk cursors, see Scratch
     int parity = 0;
     Request *req = nullptr;
@@ -107,6 +109,7 @@ struct Server {
     bool pred3_any = false;
     // statistics
     std::vector<double> lat_ms;
+    std::vector<cs_serve_record> trace;   // finished requests, in finishing order
     int64_t completed = 0, rejected = 0, particles = 0;
     int32_t active = 0, max_active = 0;
     Clock::time_point t_first, t_last;
@@ -155,10 +158,12 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     float *own_grid = cnn && !q.grid ? reinterpret_cast<float *>(take(size_t(m.d.n_pasg) * d * 4))
                                      : nullptr;
     cudaStream_t st = sl.st;
-    cudaError_t e = cudaMemcpyAsync(x, r.x, n * d * 8, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaEventRecord(sl.stage[0], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, r.x, n * d * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, r.u, n * d * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && start)
         e = cudaMemcpyAsync(start, r.start, n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.stage[1], st);
     if (e != cudaSuccess) return CS_ECUDA;
     if (cnn) {
         // the start predictor on the request's own field: the field's resident
@@ -180,6 +185,7 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
             S.pred3_any = true;
         }
     }
+    if (cudaEventRecord(sl.stage[2], st) != cudaSuccess) return CS_ECUDA;
     TrackArgs a{};
     a.n = r.n;
     a.x = x;
@@ -197,9 +203,11 @@ cs_status start_request(Server &S, Slot &sl, Request &q) {
     sc.parity = sl.parity;
     ctx->launches += launch_track(m.d, a, sc, ctx->sm_count, st, nullptr);
     sl.parity = sc.parity;
-    e = cudaMemcpyAsync(r.host_out, host, n * 4, cudaMemcpyDeviceToHost, st);
+    e = cudaEventRecord(sl.stage[3], st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(r.host_out, host, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.path_len_out, path, n * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(r.status_out, status, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.stage[4], st);
     if (e == cudaSuccess) e = cudaEventRecord(sl.ev, st);
     return e == cudaSuccess ? CS_OK : CS_ECUDA;
 }
@@ -219,6 +227,30 @@ void finish(Server &S, Slot &sl, cs_status rc) {
         S.lat_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
         S.t_last = q->t_done;
     }
+    auto ms = [&S](Clock::time_point t) {
+        return std::chrono::duration<double, std::milli>(t - S.t_first).count();
+    };
+    cs_serve_record rec{};
+    rec.ticket = q->ticket;
+    rec.n = q->r.n;
+    rec.mesh_id = q->r.mesh_id;
+    rec.mode_used = q->used_mode;
+    rec.slot = int32_t(&sl - S.slots.data());
+    rec.in_flight = q->in_flight;
+    rec.result = rc;
+    rec.dt = q->r.dt;
+    if (rc == CS_OK) {
+        double *span[4] = {&rec.h2d_ms, &rec.predict_ms, &rec.walk_ms, &rec.d2h_ms};
+        for (int i = 0; i < 4; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, sl.stage[i], sl.stage[i + 1]) == cudaSuccess)
+                *span[i] = double(t);
+        }
+    }
+    rec.submit_ms = ms(q->t_submit);
+    rec.admit_ms = ms(q->t_admit);
+    rec.done_ms = ms(q->t_done);
+    S.trace.push_back(rec);
     S.done_cv.notify_all();
 }
 
@@ -253,6 +285,7 @@ void worker_loop(Server *Sp) {
                 S.pending.pop_front();
                 S.active += 1;
                 S.max_active = std::max(S.max_active, S.active);
+                h->in_flight = S.active;
                 q = h;
             }
             q->t_admit = Clock::now();
@@ -293,6 +326,8 @@ void serve_release(cs_ctx *ctx) {
     for (Slot &sl : S->slots) {
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        for (cudaEvent_t &t : sl.stage)
+            if (t) cudaEventDestroy(t);
         dfree(ctx, sl.counters);
     }
     if (S->pred3_ev) cudaEventDestroy(S->pred3_ev);
@@ -333,6 +368,9 @@ cs_status cs_serve_start(cs_ctx *ctx, const cs_serve_cfg *cfg) {
     for (Slot &sl : S->slots) {
         if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreate(&sl.stage[0]) != cudaSuccess || cudaEventCreate(&sl.stage[1]) != cudaSuccess ||
+            cudaEventCreate(&sl.stage[2]) != cudaSuccess || cudaEventCreate(&sl.stage[3]) != cudaSuccess ||
+            cudaEventCreate(&sl.stage[4]) != cudaSuccess ||
             dmalloc_n(ctx, &sl.counters, 16) != CS_OK ||
             cudaMemset(sl.counters, 0, 16 * sizeof(int32_t)) != cudaSuccess) {
             ctx->server = S;
@@ -467,6 +505,23 @@ cs_status cs_serve_report(cs_ctx *ctx, cs_serve_stats *out) {
         out->wall_s = wall;
         out->particles_per_s = wall > 0 ? double(S->particles) / wall : 0.0;
     }
+    return CS_OK;
+}
+
+cs_status cs_serve_trace(cs_ctx *ctx, int64_t cap, cs_serve_record *out, int64_t *count) {
+    if (!ctx) return CS_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return sfail(ctx, CS_EINVAL, "cs_serve_trace: not serving");
+    if (!count || cap < 0) return sfail(ctx, CS_EINVAL, "cs_serve_trace: bad arguments");
+    std::lock_guard<std::mutex> lock(S->mu);
+    const int64_t held = int64_t(S->trace.size());
+    if (!out) {
+        *count = held;
+        return CS_OK;
+    }
+    const int64_t k = std::min(cap, held);
+    if (k > 0) std::memcpy(out, S->trace.data(), size_t(k) * sizeof(cs_serve_record));
+    *count = k;
     return CS_OK;
 }
 

@@ -125,3 +125,22 @@ def test_classifier_parameters_are_sized_before_the_library_is_called():
     ctx.classifier_size = lambda dim: 100
     with pytest.raises(ValueError):
         ctx.load_classifier(2, np.zeros(99, dtype=np.float32))
+
+
+def test_submit_checks_the_callers_result_buffers():
+    """A served request writes its results into the caller's buffers when
+    given: short, mistyped, incomplete or device buffers are refused before
+    the library is called."""
+    ctx = _ctx()
+    mesh = _FakeMesh(2)
+    x, u, s = _good()
+    good = dict(host=np.empty(8, np.int32), path_len=np.empty(8, np.int32),
+                status=np.empty(8, np.uint8))
+    bad = [dict(good, host=np.empty(7, np.int32)),
+           dict(good, status=np.empty(8, np.int32)),
+           {k: v for k, v in good.items() if k != "path_len"}]
+    if torch.cuda.is_available():
+        bad.append(dict(good, host=torch.empty(8, dtype=torch.int32, device="cuda")))
+    for out in bad:
+        with pytest.raises(ValueError):
+            ctx.submit(mesh, x, u, 0.1, start=s, mode="sns", out=out)

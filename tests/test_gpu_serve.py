@@ -59,10 +59,20 @@ def _requests(meshes, count, seed):
 
 
 def _run(ctx, reqs, burst):
+    import torch
     outs = [None] * len(reqs)
     if burst:
-        tickets = [ctx.submit(m, x, u, dt, start=st, mode=mode, field=f)
-                   for m, x, u, st, dt, mode, f in reqs]
+        # odd requests write into slices of one pinned block the caller owns
+        total = sum(int(x.shape[0]) for _, x, *_ in reqs)
+        block = dict(host=torch.full((total,), -7, dtype=torch.int32, pin_memory=True),
+                     path_len=torch.full((total,), -7, dtype=torch.int32, pin_memory=True),
+                     status=torch.full((total,), 77, dtype=torch.uint8, pin_memory=True))
+        tickets, o = [], 0
+        for i, (m, x, u, st, dt, mode, f) in enumerate(reqs):
+            n = int(x.shape[0])
+            out = {k: v[o:o + n] for k, v in block.items()} if i % 2 else None
+            o += n
+            tickets.append(ctx.submit(m, x, u, dt, start=st, mode=mode, field=f, out=out))
         modes = [ctx.wait(t) for t, _ in tickets]
         outs = [{k: v.numpy().copy() for k, v in o.items()} for _, o in tickets]
     else:
@@ -82,6 +92,7 @@ def test_results_same_alone_and_in_the_mix(setup):
         alone, modes_a = _run(ctx, reqs, burst=False)
         mixed, modes_b = _run(ctx, reqs, burst=True)
         rep = ctx.serve_report()
+        trace = ctx.serve_trace()
     finally:
         ctx.serve_stop()
     assert modes_a == modes_b
@@ -98,6 +109,31 @@ def test_results_same_alone_and_in_the_mix(setup):
     assert rep["completed"] == 72 and rep["rejected"] == 0
     assert rep["max_concurrent"] > 1
     assert 0 < rep["p50_ms"] <= rep["p99_ms"] <= rep["max_ms"]
+    # the trace holds every request once, in finishing order, with its own
+    # size, mesh and start rule, and the report's latencies are its spans
+    assert len(trace) == 72
+    assert len({r["ticket"] for r in trace}) == 72
+    assert sorted(r["n"] for r in trace) == sorted(2 * [int(q[1].shape[0]) for q in reqs])
+    assert sorted(r["mesh_id"] for r in trace) == sorted(2 * [q[0].id for q in reqs])
+    assert all(r["result"] == 0 and 0 <= r["slot"] < 6 and 1 <= r["in_flight"] <= 6
+               and 0 <= r["submit_ms"] <= r["admit_ms"] <= r["done_ms"] for r in trace)
+    assert all(a["done_ms"] <= b["done_ms"] for a, b in zip(trace, trace[1:]))
+    assert max(r["in_flight"] for r in trace) == rep["max_concurrent"]
+    # the device time of a request's stages fits in its admit-to-done span;
+    # only CNN-SNS requests run the predictor, and each keeps its own dt
+    # (tickets count from 1 in submission order: both runs submit reqs in order)
+    for r in trace:
+        q = reqs[(r["ticket"] - 1) % len(reqs)]
+        assert r["n"] == int(q[1].shape[0]) and r["dt"] == q[4]
+        stages = r["h2d_ms"] + r["predict_ms"] + r["walk_ms"] + r["d2h_ms"]
+        assert r["h2d_ms"] > 0 and r["walk_ms"] > 0 and r["d2h_ms"] > 0
+        assert stages <= r["done_ms"] - r["admit_ms"] + 0.05
+        if r["mode_used"] == 1:
+            assert r["predict_ms"] > 0
+        else:
+            assert r["predict_ms"] < 0.05
+    lat = sorted(r["done_ms"] - r["submit_ms"] for r in trace)
+    assert abs(lat[-1] - rep["max_ms"]) < 1e-6 and abs(lat[35] - rep["p50_ms"]) < 1e-6
     # the serving results equal the direct host-pointer entry point
     for i in range(6):
         m, x, u, st, dt, mode, f = reqs[i]
