@@ -839,22 +839,43 @@ def main():
     hout = dict(host=torch.empty(n, dtype=torch.int32).pin_memory(),
                 path_len=torch.empty(n, dtype=torch.int32).pin_memory(),
                 status=torch.empty(n, dtype=torch.uint8).pin_memory())
-    for _ in range(0 if args.quick else 3):
-        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout, field=field)
-    torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 10) if not args.quick else 1
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout, field=field)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        e2e_s = max_over_ranks(e2e_s, device=dev)
-    e2e = {"value": (n_total if args.shard else world * n) / e2e_s, "unit": "particles/s",
-           "h2d_bytes_per_step": n * dim * 16 + (0 if sh is None else n * 4),
-           "d2h_bytes_per_step": n * 9,
-           "entry_point": "cs_track_host",
-           "transfer": "page-locked host buffers; the call copies the inputs to a device "
-                       "staging buffer and the results back (cudaMemcpyAsync), then synchronises"}
+    # The mesh-node workload goes through the nodes call: the particles sit
+    # at the uploaded vertices, so a step copies in only u. Other layouts,
+    # and the general call for comparison, copy x as well.
+    nodes = sh is None and px is case.x and n == mesh.n_vertices
+
+    def host_step(general):
+        if general:
+            ctx.track_host(mesh, xh, uh, case.dt, start=sh, mode=args.mode, out=hout, field=field)
+        else:
+            ctx.track_nodes_host(mesh, uh, case.dt, mode=args.mode, out=hout, field=field)
+
+    def time_host(general):
+        for _ in range(0 if args.quick else 3):
+            host_step(general)
+        torch.cuda.synchronize()
+        steps = max(3, args.steps // 10) if not args.quick else 1
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step(general)
+        sec = (time.perf_counter() - t0) / steps
+        if dist is not None:
+            sec = max_over_ranks(sec, device=dev)
+        return (n_total if args.shard else world * n) / sec
+
+    transfer = ("page-locked host buffers; the call copies the inputs to a device staging "
+                "buffer and the results back (cudaMemcpyAsync), then synchronises")
+    general = {"value": time_host(True), "unit": "particles/s",
+               "h2d_bytes_per_step": n * dim * 16 + (0 if sh is None else n * 4),
+               "d2h_bytes_per_step": n * 9, "entry_point": "cs_track_host", "transfer": transfer}
+    if nodes:
+        e2e = {"value": time_host(False), "unit": "particles/s",
+               "h2d_bytes_per_step": n * dim * 8, "d2h_bytes_per_step": n * 9,
+               "entry_point": "cs_track_nodes_host",
+               "transfer": transfer + "; x is the mesh's resident vertex coordinates",
+               "general_call": general}
+    else:
+        e2e = general
 
     classifier = None
     if not args.no_classifier and args.particles == "nodes" and not args.shard:

@@ -205,6 +205,18 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
                         int mode, int32_t *host_out, int32_t *path_len_out,
                         uint8_t *status_out, int32_t *start_out);
 
+/* cs_track_host for the mesh nodes: the departure points (Eq. 3) of all n_v
+ * vertices, each particle at its vertex's coordinates as passed to
+ * cs_mesh_upload (the mesh keeps a device copy, so x is not copied in) and
+ * starting from its node's element. This is the step of a solver that
+ * tracks its mesh nodes, whose coordinates do not change. u_nodal: HOST
+ * [n_v][dim]; outputs HOST [n_v]. The same results, modes, field rule,
+ * pipeline and errors as cs_track_host with n = n_v, x = those coordinates
+ * and start = NULL. */
+cs_status cs_track_nodes_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id,
+                              const double *u_nodal, double dt, int mode, int32_t *host_out,
+                              int32_t *path_len_out, uint8_t *status_out, int32_t *start_out);
+
 /*
  * cs_track without any device allocation. (This entry point is a property of
  * the library, not of the method: the paper has no counterpart.)

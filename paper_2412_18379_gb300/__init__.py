@@ -318,6 +318,27 @@ class Context:
             _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start"))))
         return out
 
+    def track_nodes_host(self, mesh, u, dt, mode="sns", out=None, start_out=False, field=None):
+        """track_host for the mesh nodes at their uploaded coordinates: only
+        u (host float64 [n_v, dim]) is copied in."""
+        if isinstance(u, np.ndarray):
+            u = np.ascontiguousarray(u, dtype=np.float64)
+        n = mesh.n_vertices
+        if getattr(u, "ndim", None) != 2 or tuple(u.shape) != (n, mesh.dim):
+            raise ValueError("u must have shape [%d, %d]" % (n, mesh.dim))
+        # x stands in for the vertices in the common check (same shape as u)
+        check_track_args(mesh.dim, u, u, None, out, on_device=False)
+        if out is None:
+            out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
+                       status=np.empty(n, dtype=np.uint8))
+            if start_out:
+                out["start"] = np.empty(n, dtype=np.int32)
+        self._check(self.lib.cs_track_nodes_host(
+            self.h, mesh.id, _field_id(field), _ptr(u), float(dt),
+            MODES[mode] if isinstance(mode, str) else int(mode), _ptr(out["host"]),
+            _ptr(out["path_len"]), _ptr(out["status"]), _ptr(out.get("start"))))
+        return out
+
     def track_error(self, mesh, x, u, dt, host, start=None, dhat=None, stream=None):
         """Error statistics (Sec. 3.1) of a finished call: mean/max origin error
         err (centroid of the start element to centroid of the host) and, with

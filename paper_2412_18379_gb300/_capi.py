@@ -66,6 +66,8 @@ SIGNATURES = {
                         _vp, _vp, _vp]),
     "cs_track_host": (_i32, [_vp, _i32, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp,
                              _vp, _vp, _vp]),
+    "cs_track_nodes_host": (_i32, [_vp, _i32, _i32, _vp, _dbl, ctypes.c_int, _vp, _vp, _vp,
+                                   _vp]),
     "cs_track_noalloc": (_i32, [_vp, _i32, _i32, _i64, _vp, _vp, _dbl, _vp, ctypes.c_int, _vp,
                                 _vp, _vp, _vp, _vp]),
     "cs_track_stats": (_i32, [_vp, _i64, _vp, _vp, ctypes.POINTER(_i64), _vp]),

@@ -251,7 +251,7 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
     unsigned char *recw = nullptr, *recx = nullptr;
     int32_t *iperm = nullptr, *node = nullptr, *seed = nullptr, *bstart = nullptr,
             *bitems = nullptr, *cn = nullptr;
-    double *cent = nullptr;
+    double *cent = nullptr, *xyzd = nullptr;
     std::vector<int32_t> node_int(static_cast<size_t>(n_v));
     for (int64_t v = 0; v < n_v; ++v)
         node_int[v] = H.node_elem[v] < 0 ? -1 : H.iperm[H.node_elem[v]];
@@ -262,10 +262,12 @@ cs_status cs_mesh_upload(cs_ctx *ctx, int dim, int64_t n_v, const double *xyz, i
         (rc = dev_copy(ctx, m, H.bstart.data(), H.bstart.size(), &bstart)) ||
         (rc = dev_copy(ctx, m, H.bitems.data(), H.bitems.size(), &bitems)) ||
         (rc = dev_copy(ctx, m, H.conn.data(), H.conn.size(), &cn)) ||
-        (rc = dev_copy(ctx, m, H.centroid.data(), H.centroid.size(), &cent))) {
+        (rc = dev_copy(ctx, m, H.centroid.data(), H.centroid.size(), &cent)) ||
+        (rc = dev_copy(ctx, m, xyz, size_t(n_v) * size_t(dim), &xyzd))) {
         free_mesh(ctx, m);
         return rc;
     }
+    m->xyz = xyzd;
     int64_t n_asg = 1, n_b = 1;
     for (int k = 0; k < dim; ++k) {
         n_asg *= H.ga[k];
@@ -526,42 +528,42 @@ cs_status cs::cs_track_impl(cs_ctx *ctx, cs::Mesh *m, int64_t n, const double *x
     return CS_OK;
 }
 
-extern "C" {
+namespace {
 
-cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
-                        const double *x, const double *u, double dt, const int32_t *start,
-                        int mode, int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
-                        int32_t *start_out) {
-    if (!ctx) return CS_EINVAL;
-    cs::Mesh *m = find_mesh(ctx, mesh_id);
-    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_host: unknown mesh id");
+// The host-memory tracking call: x either in host memory (copied in by
+// chunks) or, with x_dev, already on the device (the mesh's vertices).
+cs_status track_host_impl(cs_ctx *ctx, const std::string &name, cs::Mesh *m, int32_t mesh_id,
+                          int32_t field_id, int64_t n, const double *x, const double *x_dev,
+                          const double *u, double dt, const int32_t *start, int mode,
+                          int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                          int32_t *start_out) {
     if (n < 0 || n >= (int64_t(1) << 31) - 1)
-        return fail(ctx, CS_EINVAL, "cs_track_host: n is outside [0, 2^31 - 2]");
+        return fail(ctx, CS_EINVAL, name + ": n is outside [0, 2^31 - 2]");
     if (mode != CS_SNS && mode != CS_ASG_DIRECT && mode != CS_CNN_SNS)
-        return fail(ctx, CS_EINVAL, "cs_track_host: bad mode");
+        return fail(ctx, CS_EINVAL, name + ": bad mode");
     cs::Field *f = nullptr;
     if (mode == CS_CNN_SNS) {
         if (!ctx->pred[m->d.dim - 2].loaded)
-            return fail(ctx, CS_ENOPRED, "cs_track_host: no predictor loaded");
+            return fail(ctx, CS_ENOPRED, name + ": no predictor loaded");
         if (field_id != CS_NO_FIELD) {
             auto it = ctx->fields.find(field_id);
             if (it == ctx->fields.end() || it->second->mesh_id != mesh_id)
-                return fail(ctx, CS_EINVAL, "cs_track_host: field id is not a field of this mesh");
+                return fail(ctx, CS_EINVAL, name + ": field id is not a field of this mesh");
             f = it->second;
         }
     }
     if (n == 0) return CS_OK;
-    if (!x || !u || !host_out || !path_len_out || !status_out)
-        return fail(ctx, CS_EINVAL, "cs_track_host: null pointer");
+    if ((!x && !x_dev) || !u || !host_out || !path_len_out || !status_out)
+        return fail(ctx, CS_EINVAL, name + ": null pointer");
     if (!start && n != m->d.n_v)
-        return fail(ctx, CS_EINVAL, "cs_track_host: start == NULL needs n == n_vertices");
+        return fail(ctx, CS_EINVAL, name + ": start == NULL needs n == n_vertices");
     // CNN-SNS without a field predicts from the call's own nodal velocity:
     // all of u has to be on the device before the predictor runs
     const bool whole_u = mode == CS_CNN_SNS && !f;
     if (whole_u && start)
         return fail(ctx, CS_EINVAL,
-                    "cs_track_host: CNN-SNS needs a field id (cs_field_upload) unless the "
-                    "particles are the mesh nodes");
+                    name + ": CNN-SNS needs a field id (cs_field_upload) unless the "
+                           "particles are the mesh nodes");
     CS_CUDA(ctx, cudaSetDevice(ctx->device));
     cs_status rc = ensure_scratch(ctx);
     if (rc) return rc;
@@ -585,7 +587,7 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
     }
     if ((rc = ensure_host_streams(ctx))) return rc;
     char *buf = S.stage;
-    double *dx = reinterpret_cast<double *>(buf);
+    const double *dx = x_dev ? x_dev : reinterpret_cast<const double *>(buf);
     double *du = reinterpret_cast<double *>(buf + in_b);
     int32_t *ds = reinterpret_cast<int32_t *>(buf + 2 * in_b);
     int32_t *dh = ds + n, *dp = dh + n, *dso = dp + n;
@@ -606,7 +608,9 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
     }
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
         const int64_t lo = n * i / K, hi = n * (i + 1) / K, c = hi - lo;
-        e = cudaMemcpyAsync(dx + lo * dim, x + lo * dim, size_t(c) * dim * 8, cudaMemcpyHostToDevice, s_in);
+        if (!x_dev)
+            e = cudaMemcpyAsync(reinterpret_cast<double *>(buf) + lo * dim, x + lo * dim,
+                                size_t(c) * dim * 8, cudaMemcpyHostToDevice, s_in);
         if (e == cudaSuccess && !whole_u)
             e = cudaMemcpyAsync(du + lo * dim, u + lo * dim, size_t(c) * dim * 8, cudaMemcpyHostToDevice,
                                 s_in);
@@ -614,7 +618,7 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
             e = cudaMemcpyAsync(ds + lo, start + lo, size_t(c) * 4, cudaMemcpyHostToDevice, s_in);
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 + i], s_in);
     }
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host: copy in");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, (name + ": copy in").c_str());
     const float *dhat = nullptr;
     if (mode == CS_CNN_SNS) {
         const float *grid = nullptr;
@@ -625,7 +629,7 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
         const int64_t lo = n * i / K, hi = n * (i + 1) / K, c = hi - lo;
         e = cudaStreamWaitEvent(s_cmp, ev[2 + i], 0);
         if (e != cudaSuccess) {
-            rc = cuda_fail(ctx, e, "cs_track_host: event wait");
+            rc = cuda_fail(ctx, e, (name + ": event wait").c_str());
             break;
         }
         const int32_t *st0 = start ? ds + lo : m->node_start_user + lo;
@@ -644,7 +648,7 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
             if (e == cudaSuccess && start_out)
                 e = cudaMemcpyAsync(start_out + lo, dso + lo, size_t(c) * 4, cudaMemcpyDeviceToHost,
                                     s_out);
-            if (e != cudaSuccess) rc = cuda_fail(ctx, e, "cs_track_host: copy out");
+            if (e != cudaSuccess) rc = cuda_fail(ctx, e, (name + ": copy out").c_str());
         }
     }
     // every stream drained before return (also after a failed launch)
@@ -652,8 +656,34 @@ cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t 
                       e3 = cudaStreamSynchronize(s_out);
     if (rc) return rc;
     e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cs_track_host");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, name.c_str());
     return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_track_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, int64_t n,
+                        const double *x, const double *u, double dt, const int32_t *start,
+                        int mode, int32_t *host_out, int32_t *path_len_out, uint8_t *status_out,
+                        int32_t *start_out) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_host: unknown mesh id");
+    return track_host_impl(ctx, "cs_track_host", m, mesh_id, field_id, n, x, nullptr, u, dt, start,
+                           mode, host_out, path_len_out, status_out, start_out);
+}
+
+cs_status cs_track_nodes_host(cs_ctx *ctx, int32_t mesh_id, int32_t field_id, const double *u,
+                              double dt, int mode, int32_t *host_out, int32_t *path_len_out,
+                              uint8_t *status_out, int32_t *start_out) {
+    if (!ctx) return CS_EINVAL;
+    cs::Mesh *m = find_mesh(ctx, mesh_id);
+    if (!m) return fail(ctx, CS_ENOMESH, "cs_track_nodes_host: unknown mesh id");
+    return track_host_impl(ctx, "cs_track_nodes_host", m, mesh_id, field_id, m->d.n_v, nullptr,
+                           m->xyz, u, dt, nullptr, mode, host_out, path_len_out, status_out,
+                           start_out);
 }
 
 cs_status cs_track_stats(cs_ctx *ctx, int64_t n, const int32_t *path_len, const uint8_t *status,

@@ -118,6 +118,7 @@ struct Mesh {
     bool grid_u_valid = false;
     int32_t pgrid_version = 0;            // bumped by every cs_predictor_grid
     int32_t *node_start_user = nullptr;   // [n_v] plain starts as user ids (cs_track_host)
+    double *xyz = nullptr;                // [n_v][dim] the uploaded vertices, user order
 };
 
 // A velocity field of a mesh (cs_field_upload): the nodal velocity, kept for

@@ -144,3 +144,18 @@ def test_submit_checks_the_callers_result_buffers():
     for out in bad:
         with pytest.raises(ValueError):
             ctx.submit(mesh, x, u, 0.1, start=s, mode="sns", out=out)
+
+
+def test_nodes_call_checks_the_velocity_first():
+    """cs_track_nodes_host reads u [n_v, dim] float64 from host memory; a
+    wrong shape, dtype or layout is refused before the library is called."""
+    ctx = _ctx()
+    mesh = _FakeMesh(2, n_v=10)
+    for u in (np.zeros((9, 2)), np.zeros((10, 3)), torch.zeros((10, 2), dtype=torch.float32),
+              torch.zeros((2, 10), dtype=torch.float64).t()):
+        with pytest.raises(ValueError):
+            ctx.track_nodes_host(mesh, u, 0.1)
+    with pytest.raises(ValueError):
+        ctx.track_nodes_host(mesh, np.zeros((10, 2)), 0.1,
+                             out=dict(host=np.empty(9, np.int32), path_len=np.empty(10, np.int32),
+                                      status=np.empty(10, np.uint8)))

@@ -312,6 +312,35 @@ def test_host_entry_point_matches_the_device_one(ctx, mode):
 
 
 @pytest.mark.parametrize("mode", ["sns", "asg", "cnn"])
+def test_nodes_entry_point_matches_the_host_one(ctx, mode):
+    """cs_track_nodes_host (the particles at the mesh's own vertex
+    coordinates, only u copied in) gives the bits of cs_track_host on x = the
+    vertices: in 2-D on a mesh large enough for the chunked pipeline, and in
+    3-D; with the call's own u (page-locked and pageable) and with a resident
+    field."""
+    import torch
+    from workloads.weights import init_weights
+    for name, kw, stride in (("tg2d", {"n_side": 1001}, 5), ("abc3d", {"n_side": 41}, 3)):
+        c = make_case(name, cfl=8, **kw)
+        assert np.array_equal(c.x, c.xyz)
+        ctx.load_predictor(c.dim, init_weights(c.dim, 12))
+        mesh = ctx.upload_mesh(c.xyz, c.conn)
+        mesh.set_predictor_grid(stride)
+        want = ctx.track_host(mesh, c.x, c.u, c.dt, mode=mode, start_out=True)
+        for u in (torch.from_numpy(c.u).pin_memory(), c.u):
+            got = ctx.track_nodes_host(mesh, u, c.dt, mode=mode, start_out=True)
+            for k in ("host", "path_len", "status", "start"):
+                assert np.array_equal(got[k], want[k]), (name, mode, k)
+        f = ctx.upload_field(mesh, c.u)
+        want = ctx.track_host(mesh, c.x, c.u, c.dt, mode=mode, field=f)
+        got = ctx.track_nodes_host(mesh, c.u, c.dt, mode=mode, field=f)
+        for k in ("host", "path_len", "status"):
+            assert np.array_equal(got[k], want[k]), (name, mode, "field", k)
+        f.release()
+        mesh.release()
+
+
+@pytest.mark.parametrize("mode", ["sns", "asg", "cnn"])
 def test_shards_of_one_batch_concatenate_to_the_whole(ctx, mode):
     """The multi-GPU split of one batch (bench.py --shard): each of 3 shards
     (shard_range slices, the node particles with their node's element as an
