@@ -42,6 +42,20 @@ WORKLOADS = {
 }
 
 REC_ALG_BYTES = {2: 60, 3: 112}      # v0 + M + neighbours per walk step
+# The FP64 ceiling of the walk: R1's arithmetic has no FMA, so every
+# operation takes one FP64 issue slot; GB300's nominal 1.25 TFLOP/s counts an
+# FMA as two flops.
+FP64_OPS_PEAK_T = 1.25 / 2
+
+
+def walk_fp64_ops(n, dim, sum_path):
+    """FP64 operations of R1's arithmetic for n particles walking sum_path
+    element evaluations in all: per particle the departure point (d products,
+    d differences); per evaluation delta = x_p - v0 (d), M delta (d^2
+    products, d (d - 1) sums), lambda_0 (d differences) and the containment
+    test (d + 1 compares)."""
+    per_eval = dim + dim * dim + dim * (dim - 1) + dim + (dim + 1)
+    return n * 2 * dim + sum_path * per_eval
 # useful FLOPs of the grid predictor per ASG cell (2-D): conv1 2*18*32, conv2-4
 # 3 * 2*288*32, fc1 2*32*256, fc2 2*256*2
 CNN_FLOP_PER_CELL_2D = 2 * (18 * 32 + 3 * 288 * 32 + 32 * 256 + 256 * 2)
@@ -818,6 +832,16 @@ def main():
                  "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
     walk_roof["frac"] = walk_roof["achieved"] / hbm_peak
     rooflines = {"walk": walk_roof}
+    fp64_ops = walk_fp64_ops(n, dim, sum_path)
+    fp64_t = fp64_ops / (walk_ms / walk_l * 1e-3) / 1e12
+    rooflines["walk_fp64"] = {
+        "bound": "alu", "achieved": fp64_t, "peak": FP64_OPS_PEAK_T, "unit": "TFLOP/s",
+        "frac": fp64_t / FP64_OPS_PEAK_T, "kernel": "walk_kernel<%d>" % dim,
+        "algorithmic_flops_per_launch": fp64_ops,
+        "peak_source": "nominal FP64 1.25 TFLOP/s (an FMA as two flops) = 0.625 T unfused "
+                       "operations/s; R1's arithmetic has no FMA",
+        "note": "R1's operations counted as if executed in FP64; the walk decides most steps "
+                "in certified FP32, so the fraction can pass 1"}
     cnn_l, cnn_ms = main_prof.get("cnn", (0, 0.0))
     if cnn_l and dim == 2:
         flops = CNN_FLOP_PER_CELL_2D * int(np.prod(info["pred_grid"]))

@@ -106,3 +106,12 @@ def test_shards_cover_the_batch_with_explicit_node_starts():
     start = rng.integers(0, 5000, size=1001).astype(np.int32)
     p = bench.shard_particles(x, u, start, node, 1, 4)
     assert np.array_equal(p[2], start[251:501]) and p[2].dtype == np.int32
+
+
+def test_walk_fp64_operation_count():
+    """R1's FP64 operations, counted by hand: 2-D, per evaluation 2
+    differences, 4 products, 2 sums, 2 differences for lambda_0, 3 compares
+    (13); 3-D, 3 + 9 + 6 + 3 + 4 (25); per particle 2d for the departure."""
+    assert bench.walk_fp64_ops(1, 2, 1) == 4 + 13
+    assert bench.walk_fp64_ops(10, 3, 25) == 10 * 6 + 25 * 25
+    assert bench.walk_fp64_ops(0, 2, 0) == 0
