@@ -326,8 +326,20 @@ class Context:
         n = mesh.n_vertices
         if getattr(u, "ndim", None) != 2 or tuple(u.shape) != (n, mesh.dim):
             raise ValueError("u must have shape [%d, %d]" % (n, mesh.dim))
-        # x stands in for the vertices in the common check (same shape as u)
-        check_track_args(mesh.dim, u, u, None, out, on_device=False)
+        if _dtype_name(u) != "float64" or not _contiguous(u) or getattr(u, "is_cuda", False):
+            raise ValueError("u must be contiguous float64 in host memory")
+        if out is not None:
+            for key, want, need in (("host", "int32", True), ("path_len", "int32", True),
+                                    ("status", "uint8", True), ("start", "int32", False)):
+                a = out.get(key)
+                if a is None:
+                    if need:
+                        raise ValueError("out['%s'] is missing" % key)
+                    continue
+                if (_dtype_name(a) != want or not _contiguous(a) or _numel(a) < n
+                        or getattr(a, "is_cuda", False)):
+                    raise ValueError("out['%s'] must be contiguous %s in host memory with at "
+                                     "least n = %d elements" % (key, want, n))
         if out is None:
             out = dict(host=np.empty(n, dtype=np.int32), path_len=np.empty(n, dtype=np.int32),
                        status=np.empty(n, dtype=np.uint8))

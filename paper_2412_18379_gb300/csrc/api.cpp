@@ -601,11 +601,9 @@ cs_status track_host_impl(cs_ctx *ctx, const std::string &name, cs::Mesh *m, int
     cudaError_t e = cudaEventRecord(ev[0], nullptr);   // after the caller's earlier work
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev[0], 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev[0], 0);
-    if (e == cudaSuccess && whole_u) {
-        e = cudaMemcpyAsync(du, u, in_b, cudaMemcpyHostToDevice, s_in);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s_in);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s_cmp, ev[1], 0);
-    }
+    // the whole velocity goes on the compute stream itself: the predictor
+    // that reads it follows with no hop between streams
+    if (e == cudaSuccess && whole_u) e = cudaMemcpyAsync(du, u, in_b, cudaMemcpyHostToDevice, s_cmp);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
         const int64_t lo = n * i / K, hi = n * (i + 1) / K, c = hi - lo;
         if (!x_dev)

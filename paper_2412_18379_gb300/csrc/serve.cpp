@@ -246,6 +246,9 @@ void finish(Server &S, Slot &sl, cs_status rc) {
             if (cudaEventElapsedTime(&t, sl.stage[i], sl.stage[i + 1]) == cudaSuccess)
                 *span[i] = double(t);
         }
+        // no predictor ran: the gap between its two events is only the
+        // stream's wait behind other slots' work
+        if (q->used_mode != CS_CNN_SNS) rec.predict_ms = 0.0;
     }
     rec.submit_ms = ms(q->t_submit);
     rec.admit_ms = ms(q->t_admit);

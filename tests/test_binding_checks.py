@@ -159,3 +159,31 @@ def test_nodes_call_checks_the_velocity_first():
         ctx.track_nodes_host(mesh, np.zeros((10, 2)), 0.1,
                              out=dict(host=np.empty(9, np.int32), path_len=np.empty(10, np.int32),
                                       status=np.empty(10, np.uint8)))
+
+
+def test_nodes_call_passes_its_arguments_through():
+    """A well-formed call reaches cs_track_nodes_host once, with the mesh and
+    field ids, u's address, dt, the mode and the output addresses as given."""
+    calls = []
+
+    class _Record:
+        def __getattr__(self, name):
+            def f(*args):
+                calls.append((name, args))
+                return 0
+            return f
+
+    ctx = object.__new__(cs.Context)
+    ctx.lib = _Record()
+    ctx.h = None
+    mesh = _FakeMesh(2, n_v=10)
+    u = torch.zeros((10, 2), dtype=torch.float64)
+    out = dict(host=np.empty(10, np.int32), path_len=np.empty(10, np.int32),
+               status=np.empty(10, np.uint8))
+    got = ctx.track_nodes_host(mesh, u, 0.25, mode="cnn", out=out, field=7)
+    assert got is out
+    assert [c[0] for c in calls] == ["cs_track_nodes_host"]
+    args = calls[0][1]
+    assert args[1:6] == (mesh.id, 7, u.data_ptr(), 0.25, cs.CS_CNN_SNS)
+    assert args[6:] == (out["host"].ctypes.data, out["path_len"].ctypes.data,
+                        out["status"].ctypes.data, None)

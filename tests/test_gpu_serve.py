@@ -131,7 +131,7 @@ def test_results_same_alone_and_in_the_mix(setup):
         if r["mode_used"] == 1:
             assert r["predict_ms"] > 0
         else:
-            assert r["predict_ms"] < 0.05
+            assert r["predict_ms"] == 0
     lat = sorted(r["done_ms"] - r["submit_ms"] for r in trace)
     assert abs(lat[-1] - rep["max_ms"]) < 1e-6 and abs(lat[35] - rep["p50_ms"]) < 1e-6
     # the serving results equal the direct host-pointer entry point
