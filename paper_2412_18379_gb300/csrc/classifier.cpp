@@ -48,9 +48,11 @@ struct Classifier {
     int64_t n = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
     int64_t t = 0;
-    // workspace for `cap` rows (forward; backward when `train`)
-    int64_t cap = 0;
-    bool cap_train = false;
+    // workspace: the fully connected layers' buffers for `cap` rows, the
+    // unfused module 1's for `cap_conv` rows and the backward pass's for
+    // `cap_grad` rows (0 until a path needs them): the fused inference path
+    // runs long chunks without growing the training path's im2col buffers
+    int64_t cap = 0, cap_conv = 0, cap_grad = 0;
     std::vector<void *> ws;
     float *a0 = nullptr, *off = nullptr, *col1 = nullptr, *z1 = nullptr, *y1 = nullptr,
           *a1 = nullptr, *col2 = nullptr, *z2 = nullptr, *cat = nullptr, *h1 = nullptr,
@@ -102,8 +104,7 @@ void free_ws(cs_ctx *ctx, Classifier &C) {
     C.idx = nullptr;
     C.splitk = nullptr;
     C.splitk_n = 0;
-    C.cap = 0;
-    C.cap_train = false;
+    C.cap = C.cap_conv = C.cap_grad = 0;
 }
 
 void release(cs_ctx *ctx, Classifier *C) {
@@ -124,48 +125,63 @@ cs_status ws_alloc(cs_ctx *ctx, Classifier &C, T **p, int64_t count) {
     return rc;
 }
 
-// workspace for B rows; `train` adds the backward buffers
-cs_status ensure_ws(cs_ctx *ctx, Classifier &C, int64_t B, bool train) {
+// workspace for B rows of the fully connected layers; `conv` adds the
+// unfused module 1's buffers, `grad` the backward pass's (which reuses
+// module 1's, so it needs `conv` too). Growing any set reallocates all of
+// them, each at its own row count.
+cs_status ensure_ws(cs_ctx *ctx, Classifier &C, int64_t B, bool conv, bool grad) {
     if (!ctx->dev_err) {
         cs_status rc = dmalloc_n(ctx, &ctx->dev_err, 1);
         if (rc) return rc;
         if (cudaMemset(ctx->dev_err, 0, sizeof(int)) != cudaSuccess)
             return fail(ctx, CS_ECUDA, "cudaMemset of the device error flag failed");
     }
-    if (C.cap >= B && (C.cap_train || !train)) return CS_OK;
-    B = std::max(B, C.cap);
-    train = train || C.cap_train;
+    conv = conv || grad;
+    if (C.cap >= B && (!conv || C.cap_conv >= B) && (!grad || C.cap_grad >= B)) return CS_OK;
+    const int64_t rows = std::max(B, C.cap);
+    const int64_t rows_conv = conv ? std::max(B, C.cap_conv) : C.cap_conv;
+    const int64_t rows_grad = grad ? std::max(B, C.cap_grad) : C.cap_grad;
     free_ws(ctx, C);
     const ClsShape S(C.dim);
     const int64_t d = C.dim, K1 = d * S.taps, K2 = int64_t(kClsCh) * S.taps;
     cs_status rc;
-    if ((rc = ws_alloc(ctx, C, &C.a0, B * d * S.Pq)) || (rc = ws_alloc(ctx, C, &C.off, B * d)) ||
-        (rc = ws_alloc(ctx, C, &C.col1, B * S.P * K1)) ||
-        (rc = ws_alloc(ctx, C, &C.z1, B * S.P * kClsCh)) ||
-        (rc = ws_alloc(ctx, C, &C.y1, B * S.P * kClsCh)) ||
-        (rc = ws_alloc(ctx, C, &C.a1, B * S.Pq * kClsCh)) ||
-        (rc = ws_alloc(ctx, C, &C.col2, B * S.P * K2)) ||
-        (rc = ws_alloc(ctx, C, &C.z2, B * S.P * kClsCh)) ||
-        (rc = ws_alloc(ctx, C, &C.cat, B * S.ldc)) || (rc = ws_alloc(ctx, C, &C.h1, B * kClsH1)) ||
-        (rc = ws_alloc(ctx, C, &C.r1, B * kClsH1)) || (rc = ws_alloc(ctx, C, &C.h2, B * kClsH1)) ||
-        (rc = ws_alloc(ctx, C, &C.u, B * kClsH2)) || (rc = ws_alloc(ctx, C, &C.ru, B * kClsH2)) ||
-        (rc = ws_alloc(ctx, C, &C.H, B * S.n_cls)) ||
+    if ((rc = ws_alloc(ctx, C, &C.off, rows * d)) || (rc = ws_alloc(ctx, C, &C.cat, rows * S.ldc)) ||
+        (rc = ws_alloc(ctx, C, &C.h1, rows * kClsH1)) ||
+        (rc = ws_alloc(ctx, C, &C.r1, rows * kClsH1)) ||
+        (rc = ws_alloc(ctx, C, &C.h2, rows * kClsH1)) ||
+        (rc = ws_alloc(ctx, C, &C.u, rows * kClsH2)) ||
+        (rc = ws_alloc(ctx, C, &C.ru, rows * kClsH2)) ||
+        (rc = ws_alloc(ctx, C, &C.H, rows * S.n_cls)) ||
         (rc = ws_alloc(ctx, C, &C.splitk, tc_gemm_work_floats(ctx->sm_count)))) {
         free_ws(ctx, C);
         return rc;
     }
-    if (train &&
-        ((rc = ws_alloc(ctx, C, &C.gH, B * S.n_cls)) || (rc = ws_alloc(ctx, C, &C.gu, B * kClsH2)) ||
-         (rc = ws_alloc(ctx, C, &C.gcat, B * S.ldc)) ||
-         (rc = ws_alloc(ctx, C, &C.gh2, B * kClsH1)) ||
-         (rc = ws_alloc(ctx, C, &C.gh1, B * kClsH1)) ||
-         (rc = ws_alloc(ctx, C, &C.gz2, B * S.P * kClsCh)) || (rc = ws_alloc(ctx, C, &C.idx, B)))) {
+    const int64_t rv = rows_conv;
+    if (rv > 0 &&
+        ((rc = ws_alloc(ctx, C, &C.a0, rv * d * S.Pq)) ||
+         (rc = ws_alloc(ctx, C, &C.col1, rv * S.P * K1)) ||
+         (rc = ws_alloc(ctx, C, &C.z1, rv * S.P * kClsCh)) ||
+         (rc = ws_alloc(ctx, C, &C.y1, rv * S.P * kClsCh)) ||
+         (rc = ws_alloc(ctx, C, &C.a1, rv * S.Pq * kClsCh)) ||
+         (rc = ws_alloc(ctx, C, &C.col2, rv * S.P * K2)) ||
+         (rc = ws_alloc(ctx, C, &C.z2, rv * S.P * kClsCh)))) {
+        free_ws(ctx, C);
+        return rc;
+    }
+    const int64_t rg = rows_grad;
+    if (rg > 0 &&
+        ((rc = ws_alloc(ctx, C, &C.gH, rg * S.n_cls)) || (rc = ws_alloc(ctx, C, &C.gu, rg * kClsH2)) ||
+         (rc = ws_alloc(ctx, C, &C.gcat, rg * S.ldc)) ||
+         (rc = ws_alloc(ctx, C, &C.gh2, rg * kClsH1)) ||
+         (rc = ws_alloc(ctx, C, &C.gh1, rg * kClsH1)) ||
+         (rc = ws_alloc(ctx, C, &C.gz2, rg * S.P * kClsCh)) || (rc = ws_alloc(ctx, C, &C.idx, rg)))) {
         free_ws(ctx, C);
         return rc;
     }
     C.splitk_n = tc_gemm_work_floats(ctx->sm_count);
-    C.cap = B;
-    C.cap_train = train;
+    C.cap = rows;
+    C.cap_conv = rows_conv;
+    C.cap_grad = rows_grad;
     return CS_OK;
 }
 
@@ -304,9 +320,14 @@ uint64_t splitmix(uint64_t &s) {
     return z ^ (z >> 31);
 }
 
-// rows per forward chunk: about 1 GB of workspace on the training path's
-// kernels (the fused path uses a fraction of it)
-int64_t chunk_rows(int dim) { return dim == 2 ? 8192 : 1024; }
+// rows per forward chunk. The fused path needs only the fully connected
+// layers' buffers (about 10 KB a row in 2-D, 13 KB in 3-D): chunks of this
+// size give those GEMMs enough tiles to fill the GPU without splitting K.
+// The unfused path's im2col buffers take about 1 GB at its smaller chunks.
+int64_t chunk_rows(int dim, bool fused) {
+    if (fused) return dim == 2 ? 32768 : 16384;
+    return dim == 2 ? 8192 : 1024;
+}
 
 cs_status ensure_xp(cs_ctx *ctx, Classifier &C, int64_t n) {
     if (C.xp_cap >= n) return CS_OK;
@@ -328,8 +349,9 @@ cs_status ensure_xp(cs_ctx *ctx, Classifier &C, int64_t n) {
 template <class F>
 cs_status forward_chunks(cs_ctx *ctx, Classifier &C, const DevMesh &m, int64_t n, const double *xp,
                          cudaStream_t st, F each) {
-    const int64_t R = std::min<int64_t>(n, chunk_rows(C.dim));
-    cs_status rc = ensure_ws(ctx, C, R, false);
+    const bool fused = gemm_bf16();
+    const int64_t R = std::min<int64_t>(n, chunk_rows(C.dim, fused));
+    cs_status rc = ensure_ws(ctx, C, R, !fused, false);
     if (rc) return rc;
     for (int64_t r0 = 0; r0 < n; r0 += R) {
         const int64_t B = std::min(R, n - r0);
@@ -520,7 +542,7 @@ cs_status cs_classifier_grad(cs_ctx *ctx, int32_t mesh_id, int64_t B, const doub
     Classifier *C = get_cls(ctx, m->d.dim);
     if (!C) return fail(ctx, CS_ENOPRED, "cs_classifier_grad: no classifier loaded");
     CCHK(cudaSetDevice(ctx->device));
-    cs_status rc = ensure_ws(ctx, *C, B, true);
+    cs_status rc = ensure_ws(ctx, *C, B, true, true);
     if (rc) return rc;
     CCHK(cudaMemset(C->loss, 0, sizeof(float)));
     ctx->launches += forward(ctx, *C, m->d, B, xp, nullptr, nullptr);
@@ -544,7 +566,7 @@ cs_status cs_classifier_train(cs_ctx *ctx, int32_t mesh_id, const double *xp,
     if (!C) return fail(ctx, CS_ENOPRED, "cs_classifier_train: no classifier loaded");
     CCHK(cudaSetDevice(ctx->device));
     const int64_t B = std::min(batch, N);
-    cs_status rc = ensure_ws(ctx, *C, B, true);
+    cs_status rc = ensure_ws(ctx, *C, B, true, true);
     if (rc) return rc;
     float *losses = nullptr;
     if ((rc = dmalloc_n(ctx, &losses, size_t(std::max<int64_t>(steps, 1))))) return rc;

@@ -179,11 +179,11 @@ def test_forward_and_gradient_match_oracle(ctx, name, kw, bf16):
     _grad_check(ctx, mesh, om, flat, xp, labels, bf16)
 
 
-@pytest.mark.parametrize("name,kw,n", [("tg2d", {"n_side": 41}, 20000),
-                                        ("abc3d", {"n_side": 9}, 2500)])
+@pytest.mark.parametrize("name,kw,n", [("tg2d", {"n_side": 41}, 70000),
+                                        ("abc3d", {"n_side": 9}, 36000)])
 def test_inference_over_several_chunks(ctx, name, kw, n):
-    """Inference runs module 1 fused on the tensor cores, in chunks of 8192
-    (2-D) or 1024 (3-D) particles: logits of a batch spanning three chunks,
+    """Inference runs module 1 fused on the tensor cores, in chunks of 32768
+    (2-D) or 16384 (3-D) particles: logits of a batch spanning three chunks,
     with a ragged last one, against the FP64 forward on a sample of rows
     (every chunk's first and last row included), within the BF16 bound."""
     c, mesh, om = _setup(ctx, name, kw)
@@ -192,7 +192,7 @@ def test_inference_over_several_chunks(ctx, name, kw, n):
     flat = init_classifier(dim, 11)
     ctx.load_classifier(dim, flat)
     H = ctx.classifier_forward(mesh, _dev(xp)).cpu().numpy()
-    chunk = 8192 if dim == 2 else 1024
+    chunk = 32768 if dim == 2 else 16384
     rng = np.random.default_rng(22)
     rows = np.unique(np.concatenate([rng.choice(n, 150 if dim == 2 else 40, replace=False),
                                      np.arange(0, n, chunk), np.arange(chunk - 1, n, chunk),
